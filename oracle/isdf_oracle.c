@@ -1,0 +1,216 @@
+/*
+ * CPU FP64 oracle for the weight function and the weighted K-means of the
+ * complex-valued K-means ISDF (arXiv 2208.07731).
+ *
+ * TEST INFRASTRUCTURE ONLY. This file is the slow, plain reference that the
+ * CUDA path is checked against. Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark may load it; the product path never does.
+ * It shares no code with the CUDA library.
+ *
+ * Build: gcc -O2 -fopenmp -ffp-contract=off -shared -fPIC (no fast-math), so
+ * that every floating-point operation below is one IEEE-rounded operation in
+ * the written order.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef unsigned __int128 u128;
+
+/* |z|^alpha for z = re + i im, via m = |z|^2 = re*re + im*im (Eq. weight
+ * function 2). The four values of alpha the paper studies (SM, SSM, SCM, SQM:
+ * alpha = 1, 2, 3, 4) use sqrt and products only; any other alpha uses pow. */
+static double modpow(double re, double im, double alpha)
+{
+    double m = re * re;
+    m = m + im * im;
+    if (alpha == 2.0) return m;
+    if (alpha == 1.0) return sqrt(m);
+    if (alpha == 3.0) return m * sqrt(m);
+    if (alpha == 4.0) return m * m;
+    return pow(m, 0.5 * alpha);
+}
+
+/*
+ * Weight function, Sec. 2.2.
+ *   kind 0 (SSM family, Eq. weight function 2): w(r) = sum_i |phi_i(r)|^a + sum_j |psi_j(r)|^a
+ *   kind 1 (PSM, Eq. weight function):          w(r) = (sum_i |phi_i(r)|^2)(sum_j |psi_j(r)|^2)
+ * Each sum runs over all columns of its orbital set in ascending order,
+ * left to right. phi, psi: interleaved complex128, row r at phi + 2*r*ld.
+ */
+int oracle_weights(const double *phi, int64_t ld_phi, int32_t n_phi,
+                   const double *psi, int64_t ld_psi, int32_t n_psi,
+                   int64_t n_r, int32_t kind, double alpha, double *w)
+{
+    if (kind == 1) alpha = 2.0;
+#pragma omp parallel for schedule(static)
+    for (int64_t r = 0; r < n_r; ++r) {
+        const double *a = phi + 2 * r * ld_phi;
+        const double *b = psi + 2 * r * ld_psi;
+        double sa = 0.0, sb = 0.0;
+        for (int32_t i = 0; i < n_phi; ++i) sa = sa + modpow(a[2 * i], a[2 * i + 1], alpha);
+        for (int32_t j = 0; j < n_psi; ++j) sb = sb + modpow(b[2 * j], b[2 * j + 1], alpha);
+        w[r] = (kind == 1) ? sa * sb : sa + sb;
+    }
+    return 0;
+}
+
+/* squared Euclidean distance, Eq. opt (second form): ((dx^2 + dy^2) + dz^2) */
+static inline double dist2(double x, double y, double z, const double *c)
+{
+    double dx = x - c[0], dy = y - c[1], dz = z - c[2];
+    double d = dx * dx;
+    d = d + dy * dy;
+    d = d + dz * dz;
+    return d;
+}
+
+static int bits_of(uint64_t v) { int b = 0; while (v) { ++b; v >>= 1; } return b; }
+
+/*
+ * Weighted Lloyd K-means on the real-space grid, Algorithm 1 with Eq. opt
+ * (second form) and Eq. r_k.
+ *
+ * Grid: x_r = h*(ix, iy, iz), h_k = cell[k]/n_k, r = (ix*ny + iy)*nz + iz.
+ * Start: c_0 = x[init_idx]. For t = 0 .. max_iter-1:
+ *   (i)   a_t(r) = argmin_mu |x_r - c_mu|^2, ties to the lowest mu;
+ *         J_t = sum_r w(r) |x_r - c_{a_t(r)}|^2 (ascending r);
+ *   (ii)  c_{t+1,mu} = sum_{a_t(r)=mu} w x_r / sum_{a_t(r)=mu} w, where each
+ *         product w*x_r is rounded to FP64 and then taken as the integer
+ *         floor(w*x_r * 2^s) in 128 bits; the integer sums are exact, and each
+ *         is rounded to FP64 before one IEEE division. An empty cluster keeps
+ *         its centroid.
+ *   early_stop: stop once a_t equals a_{t-1} (then c_{t+1} = c_t exactly).
+ * Final: a_T from c_T, J_T, and idx_mu = the member of cluster mu nearest to
+ * c_mu (ties to the lowest r); -1 for an empty cluster.
+ *
+ * near_ties counts, over all assignment passes, points whose two smallest
+ * distances d1 <= d2 satisfy d2 - d1 <= 1e-12 * max(d1, hmin^2).
+ * Returns 0, -1 for invalid arguments, or the number of empty clusters
+ * (as a positive count) after writing all outputs.
+ */
+int oracle_kmeans(const double *w, int32_t nx, int32_t ny, int32_t nz, const double *cell,
+                  int32_t n_mu, const int64_t *init_idx, int32_t max_iter, int32_t early_stop,
+                  int64_t *idx_out, double *centroids_out, double *objective,
+                  int32_t *n_iter_out, int64_t *near_ties_out, int32_t *labels_out)
+{
+    const int64_t n_r = (int64_t)nx * ny * nz;
+    if (n_mu <= 0 || n_r <= 0 || max_iter < 0) return -1;
+    const double hx = cell[0] / nx, hy = cell[1] / ny, hz = cell[2] / nz;
+    double hmin = hx < hy ? hx : hy; hmin = hmin < hz ? hmin : hz;
+    const double tie_floor = hmin * hmin;
+
+    /* fixed-point scale: N_r * w_max * max(L, 1) < 2^(126 - s) */
+    double wmax = 0.0;
+    for (int64_t r = 0; r < n_r; ++r) {
+        if (!(w[r] >= 0.0) || isinf(w[r])) return -1;
+        if (w[r] > wmax) wmax = w[r];
+    }
+    double lmax = 1.0;
+    for (int k = 0; k < 3; ++k) if (cell[k] > lmax) lmax = cell[k];
+    int ew = 0, el = 0;
+    if (wmax > 0.0) frexp(wmax, &ew);
+    frexp(lmax, &el);
+    const int s = 126 - (bits_of((uint64_t)n_r) + ew + el);
+    if (s < 0) return -1;
+
+    double *c = (double *)malloc(sizeof(double) * 3 * n_mu);
+    int32_t *lab = (int32_t *)malloc(sizeof(int32_t) * n_r);
+    int32_t *prev = (int32_t *)malloc(sizeof(int32_t) * n_r);
+    double *d1 = (double *)malloc(sizeof(double) * n_r);
+    u128 *S = (u128 *)malloc(sizeof(u128) * 4 * n_mu);
+    for (int32_t m = 0; m < n_mu; ++m) {
+        int64_t r = init_idx[m];
+        if (r < 0 || r >= n_r) { free(c); free(lab); free(prev); free(d1); free(S); return -1; }
+        int64_t ix = r / ((int64_t)ny * nz), iy = (r / nz) % ny, iz = r % nz;
+        c[3 * m + 0] = (double)ix * hx;
+        c[3 * m + 1] = (double)iy * hy;
+        c[3 * m + 2] = (double)iz * hz;
+    }
+
+    int64_t ties = 0;
+    int32_t t = 0;
+    int stopped = 0;
+    for (int pass = 0; pass <= max_iter; ++pass) {
+        /* (i) assignment with the current centroids */
+        int64_t pass_ties = 0;
+#pragma omp parallel for schedule(static) reduction(+ : pass_ties)
+        for (int64_t r = 0; r < n_r; ++r) {
+            int64_t ix = r / ((int64_t)ny * nz), iy = (r / nz) % ny, iz = r % nz;
+            double x = (double)ix * hx, y = (double)iy * hy, z = (double)iz * hz;
+            double best = INFINITY, second = INFINITY;
+            int32_t arg = 0;
+            for (int32_t m = 0; m < n_mu; ++m) {
+                double d = dist2(x, y, z, c + 3 * m);
+                if (d < best) { second = best; best = d; arg = m; }
+                else if (d < second) second = d;
+            }
+            lab[r] = arg;
+            d1[r] = best;
+            double fl = best > tie_floor ? best : tie_floor;
+            if (n_mu > 1 && second - best <= 1e-12 * fl) pass_ties += 1;
+        }
+        ties += pass_ties;
+        double J = 0.0;
+        for (int64_t r = 0; r < n_r; ++r) J = J + w[r] * d1[r];
+        if (objective) objective[pass] = J;
+        if (pass == max_iter) break;
+        if (early_stop && pass > 0 && memcmp(lab, prev, sizeof(int32_t) * n_r) == 0) {
+            for (int p = pass + 1; p <= max_iter; ++p) if (objective) objective[p] = J;
+            stopped = 1;
+            break;
+        }
+        memcpy(prev, lab, sizeof(int32_t) * n_r);
+
+        /* (ii) weighted centroid update, Eq. r_k, with exact integer sums */
+        memset(S, 0, sizeof(u128) * 4 * n_mu);
+        for (int64_t r = 0; r < n_r; ++r) {
+            int64_t ix = r / ((int64_t)ny * nz), iy = (r / nz) % ny, iz = r % nz;
+            double x = (double)ix * hx, y = (double)iy * hy, z = (double)iz * hz;
+            u128 *q = S + 4 * (int64_t)lab[r];
+            q[0] += (u128)ldexp(w[r], s);
+            q[1] += (u128)ldexp(w[r] * x, s);
+            q[2] += (u128)ldexp(w[r] * y, s);
+            q[3] += (u128)ldexp(w[r] * z, s);
+        }
+        for (int32_t m = 0; m < n_mu; ++m) {
+            u128 *q = S + 4 * (int64_t)m;
+            if (q[0] == 0) continue;
+            double sw = (double)q[0];
+            c[3 * m + 0] = (double)q[1] / sw;
+            c[3 * m + 1] = (double)q[2] / sw;
+            c[3 * m + 2] = (double)q[3] / sw;
+        }
+        t += 1;
+    }
+    (void)stopped;
+
+    /* snap: nearest member of each cluster, ties to the lowest r */
+    int empty = 0;
+    for (int32_t m = 0; m < n_mu; ++m) idx_out[m] = -1;
+    double *best = (double *)malloc(sizeof(double) * n_mu);
+    for (int32_t m = 0; m < n_mu; ++m) best[m] = INFINITY;
+    for (int64_t r = 0; r < n_r; ++r) {
+        int32_t m = lab[r];
+        if (d1[r] < best[m]) { best[m] = d1[r]; idx_out[m] = r; }
+    }
+    for (int32_t m = 0; m < n_mu; ++m) if (idx_out[m] < 0) ++empty;
+    if (centroids_out) memcpy(centroids_out, c, sizeof(double) * 3 * n_mu);
+    if (labels_out) memcpy(labels_out, lab, sizeof(int32_t) * n_r);
+    if (n_iter_out) *n_iter_out = t;
+    if (near_ties_out) *near_ties_out = ties;
+    free(best); free(c); free(lab); free(prev); free(d1); free(S);
+    return empty;
+}
+
+/* the fixed-point exponent s used above, exposed for tests */
+int oracle_fixed_point_scale(int64_t n_r, double wmax, const double *cell)
+{
+    double lmax = 1.0;
+    for (int k = 0; k < 3; ++k) if (cell[k] > lmax) lmax = cell[k];
+    int ew = 0, el = 0;
+    if (wmax > 0.0) frexp(wmax, &ew);
+    frexp(lmax, &el);
+    return 126 - (bits_of((uint64_t)n_r) + ew + el);
+}

@@ -1,0 +1,228 @@
+"""Oracle functions. TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+The weight function and the K-means live in isdf_oracle.c (plain C, FP64,
+no FMA contraction); everything from the gathered rows on is numpy/scipy in
+complex128. Each function names the part of the paper it restates.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import scipy.linalg as sla
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "isdf_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C half of the oracle (gcc, OpenMP, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+                               "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        lib.oracle_weights.argtypes = [P, ctypes.c_int64, ctypes.c_int32, P, ctypes.c_int64, ctypes.c_int32,
+                                       ctypes.c_int64, ctypes.c_int32, ctypes.c_double, P]
+        lib.oracle_kmeans.argtypes = [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, ctypes.c_int32, P,
+                                      ctypes.c_int32, ctypes.c_int32, P, P, P, P, P, P]
+        lib.oracle_fixed_point_scale.argtypes = [ctypes.c_int64, ctypes.c_double, P]
+        _lib = lib
+    return _lib
+
+
+def _c128(x) -> np.ndarray:
+    x = np.asarray(x)
+    if x.dtype != np.complex128:
+        x = x.astype(np.complex128)  # exact for complex64
+    return np.ascontiguousarray(x)
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+# --------------------------------------------------------------------------
+# Weight function, Sec. 2.2, Eq. weight function 2 (SSM and its alpha family)
+# and Eq. weight function (PSM).
+# --------------------------------------------------------------------------
+def weights(phi, psi, kind: str = "ssm", alpha: float = 2.0) -> np.ndarray:
+    phi, psi = _c128(phi), _c128(psi)
+    n_r = phi.shape[0]
+    assert psi.shape[0] == n_r
+    w = np.empty(n_r, dtype=np.float64)
+    load().oracle_weights(_ptr(phi), phi.shape[1], phi.shape[1], _ptr(psi), psi.shape[1], psi.shape[1],
+                          n_r, 1 if kind == "psm" else 0, float(alpha), _ptr(w))
+    return w
+
+
+def fixed_point_scale(n_r: int, wmax: float, cell) -> int:
+    cell = np.ascontiguousarray(cell, dtype=np.float64)
+    return int(load().oracle_fixed_point_scale(n_r, float(wmax), _ptr(cell)))
+
+
+# --------------------------------------------------------------------------
+# Weighted K-means, Algorithm 1 with Eq. opt (second form) and Eq. r_k.
+# --------------------------------------------------------------------------
+def kmeans(w, shape, cell, n_mu: int, init_idx, max_iter: int, early_stop: bool = False) -> dict:
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    nx, ny, nz = (int(v) for v in shape)
+    cell = np.ascontiguousarray(cell, dtype=np.float64)
+    init = np.ascontiguousarray(init_idx, dtype=np.int64)
+    assert init.shape == (n_mu,) and w.shape == (nx * ny * nz,)
+    idx = np.empty(n_mu, np.int64)
+    cen = np.empty((n_mu, 3), np.float64)
+    obj = np.empty(max_iter + 1, np.float64)
+    nit = np.zeros(1, np.int32)
+    ties = np.zeros(1, np.int64)
+    lab = np.empty(nx * ny * nz, np.int32)
+    rc = load().oracle_kmeans(_ptr(w), nx, ny, nz, _ptr(cell), n_mu, _ptr(init), max_iter, int(early_stop),
+                              _ptr(idx), _ptr(cen), _ptr(obj), _ptr(nit), _ptr(ties), _ptr(lab))
+    if rc < 0:
+        raise ValueError("oracle_kmeans: invalid arguments")
+    return {"idx": idx, "centroids": cen, "objective": obj, "n_iter": int(nit[0]),
+            "near_ties": int(ties[0]), "labels": lab, "empty": int(rc)}
+
+
+def grid_coords(shape, cell) -> np.ndarray:
+    """x_r = h*(ix, iy, iz) for every grid point, in FP64 (N_r x 3)."""
+    nx, ny, nz = shape
+    h = [cell[0] / nx, cell[1] / ny, cell[2] / nz]
+    ix, iy, iz = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    return np.stack([ix.ravel() * h[0], iy.ravel() * h[1], iz.ravel() * h[2]], axis=1)
+
+
+# --------------------------------------------------------------------------
+# Interpolation vectors, Sec. 2.1: Theta = Z C^H (C C^H)^-1 (Eq. theta, read
+# with the Hermitian adjoint for complex orbitals) built through the separable
+# structure Z C^H = (Phi Phi_mu^H) o conj(Psi Psi_mu^H) (Eqs. phipsi,
+# muRownuCol, muRownuColden), with C C^H = M formed the same way from the
+# selected rows (Eq. Cmu: C's rows are Z at the interpolation points).
+# --------------------------------------------------------------------------
+def gather(phi, psi, idx):
+    """Phi_mu = Phi[idx, :], Psi_mu = Psi[idx, :] (Eq. Cmu)."""
+    idx = np.asarray(idx, dtype=np.int64)
+    return _c128(np.asarray(phi)[idx]), _c128(np.asarray(psi)[idx])
+
+
+def gram_hadamard(phi_rows, psi_rows, phi_mu, psi_mu) -> np.ndarray:
+    """Y = (Phi Phi_mu^H) o conj(Psi Psi_mu^H) for the given rows (Eq. muRownuCol)."""
+    A = _c128(phi_rows) @ phi_mu.conj().T
+    B = _c128(psi_rows) @ psi_mu.conj().T
+    return A * B.conj()
+
+
+def form_M(phi_mu, psi_mu) -> np.ndarray:
+    """M = C C^H = (Phi_mu Phi_mu^H) o conj(Psi_mu Psi_mu^H)."""
+    return gram_hadamard(phi_mu, psi_mu, phi_mu, psi_mu)
+
+
+def cholesky(M) -> np.ndarray:
+    """Lower Cholesky factor L, M = L L^H (the linear solver of Sec. 2.4)."""
+    return sla.cholesky(M, lower=True, check_finite=True)
+
+
+def theta_rows(phi, psi, phi_mu, psi_mu, L, rows) -> np.ndarray:
+    """Theta rows for a set of grid rows: Theta^H = L^-H (L^-1 Y^H)."""
+    rows = np.asarray(rows, dtype=np.int64)
+    Y = gram_hadamard(np.asarray(phi)[rows], np.asarray(psi)[rows], phi_mu, psi_mu)
+    X = sla.solve_triangular(L, Y.conj().T, lower=True)
+    T = sla.solve_triangular(L.conj().T, X, lower=False)
+    return T.conj().T
+
+
+def fit_theta(phi, psi, idx, block: int = 65536) -> dict:
+    """Full Theta (N_r x N_mu, complex128), computed in row blocks."""
+    phi_mu, psi_mu = gather(phi, psi, idx)
+    M = form_M(phi_mu, psi_mu)
+    L = cholesky(M)
+    n_r = np.asarray(phi).shape[0]
+    theta = np.empty((n_r, len(idx)), np.complex128)
+    for b in range(0, n_r, block):
+        rows = np.arange(b, min(n_r, b + block))
+        theta[rows] = theta_rows(phi, psi, phi_mu, psi_mu, L, rows)
+    return {"theta": theta, "M": M, "L": L, "phi_mu": phi_mu, "psi_mu": psi_mu}
+
+
+# --------------------------------------------------------------------------
+# Exchange-like surrogate loss and the adjoint of the Theta fit at fixed
+# interpolation points (derived from Eq. theta and Eq. muRownuCol):
+#   L = dV sum_r sum_{mu,nu} Re[conj(Theta_r,mu) K_mu,nu Theta_r,nu]
+#   grad convention: G = dL/dRe X + i dL/dIm X, so dL = Re tr(G^H dX).
+# --------------------------------------------------------------------------
+def surrogate_loss(theta, K, dV: float) -> float:
+    theta = _c128(theta)
+    return float(dV * np.real(np.sum(theta.conj() * (theta @ np.asarray(K).T))))
+
+
+def surrogate_grad_theta(theta, K, dV: float) -> np.ndarray:
+    """dL/dTheta = 2 dV Theta conj(K) for Hermitian K."""
+    return 2.0 * dV * (_c128(theta) @ np.asarray(K).conj())
+
+
+def theta_backward(phi, psi, idx, grad_theta_fn, block: int = 65536) -> dict:
+    """Gradients of a real loss of Theta(Phi, Psi) at fixed idx.
+
+    grad_theta_fn(rows, theta_rows) -> dL/dTheta on those rows. Steps:
+      Ybar = Thetabar M^-1, Mbar = -Theta^H Ybar,
+      Abar = Ybar o B, Bbar = conj(Ybar) o A,
+      Phibar = Abar Phi_mu, Phibar_mu += Abar^H Phi   (Psi likewise with Bbar),
+      Abar_mu = Mbar o B_mu, Bbar_mu = conj(Mbar) o A_mu,
+      Phibar_mu += (Abar_mu + Abar_mu^H) Phi_mu, scattered into Phibar[idx].
+    """
+    phi, psi = _c128(phi), _c128(psi)
+    idx = np.asarray(idx, dtype=np.int64)
+    phi_mu, psi_mu = gather(phi, psi, idx)
+    A_mu = phi_mu @ phi_mu.conj().T
+    B_mu = psi_mu @ psi_mu.conj().T
+    M = A_mu * B_mu.conj()
+    L = cholesky(M)
+    n_r, n_mu = phi.shape[0], len(idx)
+    gphi = np.zeros_like(phi)
+    gpsi = np.zeros_like(psi)
+    gphi_mu = np.zeros_like(phi_mu)
+    gpsi_mu = np.zeros_like(psi_mu)
+    Mbar = np.zeros((n_mu, n_mu), np.complex128)
+    loss = 0.0
+    for b in range(0, n_r, block):
+        rows = np.arange(b, min(n_r, b + block))
+        A = phi[rows] @ phi_mu.conj().T
+        B = psi[rows] @ psi_mu.conj().T
+        Y = A * B.conj()
+        T = sla.solve_triangular(L.conj().T, sla.solve_triangular(L, Y.conj().T, lower=True), lower=False).conj().T
+        G = grad_theta_fn(rows, T)
+        # Ybar = G M^-1 (M Hermitian): Ybar^H = M^-1 G^H
+        Yb = sla.solve_triangular(L.conj().T, sla.solve_triangular(L, G.conj().T, lower=True), lower=False).conj().T
+        Mbar -= T.conj().T @ Yb
+        Ab = Yb * B
+        Bb = Yb.conj() * A
+        gphi[rows] += Ab @ phi_mu
+        gpsi[rows] += Bb @ psi_mu
+        gphi_mu += Ab.conj().T @ phi[rows]
+        gpsi_mu += Bb.conj().T @ psi[rows]
+    Ab_mu = Mbar * B_mu
+    Bb_mu = Mbar.conj() * A_mu
+    gphi_mu += (Ab_mu + Ab_mu.conj().T) @ phi_mu
+    gpsi_mu += (Bb_mu + Bb_mu.conj().T) @ psi_mu
+    np.add.at(gphi, idx, gphi_mu)
+    np.add.at(gpsi, idx, gpsi_mu)
+    return {"grad_phi": gphi, "grad_psi": gpsi, "Mbar": Mbar, "L": L}
+
+
+def explicit_Z(phi, psi) -> np.ndarray:
+    """Z(r) = [phi_i(r) conj(psi_j(r))]_{i,j}, N_r x (N_phi N_psi), column i*N_psi + j
+    (the transposed Khatri-Rao product, Sec. 1). Small inputs only."""
+    phi, psi = _c128(phi), _c128(psi)
+    return (phi[:, :, None] * psi.conj()[:, None, :]).reshape(phi.shape[0], -1)
