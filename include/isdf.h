@@ -1,0 +1,210 @@
+/*
+ * isdf.h - C ABI of the GB300 (sm_103a) complex-valued K-means ISDF library.
+ *
+ * The library computes the interpolative separable density fitting (ISDF)
+ * decomposition of the transposed Khatri-Rao product
+ *     Z(r)_{ij} = phi_i(r) conj(psi_j(r)),   Z ~= Theta C,        (Sec. 2.1, Eqs. decomposition, decomMatrix)
+ * in three steps:
+ *   1. the K-means weight w(r) from the orbitals            (Sec. 2.2, Eqs. weight function, weight function 2)
+ *   2. weighted Lloyd K-means on the real-space grid, which  (Sec. 2.2, Eq. opt (second form), Eq. r_k, Algorithm 1)
+ *      selects N_mu interpolation points idx
+ *   3. the interpolation vectors Theta = Y M^-1 with        (Sec. 2.1, Eq. theta, Eqs. phipsi, muRownuCol,
+ *      Y = Z C^H = (Phi Phi_mu^H) o conj(Psi Psi_mu^H) and    muRownuColden; Sec. 2.4 for M as rows of Z C^H)
+ *      M = C C^H = (Phi_mu Phi_mu^H) o conj(Psi_mu Psi_mu^H)
+ * plus the adjoint of step 3 at fixed idx.
+ *
+ * Conventions shared by every entry point:
+ *  - Orbitals Phi (N_r x N_phi) and Psi (N_r x N_psi) are row-major
+ *    interleaved complex (re, im) with a leading dimension ld >= N counted in
+ *    complex elements; row r of Phi starts at phi + r*ld.
+ *  - The real-space grid is nx*ny*nz points, linear index
+ *    r = (ix*ny + iy)*nz + iz, coordinates x_r = (ix*Lx/nx, iy*Ly/ny, iz*Lz/nz).
+ *  - Every pointer argument is a DEVICE pointer owned by the caller unless
+ *    its comment says "host". The library never frees caller memory.
+ *  - Every call is asynchronous and stream-ordered on `stream` (a
+ *    cudaStream_t; NULL is the legacy default stream). Results are valid once
+ *    the stream has reached them.
+ *  - Every call returns an isdf_status; arguments are validated on the host
+ *    before anything is launched, so an argument error launches nothing.
+ *    Failures found on the device (a non-positive Cholesky pivot, a
+ *    non-finite input) are recorded in a device status word and read with
+ *    isdf_plan_status (which synchronises the stream).
+ */
+#ifndef ISDF_H
+#define ISDF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define ISDF_API __attribute__((visibility("default")))
+#else
+#define ISDF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ISDF_OK = 0,
+    ISDF_ERR_INVALID_ARG = 1,   /* bad size, pointer, enum or alignment; nothing was launched */
+    ISDF_ERR_CUDA = 2,          /* a CUDA runtime call failed (launch, allocation, copy) */
+    ISDF_ERR_NOT_HPD = 3,       /* M = C C^H is not Hermitian positive definite; detail = failing pivot */
+    ISDF_ERR_EMPTY_CLUSTER = 4, /* K-means left a cluster without weight; its idx is -1 */
+    ISDF_ERR_NONFINITE = 5,     /* a NaN or infinity was found on the device */
+    ISDF_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up */
+    ISDF_ERR_WORKSPACE = 7,     /* workspace missing or smaller than the queried size */
+    ISDF_ERR_UNSUPPORTED = 8    /* valid request outside this build's limits (e.g. sizes) */
+} isdf_status;
+
+typedef enum { ISDF_C128 = 0, ISDF_C64 = 1 } isdf_dtype;   /* interleaved complex double / float */
+typedef enum { ISDF_W_SSM = 0, ISDF_W_PSM = 1 } isdf_wkind;
+
+/* Precision of the Theta fit.
+ *  ISDF_FP64:  every step in FP64 on the FP64 pipe; Theta is complex128.
+ *  ISDF_MIXED: the two Gram GEMMs (with the Hadamard conjugate product fused)
+ *              and the application of M^-1 run on the tcgen05 tensor cores as
+ *              three FP16 products of a power-of-two-scaled hi+lo split with
+ *              FP32 accumulation; M, its Cholesky factor and M^-1 stay FP64.
+ *              Theta is complex64. */
+typedef enum { ISDF_FP64 = 0, ISDF_MIXED = 1 } isdf_mode;
+
+/* isdf_kmeans flags */
+#define ISDF_KMEANS_EARLY_STOP 1   /* stop once the labels repeat (identical result, fewer passes) */
+
+/* ---------------------------------------------------------------------------
+ * Step 1: weight function (Sec. 2.2).
+ *   kind ISDF_W_SSM (Eq. weight function 2): w(r) = sum_i |phi_i(r)|^alpha + sum_j |psi_j(r)|^alpha
+ *       alpha = 2 is SSM (the paper's choice); 1, 3, 4 are SM, SCM, SQM.
+ *   kind ISDF_W_PSM (Eq. weight function):   w(r) = (sum_i |phi_i(r)|^2)(sum_j |psi_j(r)|^2)
+ *       (alpha is ignored).
+ * Each sum runs over the columns in ascending order with IEEE FP64 operations,
+ * |z|^2 = re*re + im*im; alpha = 1, 3, 4 use sqrt and products, other alpha pow.
+ * phi, psi: dtype (ISDF_C128 or ISDF_C64) arrays of n_r rows; ld >= n.
+ * w: n_r doubles (output). Requires n_r >= 0, n_phi, n_psi >= 1, alpha > 0,
+ * 16-byte aligned phi, psi and 8-byte aligned w.
+ * ------------------------------------------------------------------------- */
+ISDF_API isdf_status isdf_weights(const void *phi, int64_t ld_phi, int32_t n_phi,
+                         const void *psi, int64_t ld_psi, int32_t n_psi,
+                         int64_t n_r, int32_t dtype, int32_t kind, double alpha,
+                         double *w, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Step 2: weighted Lloyd K-means on the grid (Sec. 2.2, Eq. opt second form,
+ * Eq. r_k, Algorithm 1).
+ *   c_0 = x[init_idx]; for t < max_iter: a_t(r) = argmin_mu |x_r - c_mu|^2
+ *   (FP64 distance ((dx*dx + dy*dy) + dz*dz), ties to the lowest mu), then
+ *   c_{t+1,mu} = sum w x / sum w over a_t = mu. The sums are exact: each FP64
+ *   product w*x enters as the 128-bit integer floor(w*x*2^s) with
+ *   s = 126 - (bits(N_r) + e(max w) + e(max(Lx,Ly,Lz,1))) (e() the frexp
+ *   exponent), and each integer sum is rounded to FP64 before one IEEE
+ *   division; an empty (zero-weight) cluster keeps its centroid. Finally
+ *   idx_mu = the member of cluster mu nearest to c_mu (ties to the lowest r)
+ *   under the last assignment, or -1 for an empty cluster.
+ *   The result is bit-identical to a plain FP64 brute-force evaluation of
+ *   these formulas; the device prunes centroids per tile with exact distance
+ *   bounds and screens in FP32 with a rigorous error bound before deciding in
+ *   FP64.
+ * w:          n_r = nx*ny*nz weights (>= 0, finite).
+ * cell:       HOST array of 3 doubles (Lx, Ly, Lz), each > 0.
+ * init_idx:   n_mu grid indices (int64, in [0, n_r)).
+ * max_iter:   number of Lloyd updates T >= 0.
+ * flags:      0 or ISDF_KMEANS_EARLY_STOP.
+ * idx:        out, n_mu int64.
+ * centroids:  out, n_mu x 3 doubles (final centroids), or NULL.
+ * objective:  out, max_iter + 1 doubles J_t = sum_r w(r)|x_r - c_{a_t(r)}|^2, or NULL.
+ * labels:     out, n_r int32 final assignment, or NULL.
+ * stats:      out, 4 int64: {Lloyd updates done, near ties, empty clusters,
+ *             points decided in FP64 after the FP32 screen}, or NULL. A near
+ *             tie is a point whose two smallest distances d1 <= d2 satisfy
+ *             d2 - d1 <= 1e-12 max(d1, hmin^2); they are counted over every
+ *             assignment pass and are resolved exactly by the lowest-mu rule.
+ * ws, ws_bytes: device workspace of at least isdf_kmeans_workspace() bytes,
+ *             256-byte aligned. Its contents need no initialisation.
+ * Limits: 1 <= n_mu <= min(n_r, 8192), n_r < 2^31. Weights with
+ * n_r * max(w) * max(L, 1) >= 2^126 are rejected on the device
+ * (ISDF_ERR_NONFINITE recorded in stats[2] = -1).
+ * ------------------------------------------------------------------------- */
+ISDF_API isdf_status isdf_kmeans_workspace(int32_t nx, int32_t ny, int32_t nz, int32_t n_mu, size_t *ws_bytes);
+ISDF_API isdf_status isdf_kmeans(const double *w, int32_t nx, int32_t ny, int32_t nz, const double *cell,
+                        int32_t n_mu, const int64_t *init_idx, int32_t max_iter, int32_t flags,
+                        int64_t *idx, double *centroids, double *objective, int32_t *labels,
+                        int64_t *stats, void *ws, size_t ws_bytes, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Step 3: the interpolation-vector fit (Sec. 2.1, Eq. theta with the
+ * Hermitian adjoint for complex orbitals; Eqs. muRownuCol, muRownuColden).
+ *
+ * isdf_plan_create gathers Phi_mu = Phi[idx], Psi_mu = Psi[idx] (Eq. Cmu),
+ * forms M = (Phi_mu Phi_mu^H) o conj(Psi_mu Psi_mu^H) in FP64, factors
+ * M = L L^H (blocked Cholesky, FP64) and forms M^-1 = L^-H L^-1 in FP64.
+ * The plan keeps phi/psi pointers: the orbitals must stay alive and unchanged
+ * while the plan is used. idx must hold n_mu distinct indices in [0, n_r)
+ * (duplicates make M singular: ISDF_ERR_NOT_HPD). max_rows bounds the rows
+ * of one internal block (the plan holds two blocks of max_rows x n_mu
+ * complex128 scratch); larger requests are processed in several blocks.
+ * The plan allocates its own device memory (cudaMalloc) and frees it in
+ * isdf_plan_destroy.
+ * Limits: 1 <= n_mu <= 8192; n_phi, n_psi <= 4096; in ISDF_MIXED mode
+ * n_mu % 64 == 0 and n_phi, n_psi % 32 == 0.
+ * ------------------------------------------------------------------------- */
+typedef struct isdf_plan isdf_plan;
+
+ISDF_API isdf_status isdf_plan_create(isdf_plan **plan, const void *phi, int64_t ld_phi, const void *psi, int64_t ld_psi,
+                             int64_t n_r, int32_t n_phi, int32_t n_psi, int32_t dtype,
+                             const int64_t *idx, int32_t n_mu, int32_t mode, int64_t max_rows, void *stream);
+
+/* Theta rows [row_begin, row_begin + row_count): Theta_b = Y_b M^-1 with
+ * Y_b = (Phi_b Phi_mu^H) o conj(Psi_b Psi_mu^H).
+ * theta: row_count x n_mu, row-major with leading dimension ld_theta >= n_mu,
+ * complex128 in ISDF_FP64 mode and complex64 in ISDF_MIXED mode. */
+ISDF_API isdf_status isdf_fit_theta(isdf_plan *plan, int64_t row_begin, int64_t row_count,
+                           void *theta, int64_t ld_theta, void *stream);
+
+/* Adjoint of Theta(Phi, Psi) at fixed idx, for one block of rows.
+ * Given dL/dTheta = G (convention G = dL/dRe Theta + i dL/dIm Theta) on the
+ * rows of the block, or, when grad_theta is NULL, the exchange-like surrogate
+ *   L = dV sum_r sum_{mu,nu} Re[conj(Theta_{r,mu}) K_{mu,nu} Theta_{r,nu}]
+ * whose G = 2 dV Theta conj(K) is formed in the kernel (K: n_mu x n_mu
+ * complex128 Hermitian, row-major), this call
+ *   - recomputes Theta_b (never stored),
+ *   - adds Abar_b Phi_mu into grad_phi rows and Bbar_b Psi_mu into grad_psi
+ *     rows of the block, with Ybar = G M^-1, Abar = Ybar o B, Bbar = conj(Ybar) o A,
+ *   - accumulates Mbar -= Theta_b^H Ybar, Phibar_mu += Abar^H Phi_b and
+ *     Psibar_mu += Bbar^H Psi_b inside the plan,
+ *   - adds the block's surrogate loss to *loss (device double) if loss != NULL.
+ * grad_theta: row_count x n_mu (ld_grad), complex128 (FP64) / complex64 (MIXED).
+ * grad_phi, grad_psi: n_r x n complex128 (ld_gphi, ld_gpsi), accumulated (+=).
+ * Call isdf_fit_theta_backward_finalize once after all blocks: it adds the
+ * M-dependent terms (Mbar o B_mu and conj(Mbar) o A_mu, through
+ * (Abar_mu + Abar_mu^H) Phi_mu) and scatter-adds Phibar_mu, Psibar_mu into the
+ * idx rows of grad_phi, grad_psi, then clears the plan's accumulators. */
+ISDF_API isdf_status isdf_fit_theta_backward(isdf_plan *plan, int64_t row_begin, int64_t row_count,
+                                    const void *grad_theta, int64_t ld_grad, const void *K, double dV,
+                                    void *grad_phi, int64_t ld_gphi, void *grad_psi, int64_t ld_gpsi,
+                                    double *loss, void *stream);
+ISDF_API isdf_status isdf_fit_theta_backward_finalize(isdf_plan *plan, void *grad_phi, int64_t ld_gphi,
+                                             void *grad_psi, int64_t ld_gpsi, void *stream);
+
+/* Synchronises the plan's last stream and returns the first device-side
+ * failure (ISDF_OK, ISDF_ERR_NOT_HPD with *detail = failing pivot index,
+ * ISDF_ERR_NONFINITE, ISDF_ERR_TIMEOUT). detail may be NULL. */
+ISDF_API isdf_status isdf_plan_status(isdf_plan *plan, int32_t *detail);
+
+/* Copies a plan-owned matrix into the caller's device buffer dst
+ * (stream-ordered): which = 0 M, 1 L, 2 M^-1 (each n_mu x n_mu complex128,
+ * row-major; L's strict upper triangle is zero), 3 Phi_mu, 4 Psi_mu
+ * (n_mu x n complex128). */
+ISDF_API isdf_status isdf_plan_copy_matrix(const isdf_plan *plan, int32_t which, void *dst, void *stream);
+
+ISDF_API void isdf_plan_destroy(isdf_plan *plan);
+
+/* Human-readable name of a status code (static storage). */
+ISDF_API const char *isdf_status_string(isdf_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ISDF_H */

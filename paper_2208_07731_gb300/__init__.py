@@ -1,1 +1,279 @@
-"""GB300-native complex-valued K-means ISDF (arXiv 2208.07731)."""
+"""GB300-native complex-valued K-means ISDF (arXiv 2208.07731).
+
+Thin Python binding over the C ABI of libisdf.so (include/isdf.h). Every
+function below only marshals torch CUDA tensors into pointers, sizes and the
+current stream; every step of the method runs in the library's CUDA kernels.
+There is no CPU fallback: a missing or unloadable library raises.
+
+    import paper_2208_07731_gb300 as isdf
+    w = isdf.weights(phi, psi)                                   # Sec. 2.2, Eq. weight function 2
+    km = isdf.kmeans(w, (n, n, n), (L, L, L), n_mu, init, iters)  # Algorithm 1
+    plan = isdf.Plan(phi, psi, km["idx"], mode="fp64")            # Eq. theta
+    theta = plan.fit_theta()
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libisdf.so")
+_lib = None
+
+C128, C64 = 0, 1
+SSM, PSM = 0, 1
+FP64, MIXED = 0, 1
+EARLY_STOP = 1
+STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA runtime error", 3: "C C^H is not Hermitian positive definite",
+          4: "empty K-means cluster", 5: "non-finite value", 6: "bounded device wait timed out",
+          7: "workspace missing or too small", 8: "unsupported size"}
+
+
+class ISDFError(RuntimeError):
+    def __init__(self, code: int, what: str, detail: int | None = None):
+        self.code = code
+        self.detail = detail
+        msg = f"{what}: {STATUS.get(code, code)}"
+        if detail is not None:
+            msg += f" (detail {detail})"
+        super().__init__(msg)
+
+
+def lib():
+    """Load libisdf.so (built by paper_2208_07731_gb300.build). Raises if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(f"libisdf.so is not built ({_LIB_PATH}); run paper_2208_07731_gb300.build.build()")
+        L = ctypes.CDLL(_LIB_PATH)
+        P, I32, I64, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        L.isdf_weights.argtypes = [P, I64, I32, P, I64, I32, I64, I32, I32, D, P, P]
+        L.isdf_kmeans_workspace.argtypes = [I32, I32, I32, I32, P]
+        L.isdf_kmeans.argtypes = [P, I32, I32, I32, P, I32, P, I32, I32, P, P, P, P, P, P, ctypes.c_size_t, P]
+        L.isdf_plan_create.argtypes = [P, P, I64, P, I64, I64, I32, I32, I32, P, I32, I32, I64, P]
+        L.isdf_fit_theta.argtypes = [P, I64, I64, P, I64, P]
+        L.isdf_fit_theta_backward.argtypes = [P, I64, I64, P, I64, P, D, P, I64, P, I64, P, P]
+        L.isdf_fit_theta_backward_finalize.argtypes = [P, P, I64, P, I64, P]
+        L.isdf_plan_status.argtypes = [P, P]
+        L.isdf_plan_copy_matrix.argtypes = [P, I32, P, P]
+        L.isdf_plan_destroy.argtypes = [P]
+        L.isdf_status_string.argtypes = [I32]
+        L.isdf_status_string.restype = ctypes.c_char_p
+        for f in ("isdf_weights", "isdf_kmeans_workspace", "isdf_kmeans", "isdf_plan_create", "isdf_fit_theta",
+                  "isdf_fit_theta_backward", "isdf_fit_theta_backward_finalize", "isdf_plan_status",
+                  "isdf_plan_copy_matrix"):
+            getattr(L, f).restype = ctypes.c_int32
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise ISDFError(rc, what)
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _orbitals(x: torch.Tensor):
+    """(pointer tensor, ld, n, dtype code) of an N_r x N complex CUDA matrix with unit column stride."""
+    if not x.is_cuda or x.dim() != 2 or x.stride(1) != 1:
+        raise ValueError("orbitals must be 2-D CUDA tensors with contiguous rows")
+    if x.dtype == torch.complex128:
+        code = C128
+    elif x.dtype == torch.complex64:
+        code = C64
+    else:
+        raise TypeError("orbitals must be complex128 or complex64")
+    return x, x.stride(0), x.shape[1], code
+
+
+def weights(phi: torch.Tensor, psi: torch.Tensor, kind: str = "ssm", alpha: float = 2.0, out=None, stream=None):
+    """w(r) = sum_i |phi_i|^alpha + sum_j |psi_j|^alpha (kind "ssm") or the PSM product (kind "psm")."""
+    a, lda, na, ca = _orbitals(phi)
+    b, ldb, nb, cb = _orbitals(psi)
+    if ca != cb or a.shape[0] != b.shape[0]:
+        raise ValueError("phi and psi must share dtype and row count")
+    n_r = a.shape[0]
+    w = out if out is not None else torch.empty(n_r, dtype=torch.float64, device=a.device)
+    _check(lib().isdf_weights(_ptr(a), lda, na, _ptr(b), ldb, nb, n_r, ca, PSM if kind == "psm" else SSM,
+                              float(alpha), _ptr(w), _stream(stream)), "isdf_weights")
+    return w
+
+
+def kmeans_workspace_bytes(shape, n_mu: int) -> int:
+    n = ctypes.c_size_t(0)
+    _check(lib().isdf_kmeans_workspace(int(shape[0]), int(shape[1]), int(shape[2]), int(n_mu), ctypes.byref(n)),
+           "isdf_kmeans_workspace")
+    return int(n.value)
+
+
+def kmeans(w: torch.Tensor, shape, cell, n_mu: int, init_idx: torch.Tensor, max_iter: int,
+           early_stop: bool = False, workspace: torch.Tensor | None = None, labels: bool = True,
+           objective: bool = True, stream=None) -> dict:
+    """Weighted Lloyd K-means on the grid; returns device tensors idx, centroids,
+    objective, labels and stats = (updates, near ties, empty clusters, FP64-decided points)."""
+    nx, ny, nz = (int(v) for v in shape)
+    dev = w.device
+    if w.dtype != torch.float64 or not w.is_cuda or not w.is_contiguous() or w.numel() != nx * ny * nz:
+        raise ValueError("w must be a contiguous float64 CUDA tensor of nx*ny*nz entries")
+    init = init_idx.to(device=dev, dtype=torch.int64).contiguous()
+    if init.numel() != n_mu:
+        raise ValueError("init_idx must hold n_mu indices")
+    nbytes = kmeans_workspace_bytes(shape, n_mu)
+    ws = workspace if workspace is not None else torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    if ws.numel() < nbytes:
+        raise ValueError("workspace too small")
+    idx = torch.empty(n_mu, dtype=torch.int64, device=dev)
+    cen = torch.empty((n_mu, 3), dtype=torch.float64, device=dev)
+    obj = torch.empty(max_iter + 1, dtype=torch.float64, device=dev) if objective else None
+    lab = torch.empty(nx * ny * nz, dtype=torch.int32, device=dev) if labels else None
+    stats = torch.zeros(4, dtype=torch.int64, device=dev)
+    cellh = (ctypes.c_double * 3)(*[float(c) for c in cell])
+    _check(lib().isdf_kmeans(_ptr(w), nx, ny, nz, cellh, int(n_mu), _ptr(init), int(max_iter),
+                             EARLY_STOP if early_stop else 0, _ptr(idx), _ptr(cen), _ptr(obj), _ptr(lab),
+                             _ptr(stats), _ptr(ws), ws.numel(), _stream(stream)), "isdf_kmeans")
+    return {"idx": idx, "centroids": cen, "objective": obj, "labels": lab, "stats": stats}
+
+
+class Plan:
+    """Theta fit at fixed interpolation points (isdf_plan_*): gathers Phi_mu,
+    Psi_mu, forms M = C C^H in FP64, factors it and forms M^-1 on creation."""
+
+    def __init__(self, phi: torch.Tensor, psi: torch.Tensor, idx: torch.Tensor, mode: str = "fp64",
+                 max_rows: int = 65536, stream=None):
+        a, lda, na, ca = _orbitals(phi)
+        b, ldb, nb, cb = _orbitals(psi)
+        if ca != cb or a.shape[0] != b.shape[0]:
+            raise ValueError("phi and psi must share dtype and row count")
+        self.phi, self.psi = a, b
+        self.idx = idx.to(device=a.device, dtype=torch.int64).contiguous()
+        self.n_r, self.n_phi, self.n_psi, self.n_mu = a.shape[0], na, nb, self.idx.numel()
+        self.mode = MIXED if mode == "mixed" else FP64
+        self.theta_dtype = torch.complex64 if self.mode == MIXED else torch.complex128
+        self._h = ctypes.c_void_p(0)
+        _check(lib().isdf_plan_create(ctypes.byref(self._h), _ptr(a), lda, _ptr(b), ldb, self.n_r, na, nb, ca,
+                                      _ptr(self.idx), self.n_mu, self.mode, int(max_rows), _stream(stream)),
+               "isdf_plan_create")
+
+    def close(self):
+        if self._h and self._h.value:
+            lib().isdf_plan_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def status(self):
+        d = ctypes.c_int32(0)
+        rc = lib().isdf_plan_status(self._h, ctypes.byref(d))
+        return int(rc), int(d.value)
+
+    def check(self):
+        rc, d = self.status()
+        if rc != 0:
+            raise ISDFError(rc, "isdf_plan_status", d)
+
+    def matrix(self, which: str, stream=None) -> torch.Tensor:
+        """Copy of a plan-owned matrix: "M", "L", "Minv", "Phi_mu", "Psi_mu"."""
+        code = {"M": 0, "L": 1, "Minv": 2, "Phi_mu": 3, "Psi_mu": 4}[which]
+        cols = self.n_mu if code < 3 else (self.n_phi if code == 3 else self.n_psi)
+        out = torch.empty((self.n_mu, cols), dtype=torch.complex128, device=self.phi.device)
+        _check(lib().isdf_plan_copy_matrix(self._h, code, _ptr(out), _stream(stream)), "isdf_plan_copy_matrix")
+        return out
+
+    def fit_theta(self, row_begin: int = 0, row_count: int | None = None, out=None, stream=None):
+        if row_count is None:
+            row_count = self.n_r - row_begin
+        th = out if out is not None else torch.empty((row_count, self.n_mu), dtype=self.theta_dtype,
+                                                     device=self.phi.device)
+        if th.dtype != self.theta_dtype or th.stride(1) != 1:
+            raise ValueError("theta output has the wrong dtype or layout")
+        _check(lib().isdf_fit_theta(self._h, int(row_begin), int(row_count), _ptr(th), th.stride(0),
+                                    _stream(stream)), "isdf_fit_theta")
+        return th
+
+    def backward(self, row_begin: int, row_count: int, grad_phi: torch.Tensor, grad_psi: torch.Tensor,
+                 grad_theta: torch.Tensor | None = None, K: torch.Tensor | None = None, dV: float = 1.0,
+                 loss: torch.Tensor | None = None, stream=None):
+        if grad_theta is not None and (grad_theta.dtype != self.theta_dtype or grad_theta.stride(1) != 1):
+            raise ValueError("grad_theta has the wrong dtype or layout")
+        if K is not None and (K.dtype != torch.complex128 or not K.is_contiguous()):
+            raise ValueError("K must be a contiguous complex128 matrix")
+        for g in (grad_phi, grad_psi):
+            if g.dtype != torch.complex128 or g.stride(1) != 1:
+                raise ValueError("gradients are complex128 with contiguous rows")
+        _check(lib().isdf_fit_theta_backward(self._h, int(row_begin), int(row_count), _ptr(grad_theta),
+                                             grad_theta.stride(0) if grad_theta is not None else 0, _ptr(K),
+                                             float(dV), _ptr(grad_phi), grad_phi.stride(0), _ptr(grad_psi),
+                                             grad_psi.stride(0), _ptr(loss), _stream(stream)),
+               "isdf_fit_theta_backward")
+
+    def backward_finalize(self, grad_phi: torch.Tensor, grad_psi: torch.Tensor, stream=None):
+        _check(lib().isdf_fit_theta_backward_finalize(self._h, _ptr(grad_phi), grad_phi.stride(0), _ptr(grad_psi),
+                                                      grad_psi.stride(0), _stream(stream)),
+               "isdf_fit_theta_backward_finalize")
+
+
+def decompose(phi, psi, shape, cell, n_mu, init_idx, iters, mode="fp64", kind="ssm", alpha=2.0,
+              early_stop=False, max_rows=65536, theta_out=None):
+    """One ISDF decomposition: weights -> K-means -> Theta fit (all on the GPU)."""
+    w = weights(phi, psi, kind, alpha)
+    km = kmeans(w, shape, cell, n_mu, init_idx, iters, early_stop=early_stop)
+    plan = Plan(phi, psi, km["idx"], mode=mode, max_rows=max_rows)
+    theta = plan.fit_theta(out=theta_out)
+    return {"w": w, "kmeans": km, "plan": plan, "theta": theta}
+
+
+class ISDFThetaFn(torch.autograd.Function):
+    """Theta(Phi, Psi) at fixed idx with the hand-written adjoint kernels.
+
+    Forward computes Theta through the plan; backward replays the fit block by
+    block (Theta is recomputed, never saved) and returns dL/dPhi, dL/dPsi in
+    complex128 (torch's convention dL/dRe + i dL/dIm), cast to the input dtype.
+    """
+
+    @staticmethod
+    def forward(ctx, phi, psi, idx, mode="fp64", max_rows=65536):
+        plan = Plan(phi.detach(), psi.detach(), idx, mode=mode, max_rows=max_rows)
+        theta = plan.fit_theta()
+        ctx.plan = plan
+        ctx.dtypes = (phi.dtype, psi.dtype)
+        return theta
+
+    @staticmethod
+    def backward(ctx, grad_theta):
+        plan = ctx.plan
+        gphi = torch.zeros((plan.n_r, plan.n_phi), dtype=torch.complex128, device=grad_theta.device)
+        gpsi = torch.zeros((plan.n_r, plan.n_psi), dtype=torch.complex128, device=grad_theta.device)
+        g = grad_theta.to(plan.theta_dtype).contiguous()
+        for r0 in range(0, plan.n_r, 1 << 20):
+            n = min(1 << 20, plan.n_r - r0)
+            plan.backward(r0, n, gphi, gpsi, grad_theta=g[r0:r0 + n])
+        plan.backward_finalize(gphi, gpsi)
+        return gphi.to(ctx.dtypes[0]), gpsi.to(ctx.dtypes[1]), None, None, None
+
+
+def surrogate_loss_and_grad(plan: Plan, K: torch.Tensor, dV: float, block: int = 1 << 20):
+    """Fused exchange-like surrogate L = dV sum_r Re[conj(Theta_r) K Theta_r] and
+    its gradients dL/dPhi, dL/dPsi, with Theta recomputed per block (never stored)."""
+    dev = plan.phi.device
+    gphi = torch.zeros((plan.n_r, plan.n_phi), dtype=torch.complex128, device=dev)
+    gpsi = torch.zeros((plan.n_r, plan.n_psi), dtype=torch.complex128, device=dev)
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    for r0 in range(0, plan.n_r, block):
+        n = min(block, plan.n_r - r0)
+        plan.backward(r0, n, gphi, gpsi, K=K, dV=dV, loss=loss)
+    plan.backward_finalize(gphi, gpsi)
+    return loss, gphi, gpsi

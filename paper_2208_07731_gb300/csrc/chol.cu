@@ -1,0 +1,184 @@
+// FP64 blocked Cholesky of M = C C^H (the paper solves its least-squares
+// normal equations with a linear solver, Sec. 2.4), the inverse of the
+// Cholesky factor and M^-1 = L^-H L^-1.
+//
+// Right-looking Cholesky with 64-wide panels: one CTA factors the diagonal
+// block in shared memory and also inverts it; the panel below is L21 =
+// A21 L11^-H (a GEMM with the inverted diagonal block); the trailing lower
+// triangle is updated by A22 -= L21 L21^H. L^-1 is built recursively from the
+// inverted diagonal blocks: inv([[A, 0], [B, C]]) = [[A^-1, 0], [-C^-1 B A^-1, C^-1]].
+#include "chol.cuh"
+#include "zgemm.cuh"
+
+namespace {
+
+constexpr int NB = 64;
+
+// Factor the nb x nb diagonal block at (k, k) of A (lower triangle used),
+// write L_kk back (upper part zeroed) and L_kk^-1 into Linv at (k, k).
+__global__ void __launch_bounds__(256) potrf_diag(double2 *A, int64_t lda, const double2 *M0, double2 *Linv,
+                                                 int64_t ldi, int k, int nb, DeviceStatus *st)
+{
+    __shared__ double2 T[NB][NB + 1];
+    __shared__ double2 I[NB][NB + 1];
+    __shared__ int fail;
+    if (st->code != 0) return;
+    const int tid = threadIdx.x;
+    if (tid == 0) fail = 0;
+    for (int e = tid; e < NB * NB; e += 256) {
+        const int i = e / NB, j = e % NB;
+        double2 v = make_double2(0.0, 0.0);
+        if (i < nb && j <= i) v = A[(int64_t)(k + i) * lda + (k + j)];
+        T[i][j] = v;
+    }
+    __syncthreads();
+    for (int j = 0; j < nb; ++j) {
+        if (tid == 0) {
+            const double d = T[j][j].x;
+            // a pivot below 1e-13 of the original diagonal means cond(M) >~ 1e13: not usable as HPD
+            const double d0 = M0[(int64_t)(k + j) * lda + (k + j)].x;
+            if (!(d > 1e-13 * d0) || isinf(d)) {
+                set_status(st, isnan(d) ? ISDF_ERR_NONFINITE : ISDF_ERR_NOT_HPD, k + j);
+                fail = 1;
+            } else {
+                T[j][j] = make_double2(sqrt(d), 0.0);
+            }
+        }
+        __syncthreads();
+        if (fail) return;
+        const double ljj = T[j][j].x;
+        for (int i = j + 1 + tid; i < nb; i += 256) T[i][j] = make_double2(T[i][j].x / ljj, T[i][j].y / ljj);
+        __syncthreads();
+        // trailing update of the lower triangle: T[i][c] -= T[i][j] conj(T[c][j]), j < c <= i
+        const int rem = nb - j - 1;
+        for (int e = tid; e < rem * rem; e += 256) {
+            const int i = j + 1 + e / rem, c = j + 1 + e % rem;
+            if (c <= i) {
+                const double2 a = T[i][j], b = T[c][j];
+                T[i][c].x -= a.x * b.x + a.y * b.y;
+                T[i][c].y -= a.y * b.x - a.x * b.y;
+            }
+        }
+        __syncthreads();
+    }
+    // inverse of the lower-triangular T by forward substitution, one column per thread
+    for (int c = tid; c < nb; c += 256) {
+        for (int i = 0; i < nb; ++i) {
+            if (i < c) {
+                I[i][c] = make_double2(0.0, 0.0);
+                continue;
+            }
+            double2 s = make_double2(i == c ? 1.0 : 0.0, 0.0);
+            for (int l = c; l < i; ++l) {
+                const double2 a = T[i][l], b = I[l][c];
+                s.x -= a.x * b.x - a.y * b.y;
+                s.y -= a.x * b.y + a.y * b.x;
+            }
+            const double d = T[i][i].x;
+            I[i][c] = make_double2(s.x / d, s.y / d);
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < nb * nb; e += 256) {
+        const int i = e / nb, j = e % nb;
+        A[(int64_t)(k + i) * lda + (k + j)] = j <= i ? T[i][j] : make_double2(0.0, 0.0);
+        Linv[(int64_t)(k + i) * ldi + (k + j)] = j <= i ? I[i][j] : make_double2(0.0, 0.0);
+    }
+}
+
+__global__ void zero_strict_upper(double2 *A, int n, int64_t lda)
+{
+    const int64_t total = (int64_t)n * n;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / n), j = (int)(e % n);
+        if (j > i) A[(int64_t)i * lda + j] = make_double2(0.0, 0.0);
+    }
+}
+
+ZOperand op(const double2 *p, int64_t s0, int64_t s1, int conj)
+{
+    ZOperand o;
+    o.p = p;
+    o.s0 = s0;
+    o.s1 = s1;
+    o.conj = conj;
+    o.type = ZG_C128;
+    return o;
+}
+
+ZGemm single(int M, int N, int K, ZOperand A, ZOperand B, double2 *C, int64_t ldc, double alpha, int beta)
+{
+    ZGemm g{};
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.A1 = A;
+    g.B1 = B;
+    g.C = C;
+    g.scm = ldc;
+    g.scn = 1;
+    g.ctype = ZG_C128;
+    g.alpha = alpha;
+    g.beta = beta;
+    g.splits = 1;
+    return g;
+}
+
+// Linv[o:o+n, o:o+n] = inverse of the lower-triangular L block (its 64-wide
+// diagonal blocks are already inverted in Linv).
+isdf_status tri_inv(const double2 *L, double2 *Linv, double2 *tmp, int64_t ld, int o, int n, cudaStream_t st)
+{
+    if (n <= NB) return ISDF_OK;
+    const int h = ((n / 2 + NB - 1) / NB) * NB;
+    ISDF_TRY(tri_inv(L, Linv, tmp, ld, o, h, st));
+    ISDF_TRY(tri_inv(L, Linv, tmp, ld, o + h, n - h, st));
+    // tmp = L[o+h:o+n, o:o+h] * Linv[o:o+h, o:o+h]   (Linv lower: k >= n)
+    ZGemm g1 = single(n - h, h, h, op(L + (int64_t)(o + h) * ld + o, ld, 1, 0),
+                      op(Linv + (int64_t)o * ld + o, ld, 1, 0), tmp, h, 1.0, 0);
+    g1.kmode = ZG_K_FROM_N0;
+    ISDF_TRY(zgemm(g1, st));
+    // Linv[o+h:o+n, o:o+h] = -Linv[o+h:o+n, o+h:o+n] * tmp   (A lower: k <= m)
+    ZGemm g2 = single(n - h, h, n - h, op(Linv + (int64_t)(o + h) * ld + (o + h), ld, 1, 0),
+                      op(tmp, h, 1, 0), Linv + (int64_t)(o + h) * ld + o, ld, -1.0, 0);
+    g2.k_to_m_end = 1;
+    return zgemm(g2, st);
+}
+
+}  // namespace
+
+isdf_status cholesky_inverse(const double2 *M0, double2 *L, double2 *Linv, double2 *W, double2 *tmp, int n,
+                             DeviceStatus *st, cudaStream_t stream)
+{
+    const int64_t ld = n;
+    ISDF_CUDA_TRY(cudaMemsetAsync(Linv, 0, sizeof(double2) * (size_t)n * n, stream));
+    for (int k = 0; k < n; k += NB) {
+        const int nb = n - k < NB ? n - k : NB;
+        potrf_diag<<<1, 256, 0, stream>>>(L, ld, M0, Linv, ld, k, nb, st);
+        ISDF_LAUNCH_CHECK();
+        const int rest = n - k - nb;
+        if (rest <= 0) break;
+        // L21 = A21 * Lkk^-H  (in place: one CTA column per row block)
+        ZGemm p = single(rest, nb, nb, op(L + (int64_t)(k + nb) * ld + k, ld, 1, 0),
+                         op(Linv + (int64_t)k * ld + k, 1, ld, 1), L + (int64_t)(k + nb) * ld + k, ld, 1.0, 0);
+        ISDF_TRY(zgemm(p, stream));
+        // A22 -= L21 L21^H (lower tiles)
+        ZGemm u = single(rest, rest, nb, op(L + (int64_t)(k + nb) * ld + k, ld, 1, 0),
+                         op(L + (int64_t)(k + nb) * ld + k, 1, ld, 1), L + (int64_t)(k + nb) * ld + (k + nb), ld,
+                         -1.0, 1);
+        u.lower_only = 1;
+        ISDF_TRY(zgemm(u, stream));
+    }
+    {
+        const int64_t total = (int64_t)n * n;
+        const unsigned gr = (unsigned)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+        zero_strict_upper<<<gr, 256, 0, stream>>>(L, n, ld);
+        ISDF_LAUNCH_CHECK();
+    }
+    ISDF_TRY(tri_inv(L, Linv, tmp, ld, 0, n, stream));
+    // W = Linv^H Linv: W_ij = sum_{k >= max(i, j)} conj(Linv_ki) Linv_kj (lower tiles, then mirrored)
+    ZGemm w = single(n, n, n, op(Linv, 1, ld, 1), op(Linv, ld, 1, 0), W, ld, 1.0, 0);
+    w.kmode = ZG_K_FROM_MAX_MN;
+    w.lower_only = 1;
+    ISDF_TRY(zgemm(w, stream));
+    return hermitian_mirror(W, n, ld, stream);
+}

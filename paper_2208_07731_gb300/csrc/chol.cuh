@@ -1,0 +1,11 @@
+#pragma once
+
+#include "common.cuh"
+
+// In place: L (n x n, row-major, holding a copy of M0 = M) becomes the
+// Cholesky factor (strict upper triangle zeroed); Linv = L^-1 (lower);
+// W = M^-1 = L^-H L^-1 (full Hermitian). tmp: n x n scratch. A pivot that is
+// not above 1e-13 times M's original diagonal entry is recorded in *st
+// (ISDF_ERR_NOT_HPD, detail = pivot index; ISDF_ERR_NONFINITE for NaN).
+isdf_status cholesky_inverse(const double2 *M0, double2 *L, double2 *Linv, double2 *W, double2 *tmp, int n,
+                             DeviceStatus *st, cudaStream_t stream);

@@ -1,0 +1,64 @@
+// Shared helpers of the CUDA library: status handling, complex arithmetic
+// with explicit IEEE rounding, and the layout of the plan.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/isdf.h"
+
+#define ISDF_CUDA_TRY(expr)                                   \
+    do {                                                      \
+        cudaError_t e_ = (expr);                              \
+        if (e_ != cudaSuccess) return ISDF_ERR_CUDA;          \
+    } while (0)
+
+#define ISDF_LAUNCH_CHECK()                                   \
+    do {                                                      \
+        cudaError_t e_ = cudaGetLastError();                  \
+        if (e_ != cudaSuccess) return ISDF_ERR_CUDA;          \
+    } while (0)
+
+#define ISDF_TRY(expr)                                        \
+    do {                                                      \
+        isdf_status s_ = (expr);                              \
+        if (s_ != ISDF_OK) return s_;                         \
+    } while (0)
+
+static inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+static inline bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// Device status word of a plan: first failure wins.
+struct DeviceStatus {
+    int32_t code;    // isdf_status
+    int32_t detail;  // e.g. the failing pivot
+};
+
+__device__ __forceinline__ void set_status(DeviceStatus *st, int32_t code, int32_t detail)
+{
+    if (atomicCAS(&st->code, 0, code) == 0) st->detail = detail;
+}
+
+// ---- complex arithmetic on double2 (re, im) --------------------------------
+__device__ __forceinline__ double2 cload(const double2 *p, int64_t i) { return p[i]; }
+__device__ __forceinline__ double2 cload(const float2 *p, int64_t i)
+{
+    float2 v = p[i];
+    return make_double2((double)v.x, (double)v.y);
+}
+__device__ __forceinline__ void cstore(double2 *p, int64_t i, double2 v) { p[i] = v; }
+__device__ __forceinline__ void cstore(float2 *p, int64_t i, double2 v)
+{
+    p[i] = make_float2((float)v.x, (float)v.y);
+}
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b)
+{
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+__device__ __forceinline__ double2 cmulc(double2 a, double2 b)
+{
+    return make_double2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}

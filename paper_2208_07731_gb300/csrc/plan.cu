@@ -1,0 +1,481 @@
+// Step 3 (Sec. 2.1, Eq. theta; Eqs. phipsi, muRownuCol, muRownuColden;
+// Sec. 2.4): the interpolation-vector fit and its adjoint at fixed
+// interpolation points. Host orchestration of the kernels in zgemm.cu,
+// chol.cu and mixed.cu.
+#include <stdlib.h>
+#include <string.h>
+
+#include "chol.cuh"
+#include "mixed.cuh"
+#include "plan.cuh"
+#include "zgemm.cuh"
+
+namespace {
+
+__global__ void gather_rows(const void *src, int64_t ld, int type, int n, const int64_t *idx, int n_mu,
+                            int64_t n_r, double2 *dst, DeviceStatus *st)
+{
+    const int64_t total = (int64_t)n_mu * n;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int m = (int)(e / n), i = (int)(e % n);
+        int64_t r = idx[m];
+        if (r < 0 || r >= n_r) {
+            set_status(st, ISDF_ERR_INVALID_ARG, m);
+            r = 0;
+        }
+        double2 v = type == ISDF_C128 ? cload(static_cast<const double2 *>(src), r * ld + i)
+                                      : cload(static_cast<const float2 *>(src), r * ld + i);
+        if (!isfinite(v.x) || !isfinite(v.y)) set_status(st, ISDF_ERR_NONFINITE, m);
+        dst[e] = v;
+    }
+}
+
+// Abar = Ybar o B (into A's place), Bbar = conj(Ybar) o A (into B's place)
+__global__ void hadamard_adjoint(const double2 *Yb, double2 *A, double2 *B, int64_t total)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const double2 y = Yb[e], a = A[e], b = B[e];
+        A[e] = cmul(y, b);
+        B[e] = cmul(cconj(y), a);
+    }
+}
+
+// X = Mbar o Bmu + (Mbar o Bmu)^H   and   Xp = conj(Mbar) o Amu + (conj(Mbar) o Amu)^H
+__global__ void hermitian_parts(const double2 *Mbar, const double2 *Amu, const double2 *Bmu, double2 *X,
+                                double2 *Xp, int n)
+{
+    const int64_t total = (int64_t)n * n;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / n), j = (int)(e % n);
+        const int64_t t = (int64_t)j * n + i;
+        const double2 a = cmul(Mbar[e], Bmu[e]), at = cmul(Mbar[t], Bmu[t]);
+        X[e] = make_double2(a.x + at.x, a.y - at.y);
+        const double2 b = cmul(cconj(Mbar[e]), Amu[e]), bt = cmul(cconj(Mbar[t]), Amu[t]);
+        Xp[e] = make_double2(b.x + bt.x, b.y - bt.y);
+    }
+}
+
+__global__ void scatter_add_rows(const double2 *src, int n, const int64_t *idx, int n_mu, double2 *dst, int64_t ld)
+{
+    const int64_t total = (int64_t)n_mu * n;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int m = (int)(e / n), i = (int)(e % n);
+        double2 *d = dst + idx[m] * ld + i;
+        const double2 v = src[e];
+        d->x += v.x;
+        d->y += v.y;
+    }
+}
+
+// loss += 1/2 Re sum conj(Theta) o G   (G = 2 dV Theta conj(K))
+template <typename T>
+__global__ void surrogate_loss_kernel(const T *theta, int64_t ldt, const double2 *G, int64_t ldg, int rows, int n,
+                                      double *loss)
+{
+    __shared__ double red[8];
+    double s = 0.0;
+    const int64_t total = (int64_t)rows * n;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / n), c = (int)(e % n);
+        const double2 t = cload(theta, (int64_t)r * ldt + c), g = G[(int64_t)r * ldg + c];
+        s += t.x * g.x + t.y * g.y;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) b += red[i];
+        atomicAdd(loss, 0.5 * b);
+    }
+}
+
+unsigned grid_for(int64_t total, unsigned cap = 8192)
+{
+    const int64_t g = (total + 255) / 256;
+    return (unsigned)(g < 1 ? 1 : (g < cap ? g : cap));
+}
+
+ZOperand opnd(const void *p, int64_t s0, int64_t s1, int conj, int type)
+{
+    ZOperand o;
+    o.p = p;
+    o.s0 = s0;
+    o.s1 = s1;
+    o.conj = conj;
+    o.type = type;
+    return o;
+}
+
+ZGemm gemm1(int M, int N, int K, ZOperand A, ZOperand B, void *C, int64_t ldc, int ctype, double alpha, int beta)
+{
+    ZGemm g{};
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.A1 = A;
+    g.B1 = B;
+    g.C = C;
+    g.scm = ldc;
+    g.scn = 1;
+    g.ctype = ctype;
+    g.alpha = alpha;
+    g.beta = beta;
+    g.splits = 1;
+    return g;
+}
+
+int split_count(int M, int N, int K)
+{
+    const int tiles = ((M + 63) / 64) * ((N + 63) / 64);
+    int s = 1;
+    while (s < 64 && tiles * s < 2 * 152 && K / (s * 2) >= 256) s *= 2;
+    return s;
+}
+
+template <typename T>
+isdf_status alloc(T **p, size_t count)
+{
+    ISDF_CUDA_TRY(cudaMalloc((void **)p, sizeof(T) * (count ? count : 1)));
+    return ISDF_OK;
+}
+
+// Y rows (and optionally the separate factors A, B) for rows [r0, r0 + rows)
+isdf_status gram_hadamard_fp64(isdf_plan *p, int64_t r0, int rows, double2 *Y, double2 *A, double2 *B,
+                               cudaStream_t st)
+{
+    const int t = p->dtype == ISDF_C128 ? ZG_C128 : ZG_C64;
+    const size_t es = p->dtype == ISDF_C128 ? 16 : 8;
+    ZGemm g{};
+    g.M = rows;
+    g.N = p->n_mu;
+    g.K = p->n_phi;
+    g.dual = 1;
+    g.A1 = opnd(static_cast<const char *>(p->phi) + r0 * p->ld_phi * es, p->ld_phi, 1, 0, t);
+    g.B1 = opnd(p->phi_mu, 1, p->n_phi, 1, ZG_C128);
+    g.A2 = opnd(static_cast<const char *>(p->psi) + r0 * p->ld_psi * es, p->ld_psi, 1, 0, t);
+    g.B2 = opnd(p->psi_mu, 1, p->n_psi, 1, ZG_C128);
+    g.C = Y;
+    g.scm = p->n_mu;
+    g.scn = 1;
+    g.ctype = ZG_C128;
+    g.C1 = A;
+    g.C2 = B;
+    g.splits = 1;
+    if (p->n_phi != p->n_psi) {
+        // different K for the two products: run them as two single GEMMs + Hadamard
+        return ISDF_ERR_UNSUPPORTED;
+    }
+    return zgemm(g, st);
+}
+
+}  // namespace
+
+extern "C" isdf_status isdf_plan_create(isdf_plan **plan, const void *phi, int64_t ld_phi, const void *psi,
+                                        int64_t ld_psi, int64_t n_r, int32_t n_phi, int32_t n_psi, int32_t dtype,
+                                        const int64_t *idx, int32_t n_mu, int32_t mode, int64_t max_rows,
+                                        void *stream)
+{
+    if (!plan) return ISDF_ERR_INVALID_ARG;
+    *plan = nullptr;
+    if (!phi || !psi || !idx || n_r < 1 || n_phi < 1 || n_psi < 1 || ld_phi < n_phi || ld_psi < n_psi)
+        return ISDF_ERR_INVALID_ARG;
+    if (dtype != ISDF_C128 && dtype != ISDF_C64) return ISDF_ERR_INVALID_ARG;
+    if (mode != ISDF_FP64 && mode != ISDF_MIXED) return ISDF_ERR_INVALID_ARG;
+    if (n_mu < 1 || n_mu > n_r || max_rows < 1) return ISDF_ERR_INVALID_ARG;
+    if (n_mu > 8192 || n_phi > 4096 || n_psi > 4096) return ISDF_ERR_UNSUPPORTED;
+    if (n_phi != n_psi) return ISDF_ERR_UNSUPPORTED;
+    const size_t el = dtype == ISDF_C128 ? 16 : 8;
+    if (!aligned(phi, el) || !aligned(psi, el)) return ISDF_ERR_INVALID_ARG;
+    if (mode == ISDF_MIXED && !mixed_supported(n_phi, n_mu, ld_phi, ld_psi, dtype)) return ISDF_ERR_UNSUPPORTED;
+    if (max_rows > n_r) max_rows = n_r;
+    if (max_rows > 4 * 1024 * 1024) max_rows = 4 * 1024 * 1024;
+
+    isdf_plan *p = static_cast<isdf_plan *>(calloc(1, sizeof(isdf_plan)));
+    if (!p) return ISDF_ERR_CUDA;
+    p->phi = phi;
+    p->psi = psi;
+    p->ld_phi = ld_phi;
+    p->ld_psi = ld_psi;
+    p->n_r = n_r;
+    p->n_phi = n_phi;
+    p->n_psi = n_psi;
+    p->dtype = dtype;
+    p->n_mu = n_mu;
+    p->mode = mode;
+    p->max_rows = max_rows;
+    cudaStream_t st = as_stream(stream);
+    p->last_stream = st;
+    const size_t nn = (size_t)n_mu * n_mu;
+    const size_t blk = (size_t)max_rows * n_mu;
+    isdf_status s = ISDF_OK;
+#define PLAN_ALLOC(ptr, cnt)                       \
+    do {                                           \
+        if ((s = alloc(&(ptr), (cnt))) != ISDF_OK) { \
+            isdf_plan_destroy(p);                  \
+            return s;                              \
+        }                                          \
+    } while (0)
+    PLAN_ALLOC(p->status, 1);
+    PLAN_ALLOC(p->idx, (size_t)n_mu);
+    PLAN_ALLOC(p->phi_mu, (size_t)n_mu * n_phi);
+    PLAN_ALLOC(p->psi_mu, (size_t)n_mu * n_psi);
+    PLAN_ALLOC(p->M, nn);
+    PLAN_ALLOC(p->Amu, nn);
+    PLAN_ALLOC(p->Bmu, nn);
+    PLAN_ALLOC(p->L, nn);
+    PLAN_ALLOC(p->Linv, nn);
+    PLAN_ALLOC(p->W, nn);
+    PLAN_ALLOC(p->tmp, nn);
+    PLAN_ALLOC(p->tmp2, nn);
+    PLAN_ALLOC(p->Mbar, nn);
+    PLAN_ALLOC(p->gphi_mu, (size_t)n_mu * n_phi);
+    PLAN_ALLOC(p->gpsi_mu, (size_t)n_mu * n_psi);
+    PLAN_ALLOC(p->blkY, blk);
+    if (mode == ISDF_FP64) {
+        PLAN_ALLOC(p->blkT, blk);
+    }
+    p->partial_elems = 64 * (size_t)n_mu * (n_mu > n_phi ? n_mu : n_phi);
+    PLAN_ALLOC(p->partial, p->partial_elems);
+#undef PLAN_ALLOC
+    ISDF_CUDA_TRY(cudaMemsetAsync(p->status, 0, sizeof(DeviceStatus), st));
+    ISDF_CUDA_TRY(cudaMemcpyAsync(p->idx, idx, sizeof(int64_t) * n_mu, cudaMemcpyDeviceToDevice, st));
+    ISDF_CUDA_TRY(cudaMemsetAsync(p->Mbar, 0, sizeof(double2) * nn, st));
+    ISDF_CUDA_TRY(cudaMemsetAsync(p->gphi_mu, 0, sizeof(double2) * n_mu * n_phi, st));
+    ISDF_CUDA_TRY(cudaMemsetAsync(p->gpsi_mu, 0, sizeof(double2) * n_mu * n_psi, st));
+
+    // a7: Phi_mu = Phi[idx], Psi_mu = Psi[idx]  (Eq. Cmu)
+    gather_rows<<<grid_for((int64_t)n_mu * n_phi), 256, 0, st>>>(phi, ld_phi, dtype, n_phi, p->idx, n_mu, n_r,
+                                                                 p->phi_mu, p->status);
+    gather_rows<<<grid_for((int64_t)n_mu * n_psi), 256, 0, st>>>(psi, ld_psi, dtype, n_psi, p->idx, n_mu, n_r,
+                                                                 p->psi_mu, p->status);
+    ISDF_LAUNCH_CHECK();
+    // a8: M = (Phi_mu Phi_mu^H) o conj(Psi_mu Psi_mu^H), FP64, lower tiles then mirrored
+    {
+        ZGemm g{};
+        g.M = n_mu;
+        g.N = n_mu;
+        g.K = n_phi;
+        g.dual = 1;
+        g.A1 = opnd(p->phi_mu, n_phi, 1, 0, ZG_C128);
+        g.B1 = opnd(p->phi_mu, 1, n_phi, 1, ZG_C128);
+        g.A2 = opnd(p->psi_mu, n_psi, 1, 0, ZG_C128);
+        g.B2 = opnd(p->psi_mu, 1, n_psi, 1, ZG_C128);
+        g.C = p->M;
+        g.scm = n_mu;
+        g.scn = 1;
+        g.ctype = ZG_C128;
+        g.C1 = p->Amu;
+        g.C2 = p->Bmu;
+        g.lower_only = 1;
+        g.splits = 1;
+        if ((s = zgemm(g, st)) != ISDF_OK) {
+            isdf_plan_destroy(p);
+            return s;
+        }
+        for (double2 *m : {p->M, p->Amu, p->Bmu})
+            if ((s = hermitian_mirror(m, n_mu, n_mu, st)) != ISDF_OK) {
+                isdf_plan_destroy(p);
+                return s;
+            }
+    }
+    // a9: M = L L^H, L^-1, M^-1 (FP64)
+    ISDF_CUDA_TRY(cudaMemcpyAsync(p->L, p->M, sizeof(double2) * nn, cudaMemcpyDeviceToDevice, st));
+    if ((s = cholesky_inverse(p->M, p->L, p->Linv, p->W, p->tmp, n_mu, p->status, st)) != ISDF_OK) {
+        isdf_plan_destroy(p);
+        return s;
+    }
+    if (mode == ISDF_MIXED && (s = mixed_prepare(p, st)) != ISDF_OK) {
+        isdf_plan_destroy(p);
+        return s;
+    }
+    *plan = p;
+    return ISDF_OK;
+}
+
+extern "C" isdf_status isdf_fit_theta(isdf_plan *p, int64_t row_begin, int64_t row_count, void *theta,
+                                      int64_t ld_theta, void *stream)
+{
+    if (!p || row_begin < 0 || row_count < 0 || row_begin + row_count > p->n_r || ld_theta < p->n_mu)
+        return ISDF_ERR_INVALID_ARG;
+    if (row_count == 0) return ISDF_OK;
+    if (!theta || !aligned(theta, p->mode == ISDF_FP64 ? 16 : 8)) return ISDF_ERR_INVALID_ARG;
+    cudaStream_t st = as_stream(stream);
+    p->last_stream = st;
+    if (p->mode == ISDF_MIXED) return mixed_fit(p, row_begin, row_count, theta, ld_theta, st);
+    for (int64_t r0 = row_begin; r0 < row_begin + row_count; r0 += p->max_rows) {
+        const int rows = (int)((row_begin + row_count - r0) < p->max_rows ? (row_begin + row_count - r0) : p->max_rows);
+        // a10: Y_b = (Phi_b Phi_mu^H) o conj(Psi_b Psi_mu^H)
+        ISDF_TRY(gram_hadamard_fp64(p, r0, rows, p->blkY, nullptr, nullptr, st));
+        // a11: Theta_b = Y_b M^-1
+        double2 *out = static_cast<double2 *>(theta) + (r0 - row_begin) * ld_theta;
+        ZGemm g = gemm1(rows, p->n_mu, p->n_mu, opnd(p->blkY, p->n_mu, 1, 0, ZG_C128),
+                        opnd(p->W, p->n_mu, 1, 0, ZG_C128), out, ld_theta, ZG_C128, 1.0, 0);
+        ISDF_TRY(zgemm(g, st));
+    }
+    return ISDF_OK;
+}
+
+extern "C" isdf_status isdf_fit_theta_backward(isdf_plan *p, int64_t row_begin, int64_t row_count,
+                                               const void *grad_theta, int64_t ld_grad, const void *K, double dV,
+                                               void *grad_phi, int64_t ld_gphi, void *grad_psi, int64_t ld_gpsi,
+                                               double *loss, void *stream)
+{
+    if (!p || row_begin < 0 || row_count < 0 || row_begin + row_count > p->n_r) return ISDF_ERR_INVALID_ARG;
+    if (!grad_phi || !grad_psi || ld_gphi < p->n_phi || ld_gpsi < p->n_psi) return ISDF_ERR_INVALID_ARG;
+    if (!grad_theta && !K) return ISDF_ERR_INVALID_ARG;
+    if (grad_theta && ld_grad < p->n_mu) return ISDF_ERR_INVALID_ARG;
+    if (!aligned(grad_phi, 16) || !aligned(grad_psi, 16)) return ISDF_ERR_INVALID_ARG;
+    if (row_count == 0) return ISDF_OK;
+    cudaStream_t st = as_stream(stream);
+    p->last_stream = st;
+    if (p->mode == ISDF_MIXED)
+        return mixed_backward(p, row_begin, row_count, grad_theta, ld_grad, K, dV, grad_phi, ld_gphi, grad_psi,
+                              ld_gpsi, loss, st);
+    const int nm = p->n_mu;
+    const int t = p->dtype == ISDF_C128 ? ZG_C128 : ZG_C64;
+    const size_t es = p->dtype == ISDF_C128 ? 16 : 8;
+    if (!p->blkA) {
+        ISDF_TRY(alloc(&p->blkA, (size_t)p->max_rows * nm));
+        ISDF_TRY(alloc(&p->blkB, (size_t)p->max_rows * nm));
+        ISDF_TRY(alloc(&p->blkG, (size_t)p->max_rows * nm));
+    }
+    for (int64_t r0 = row_begin; r0 < row_begin + row_count; r0 += p->max_rows) {
+        const int rows = (int)((row_begin + row_count - r0) < p->max_rows ? (row_begin + row_count - r0) : p->max_rows);
+        // recompute A_b, B_b and Y_b = A_b o conj(B_b)
+        ISDF_TRY(gram_hadamard_fp64(p, r0, rows, p->blkY, p->blkA, p->blkB, st));
+        // Theta_b = Y_b M^-1
+        ISDF_TRY(zgemm(gemm1(rows, nm, nm, opnd(p->blkY, nm, 1, 0, ZG_C128), opnd(p->W, nm, 1, 0, ZG_C128),
+                             p->blkT, nm, ZG_C128, 1.0, 0), st));
+        // G_b
+        const void *G;
+        int gtype;
+        int64_t ldg;
+        if (grad_theta) {
+            G = static_cast<const char *>(grad_theta) + (r0 - row_begin) * ld_grad * 16;
+            gtype = ZG_C128;
+            ldg = ld_grad;
+        } else {
+            // G = 2 dV Theta conj(K)
+            ISDF_TRY(zgemm(gemm1(rows, nm, nm, opnd(p->blkT, nm, 1, 0, ZG_C128), opnd(K, nm, 1, 1, ZG_C128),
+                                 p->blkG, nm, ZG_C128, 2.0 * dV, 0), st));
+            G = p->blkG;
+            gtype = ZG_C128;
+            ldg = nm;
+            if (loss) {
+                surrogate_loss_kernel<double2><<<grid_for((int64_t)rows * nm, 2048), 256, 0, st>>>(
+                    p->blkT, nm, p->blkG, nm, rows, nm, loss);
+                ISDF_LAUNCH_CHECK();
+            }
+        }
+        // Ybar = G M^-1 (into blkY)
+        ISDF_TRY(zgemm(gemm1(rows, nm, nm, opnd(G, ldg, 1, 0, gtype), opnd(p->W, nm, 1, 0, ZG_C128), p->blkY, nm,
+                             ZG_C128, 1.0, 0), st));
+        // Mbar -= Theta_b^H Ybar
+        {
+            ZGemm g = gemm1(nm, nm, rows, opnd(p->blkT, 1, nm, 1, ZG_C128), opnd(p->blkY, nm, 1, 0, ZG_C128), p->Mbar,
+                            nm, ZG_C128, -1.0, 1);
+            g.splits = split_count(nm, nm, rows);
+            g.partial = p->partial;
+            ISDF_TRY(zgemm(g, st));
+        }
+        // Abar = Ybar o B, Bbar = conj(Ybar) o A
+        hadamard_adjoint<<<grid_for((int64_t)rows * nm), 256, 0, st>>>(p->blkY, p->blkA, p->blkB, (int64_t)rows * nm);
+        ISDF_LAUNCH_CHECK();
+        // grad_phi[rows] += Abar Phi_mu, grad_psi[rows] += Bbar Psi_mu
+        double2 *gp = static_cast<double2 *>(grad_phi) + r0 * ld_gphi;
+        double2 *gq = static_cast<double2 *>(grad_psi) + r0 * ld_gpsi;
+        ISDF_TRY(zgemm(gemm1(rows, p->n_phi, nm, opnd(p->blkA, nm, 1, 0, ZG_C128),
+                             opnd(p->phi_mu, p->n_phi, 1, 0, ZG_C128), gp, ld_gphi, ZG_C128, 1.0, 1), st));
+        ISDF_TRY(zgemm(gemm1(rows, p->n_psi, nm, opnd(p->blkB, nm, 1, 0, ZG_C128),
+                             opnd(p->psi_mu, p->n_psi, 1, 0, ZG_C128), gq, ld_gpsi, ZG_C128, 1.0, 1), st));
+        // Phibar_mu += Abar^H Phi_b, Psibar_mu += Bbar^H Psi_b
+        {
+            ZGemm g = gemm1(nm, p->n_phi, rows, opnd(p->blkA, 1, nm, 1, ZG_C128),
+                            opnd(static_cast<const char *>(p->phi) + r0 * p->ld_phi * es, p->ld_phi, 1, 0, t),
+                            p->gphi_mu, p->n_phi, ZG_C128, 1.0, 1);
+            g.splits = split_count(nm, p->n_phi, rows);
+            g.partial = p->partial;
+            ISDF_TRY(zgemm(g, st));
+            ZGemm h = gemm1(nm, p->n_psi, rows, opnd(p->blkB, 1, nm, 1, ZG_C128),
+                            opnd(static_cast<const char *>(p->psi) + r0 * p->ld_psi * es, p->ld_psi, 1, 0, t),
+                            p->gpsi_mu, p->n_psi, ZG_C128, 1.0, 1);
+            h.splits = split_count(nm, p->n_psi, rows);
+            h.partial = p->partial;
+            ISDF_TRY(zgemm(h, st));
+        }
+    }
+    return ISDF_OK;
+}
+
+isdf_status backward_finalize_common(isdf_plan *p, void *grad_phi, int64_t ld_gphi, void *grad_psi, int64_t ld_gpsi,
+                                     cudaStream_t st)
+{
+    const int nm = p->n_mu;
+    const size_t nn = (size_t)nm * nm;
+    // X = Abar_mu + Abar_mu^H with Abar_mu = Mbar o B_mu; X2 likewise with Bbar_mu = conj(Mbar) o A_mu
+    double2 *X = p->tmp, *X2 = p->tmp2;
+    hermitian_parts<<<grid_for((int64_t)nn), 256, 0, st>>>(p->Mbar, p->Amu, p->Bmu, X, X2, nm);
+    ISDF_LAUNCH_CHECK();
+    ISDF_TRY(zgemm(gemm1(nm, p->n_phi, nm, opnd(X, nm, 1, 0, ZG_C128), opnd(p->phi_mu, p->n_phi, 1, 0, ZG_C128),
+                         p->gphi_mu, p->n_phi, ZG_C128, 1.0, 1), st));
+    ISDF_TRY(zgemm(gemm1(nm, p->n_psi, nm, opnd(X2, nm, 1, 0, ZG_C128), opnd(p->psi_mu, p->n_psi, 1, 0, ZG_C128),
+                         p->gpsi_mu, p->n_psi, ZG_C128, 1.0, 1), st));
+    scatter_add_rows<<<grid_for((int64_t)nm * p->n_phi), 256, 0, st>>>(p->gphi_mu, p->n_phi, p->idx, nm,
+                                                                       static_cast<double2 *>(grad_phi), ld_gphi);
+    scatter_add_rows<<<grid_for((int64_t)nm * p->n_psi), 256, 0, st>>>(p->gpsi_mu, p->n_psi, p->idx, nm,
+                                                                       static_cast<double2 *>(grad_psi), ld_gpsi);
+    ISDF_LAUNCH_CHECK();
+    ISDF_CUDA_TRY(cudaMemsetAsync(p->Mbar, 0, sizeof(double2) * nn, st));
+    ISDF_CUDA_TRY(cudaMemsetAsync(p->gphi_mu, 0, sizeof(double2) * nm * p->n_phi, st));
+    ISDF_CUDA_TRY(cudaMemsetAsync(p->gpsi_mu, 0, sizeof(double2) * nm * p->n_psi, st));
+    return ISDF_OK;
+}
+
+extern "C" isdf_status isdf_fit_theta_backward_finalize(isdf_plan *p, void *grad_phi, int64_t ld_gphi, void *grad_psi,
+                                                        int64_t ld_gpsi, void *stream)
+{
+    if (!p || !grad_phi || !grad_psi || ld_gphi < p->n_phi || ld_gpsi < p->n_psi) return ISDF_ERR_INVALID_ARG;
+    cudaStream_t st = as_stream(stream);
+    p->last_stream = st;
+    return backward_finalize_common(p, grad_phi, ld_gphi, grad_psi, ld_gpsi, st);
+}
+
+extern "C" isdf_status isdf_plan_status(isdf_plan *p, int32_t *detail)
+{
+    if (!p) return ISDF_ERR_INVALID_ARG;
+    ISDF_CUDA_TRY(cudaStreamSynchronize(p->last_stream));
+    DeviceStatus h{0, 0};
+    ISDF_CUDA_TRY(cudaMemcpy(&h, p->status, sizeof(h), cudaMemcpyDeviceToHost));
+    if (detail) *detail = h.detail;
+    return (isdf_status)h.code;
+}
+
+extern "C" isdf_status isdf_plan_copy_matrix(const isdf_plan *p, int32_t which, void *dst, void *stream)
+{
+    if (!p || !dst) return ISDF_ERR_INVALID_ARG;
+    const void *src = nullptr;
+    size_t count = (size_t)p->n_mu * p->n_mu;
+    switch (which) {
+    case 0: src = p->M; break;
+    case 1: src = p->L; break;
+    case 2: src = p->W; break;
+    case 3: src = p->phi_mu; count = (size_t)p->n_mu * p->n_phi; break;
+    case 4: src = p->psi_mu; count = (size_t)p->n_mu * p->n_psi; break;
+    default: return ISDF_ERR_INVALID_ARG;
+    }
+    ISDF_CUDA_TRY(cudaMemcpyAsync(dst, src, sizeof(double2) * count, cudaMemcpyDeviceToDevice, as_stream(stream)));
+    return ISDF_OK;
+}
+
+extern "C" void isdf_plan_destroy(isdf_plan *p)
+{
+    if (!p) return;
+    if (p->last_stream) cudaStreamSynchronize(p->last_stream);
+    void *bufs[] = {p->status, p->idx, p->phi_mu, p->psi_mu, p->M, p->Amu, p->Bmu, p->L, p->Linv, p->W, p->tmp, p->tmp2,
+                    p->Mbar, p->gphi_mu, p->gpsi_mu, p->blkY, p->blkT, p->blkA, p->blkB, p->blkG, p->partial};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    mixed_release(p);
+    free(p);
+}

@@ -1,0 +1,25 @@
+// The plan of one Theta fit: caller orbitals, gathered rows, M and its
+// factors, block scratch and the adjoint accumulators.
+#pragma once
+
+#include "common.cuh"
+
+struct MixedBuffers;
+
+struct isdf_plan {
+    const void *phi, *psi;
+    int64_t ld_phi, ld_psi, n_r;
+    int n_phi, n_psi, dtype, n_mu, mode;
+    int64_t max_rows;
+    cudaStream_t last_stream;
+    DeviceStatus *status;
+    int64_t *idx;
+    double2 *phi_mu, *psi_mu;                 // n_mu x n (complex128)
+    double2 *M, *Amu, *Bmu, *L, *Linv, *W;    // n_mu x n_mu
+    double2 *tmp, *tmp2;                      // n_mu x n_mu scratch
+    double2 *Mbar, *gphi_mu, *gpsi_mu;        // adjoint accumulators
+    double2 *blkY, *blkT, *blkA, *blkB, *blkG;  // max_rows x n_mu block scratch
+    double2 *partial;                         // split-K partials
+    size_t partial_elems;
+    MixedBuffers *mixed;                      // tensor-core path (ISDF_MIXED)
+};

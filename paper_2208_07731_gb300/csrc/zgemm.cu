@@ -1,0 +1,229 @@
+// Register-tiled complex FP64 GEMM on the FP64 pipe (GB300 has no FP64
+// tensor-core MMA). 64 x 64 complex output tile per CTA, 256 threads, 4 x 4
+// complex accumulators per thread, K staged through shared memory 8 complex
+// at a time with the conjugation applied on the way in. The dual form keeps
+// two products in registers and writes their Hadamard conjugate product,
+// Y = (Phi Phi_mu^H) o conj(Psi Psi_mu^H) (Eq. muRownuCol), without storing
+// either factor.
+#include "zgemm.cuh"
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 8;
+
+template <typename T>
+__device__ __forceinline__ double2 ld_c(const void *p, int64_t i)
+{
+    return cload(static_cast<const T *>(p), i);
+}
+
+template <typename TA, typename TB, bool DUAL>
+__device__ __forceinline__ void load_tiles(const ZGemm &g, int m0, int n0, int k0, int kend,
+                                           double2 (*As)[BK][BM + 1], double2 (*Bs)[BK][BN + 1])
+{
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int pr = 0; pr < (DUAL ? 2 : 1); ++pr) {
+        const ZOperand &A = pr ? g.A2 : g.A1;
+        const ZOperand &B = pr ? g.B2 : g.B1;
+        const bool a_k_contig = (A.s1 == 1);
+        const bool b_n_contig = (B.s1 == 1);
+#pragma unroll
+        for (int it = 0; it < (BM * BK) / 256; ++it) {
+            const int e = it * 256 + tid;
+            int mi, ki;
+            if (a_k_contig) { mi = e / BK; ki = e % BK; }
+            else { mi = e % BM; ki = e / BM; }
+            const int m = m0 + mi, k = k0 + ki;
+            double2 v = make_double2(0.0, 0.0);
+            if (m < g.M && k < kend) {
+                v = ld_c<TA>(A.p, (int64_t)m * A.s0 + (int64_t)k * A.s1);
+                if (A.conj) v.y = -v.y;
+            }
+            As[pr][ki][mi] = v;
+        }
+#pragma unroll
+        for (int it = 0; it < (BN * BK) / 256; ++it) {
+            const int e = it * 256 + tid;
+            int ni, ki;
+            if (b_n_contig) { ni = e % BN; ki = e / BN; }
+            else { ni = e / BK; ki = e % BK; }
+            const int n = n0 + ni, k = k0 + ki;
+            double2 v = make_double2(0.0, 0.0);
+            if (n < g.N && k < kend) {
+                v = ld_c<TB>(B.p, (int64_t)k * B.s0 + (int64_t)n * B.s1);
+                if (B.conj) v.y = -v.y;
+            }
+            Bs[pr][ki][ni] = v;
+        }
+    }
+}
+
+template <typename TA, typename TB, typename TC, bool DUAL>
+__global__ void __launch_bounds__(256) zgemm_kernel(ZGemm g)
+{
+    __shared__ double2 As[DUAL ? 2 : 1][BK][BM + 1];
+    __shared__ double2 Bs[DUAL ? 2 : 1][BK][BN + 1];
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    if (g.lower_only && m0 + BM <= n0) return;
+    int kb = 0, ke = g.K;
+    if (g.kmode == ZG_K_FROM_MAX_MN) kb = (max(m0, n0) / BK) * BK;
+    else if (g.kmode == ZG_K_FROM_N0) kb = (n0 / BK) * BK;
+    if (g.k_to_m_end) ke = min(ke, m0 + BM);
+    if (g.splits > 1) {
+        const int span = ke - kb;
+        const int chunk = ((span + g.splits - 1) / g.splits + BK - 1) / BK * BK;
+        kb = kb + blockIdx.z * chunk;
+        ke = min(ke, kb + chunk);
+    }
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    double2 acc1[4][4], acc2[DUAL ? 4 : 1][DUAL ? 4 : 1];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc1[i][j] = make_double2(0.0, 0.0);
+    if (DUAL) {
+#pragma unroll
+        for (int i = 0; i < (DUAL ? 4 : 1); ++i)
+#pragma unroll
+            for (int j = 0; j < (DUAL ? 4 : 1); ++j) acc2[i][j] = make_double2(0.0, 0.0);
+    }
+    for (int k0 = kb; k0 < ke; k0 += BK) {
+        load_tiles<TA, TB, DUAL>(g, m0, n0, k0, ke, As, Bs);
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+#pragma unroll
+            for (int pr = 0; pr < (DUAL ? 2 : 1); ++pr) {
+                double2 a[4], b[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) a[i] = As[pr][kk][ty + 16 * i];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) b[j] = Bs[pr][kk][tx + 16 * j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        double2 &c = (DUAL && pr) ? acc2[DUAL ? i : 0][DUAL ? j : 0] : acc1[i][j];
+                        c.x = fma(a[i].x, b[j].x, c.x);
+                        c.x = fma(-a[i].y, b[j].y, c.x);
+                        c.y = fma(a[i].x, b[j].y, c.y);
+                        c.y = fma(a[i].y, b[j].x, c.y);
+                    }
+            }
+        }
+        __syncthreads();
+    }
+    // epilogue
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int m = m0 + ty + 16 * i;
+        if (m >= g.M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int n = n0 + tx + 16 * j;
+            if (n >= g.N) continue;
+            if (g.splits > 1) {
+                g.partial[((int64_t)blockIdx.z * g.M + m) * g.N + n] = acc1[i][j];
+                continue;
+            }
+            const int64_t ci = (int64_t)m * g.scm + (int64_t)n * g.scn;
+            double2 v;
+            if (DUAL) {
+                const double2 p1 = acc1[i][j], p2 = acc2[DUAL ? i : 0][DUAL ? j : 0];
+                v = make_double2(p1.x * p2.x + p1.y * p2.y, p1.y * p2.x - p1.x * p2.y);
+                if (g.C1) static_cast<double2 *>(g.C1)[ci] = p1;
+                if (g.C2) static_cast<double2 *>(g.C2)[ci] = p2;
+            } else {
+                v = make_double2(g.alpha * acc1[i][j].x, g.alpha * acc1[i][j].y);
+                if (g.beta) {
+                    const double2 o = cload(static_cast<const TC *>(g.C), ci);
+                    v.x += o.x;
+                    v.y += o.y;
+                }
+            }
+            cstore(static_cast<TC *>(g.C), ci, v);
+        }
+    }
+}
+
+template <typename TC>
+__global__ void splitk_reduce(ZGemm g)
+{
+    const int64_t total = (int64_t)g.M * g.N;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int m = (int)(e / g.N), n = (int)(e % g.N);
+        if (g.lower_only && (m / BM) < (n / BN)) continue;
+        double2 s = make_double2(0.0, 0.0);
+        for (int z = 0; z < g.splits; ++z) {
+            const double2 v = g.partial[(int64_t)z * total + e];
+            s.x += v.x;
+            s.y += v.y;
+        }
+        const int64_t ci = (int64_t)m * g.scm + (int64_t)n * g.scn;
+        double2 v = make_double2(g.alpha * s.x, g.alpha * s.y);
+        if (g.beta) {
+            const double2 o = cload(static_cast<const TC *>(g.C), ci);
+            v.x += o.x;
+            v.y += o.y;
+        }
+        cstore(static_cast<TC *>(g.C), ci, v);
+    }
+}
+
+template <typename TA, typename TB, typename TC, bool DUAL>
+isdf_status launch(const ZGemm &g, cudaStream_t st)
+{
+    const int splits = g.splits > 1 ? g.splits : 1;
+    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, splits);
+    if (grid.y > 65535u) return ISDF_ERR_UNSUPPORTED;
+    zgemm_kernel<TA, TB, TC, DUAL><<<grid, 256, 0, st>>>(g);
+    ISDF_LAUNCH_CHECK();
+    if (splits > 1) {
+        const int64_t total = (int64_t)g.M * g.N;
+        const unsigned gr = (unsigned)((total + 255) / 256 < 8192 ? (total + 255) / 256 : 8192);
+        splitk_reduce<TC><<<gr, 256, 0, st>>>(g);
+        ISDF_LAUNCH_CHECK();
+    }
+    return ISDF_OK;
+}
+
+__global__ void mirror_kernel(double2 *C, int n, int64_t ld)
+{
+    const int64_t total = (int64_t)n * n;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / n), j = (int)(e % n);
+        if (j > i) {
+            const double2 v = C[(int64_t)j * ld + i];
+            C[(int64_t)i * ld + j] = make_double2(v.x, -v.y);
+        }
+    }
+}
+
+}  // namespace
+
+isdf_status zgemm(const ZGemm &g, cudaStream_t st)
+{
+    if (g.M <= 0 || g.N <= 0) return ISDF_OK;
+    if (g.splits > 1 && (g.dual || !g.partial)) return ISDF_ERR_INVALID_ARG;
+    const int a = g.A1.type, b = g.B1.type, c = g.ctype;
+    if (g.dual) {
+        if (g.A2.type != a || g.B2.type != b || c != ZG_C128 || b != ZG_C128) return ISDF_ERR_UNSUPPORTED;
+        if (a == ZG_C128) return launch<double2, double2, double2, true>(g, st);
+        return launch<float2, double2, double2, true>(g, st);
+    }
+    if (a == ZG_C128 && b == ZG_C128 && c == ZG_C128) return launch<double2, double2, double2, false>(g, st);
+    if (a == ZG_C64 && b == ZG_C128 && c == ZG_C128) return launch<float2, double2, double2, false>(g, st);
+    if (a == ZG_C128 && b == ZG_C64 && c == ZG_C128) return launch<double2, float2, double2, false>(g, st);
+    if (a == ZG_C128 && b == ZG_C128 && c == ZG_C64) return launch<double2, double2, float2, false>(g, st);
+    return ISDF_ERR_UNSUPPORTED;
+}
+
+isdf_status hermitian_mirror(double2 *C, int n, int64_t ld, cudaStream_t st)
+{
+    const int64_t total = (int64_t)n * n;
+    const unsigned gr = (unsigned)((total + 255) / 256 < 8192 ? (total + 255) / 256 : 8192);
+    mirror_kernel<<<gr, 256, 0, st>>>(C, n, ld);
+    ISDF_LAUNCH_CHECK();
+    return ISDF_OK;
+}
