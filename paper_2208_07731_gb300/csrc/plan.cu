@@ -329,12 +329,12 @@ extern "C" isdf_status isdf_fit_theta_backward(isdf_plan *p, int64_t row_begin, 
     if (row_count == 0) return ISDF_OK;
     cudaStream_t st = as_stream(stream);
     p->last_stream = st;
-    if (p->mode == ISDF_MIXED)
-        return mixed_backward(p, row_begin, row_count, grad_theta, ld_grad, K, dV, grad_phi, ld_gphi, grad_psi,
-                              ld_gpsi, loss, st);
+    // the adjoint runs on the FP64 kernels in both modes; in ISDF_MIXED mode
+    // grad_theta is complex64 like the mixed-mode Theta
     const int nm = p->n_mu;
     const int t = p->dtype == ISDF_C128 ? ZG_C128 : ZG_C64;
     const size_t es = p->dtype == ISDF_C128 ? 16 : 8;
+    if (!p->blkT) ISDF_TRY(alloc(&p->blkT, (size_t)p->max_rows * nm));
     if (!p->blkA) {
         ISDF_TRY(alloc(&p->blkA, (size_t)p->max_rows * nm));
         ISDF_TRY(alloc(&p->blkB, (size_t)p->max_rows * nm));
@@ -352,8 +352,9 @@ extern "C" isdf_status isdf_fit_theta_backward(isdf_plan *p, int64_t row_begin, 
         int gtype;
         int64_t ldg;
         if (grad_theta) {
-            G = static_cast<const char *>(grad_theta) + (r0 - row_begin) * ld_grad * 16;
-            gtype = ZG_C128;
+            const size_t ges = p->mode == ISDF_MIXED ? 8 : 16;
+            G = static_cast<const char *>(grad_theta) + (r0 - row_begin) * ld_grad * ges;
+            gtype = p->mode == ISDF_MIXED ? ZG_C64 : ZG_C128;
             ldg = ld_grad;
         } else {
             // G = 2 dV Theta conj(K)
@@ -448,6 +449,12 @@ extern "C" isdf_status isdf_plan_status(isdf_plan *p, int32_t *detail)
     DeviceStatus h{0, 0};
     ISDF_CUDA_TRY(cudaMemcpy(&h, p->status, sizeof(h), cudaMemcpyDeviceToHost));
     if (detail) *detail = h.detail;
+    if (h.code == 0) {
+        int32_t m = 0;
+        ISDF_TRY(mixed_status(p, &m));
+        if (m && detail) *detail = -1;
+        return (isdf_status)m;
+    }
     return (isdf_status)h.code;
 }
 
