@@ -1,0 +1,393 @@
+#!/usr/bin/env python
+"""ISDF decompositions per second on GB300: weights -> weighted K-means ->
+interpolation-vector fit, on seeded synthetic plane-wave orbitals.
+
+    python bench.py [--gpus N --steps K --warmup W] [--workload medium] [--impl reference]
+
+A step is one full decomposition (all steps of the hot path) of one orbital
+pair that is already resident in HBM: the weight function, T Lloyd
+iterations with the final snap, the plan update (gather, M, Cholesky, M^-1)
+and Theta for every grid row. Both precision modes run on the same workload:
+the headline `value` is the tensor-core (split-FP16) path, the `fp64` object
+is the plain FP64 GPU path, each with its Theta error against the other.
+Under torchrun every rank decomposes its own orbital pair (independent
+problems, no data-path collective); `value` counts all ranks' decompositions.
+
+`--impl reference` times the CPU FP64 oracle (the reference for this method)
+on the host cores, on a bounded sample of the same workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ISDF decompositions/sec (K-means+Θ fit), mixed vs FP64 at stated Θ error"
+UNIT = "decompositions/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="medium")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path measurement")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    return ap.parse_args()
+
+
+def algorithmic_flops(w):
+    """Per-row algorithmic FLOPs of the two GEMM kernels (real flops of the complex products)."""
+    return {"gram": 16.0 * w.n_orb * w.n_mu, "apply": 8.0 * w.n_mu * w.n_mu}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = [ln.split(",") for ln in open(self.path).read().splitlines() if ln.strip()]
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows if len(r) >= 9 for i in range(4) if "Active" == r[5 + i].strip()})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ CPU oracle (baseline / reference arm)
+def oracle_sample(w, phi_h, psi_h, init, *, km_iters=None, theta_rows=4096, threads=None):
+    """Time the CPU FP64 oracle on a bounded sample of one decomposition and
+    extrapolate to seconds per full decomposition."""
+    import numpy as np
+
+    import oracle as O
+    if threads:
+        os.environ["OMP_NUM_THREADS"] = str(threads)
+    t = {}
+    t0 = time.perf_counter()
+    wt = O.weights(phi_h, psi_h)
+    t["weights"] = time.perf_counter() - t0
+    T_s = km_iters if km_iters is not None else max(1, min(w.iters, 10))
+    t0 = time.perf_counter()
+    km = O.kmeans(wt, (w.n,) * 3, (w.L,) * 3, w.n_mu, init, T_s)
+    # T_s Lloyd updates plus the final pass and snap; scale the updates to T
+    t["kmeans"] = (time.perf_counter() - t0) * (w.iters + 1) / (T_s + 1)
+    idx = km["idx"]
+    t0 = time.perf_counter()
+    phi_mu, psi_mu = O.gather(phi_h, psi_h, idx)
+    L = O.cholesky(O.form_M(phi_mu, psi_mu))
+    t["M_cholesky"] = time.perf_counter() - t0
+    rows = np.arange(0, w.n_r, max(1, w.n_r // theta_rows))[:theta_rows]
+    t0 = time.perf_counter()
+    O.theta_rows(phi_h, psi_h, phi_mu, psi_mu, L, rows)
+    t["theta"] = (time.perf_counter() - t0) * w.n_r / len(rows)
+    total = sum(t.values())
+    sample = (f"weights on all {w.n_r} rows; K-means {T_s} of {w.iters} Lloyd updates (+final pass) on the full "
+              f"grid, scaled to {w.iters}; M and Cholesky in full; Theta on {len(rows)} of {w.n_r} rows, scaled")
+    return total, t, sample
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import numpy as np  # noqa: F401
+    import torch
+
+    import oracle as O
+    from paper_2208_07731_gb300 import workload as W
+    O.load()
+    w = W.WORKLOADS[args.workload]
+    phi, psi = W.make_pair(w)
+    phi_h, psi_h = W.storage(phi, w).numpy(), W.storage(psi, w).numpy()
+    init = W.init_indices(O.weights(phi_h, psi_h), w.n_mu, 1000 + w.seed)
+    per = []
+    sample = ""
+    for i in range(args.warmup + args.steps):
+        total, _, sample = oracle_sample(w, phi_h, psi_h, init, km_iters=2, theta_rows=2048)
+        if i >= args.warmup:
+            per.append(total)
+    sec = statistics.median(per)
+    value = 1.0 / sec
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic plane-wave orbitals (seeded)",
+            "config": {"workload": w.name, "n_r": w.n_r, "n_orb": w.n_orb, "n_mu": w.n_mu, "iters": w.iters,
+                       "orbital_dtype": w.dtype},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    del torch
+    return 0
+
+
+# ------------------------------------------------------------------ GPU path
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2208_07731_gb300 import build
+    build.build()
+    import paper_2208_07731_gb300 as isdf
+    from paper_2208_07731_gb300 import workload as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier_max(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    base = W.WORKLOADS[args.workload]
+    # independent problems per rank (like separate k-points): the seed differs by rank
+    w = W.Workload(base.name, base.n, base.L, base.n_orb, base.n_mu, base.dtype, base.iters, base.ecut,
+                   base.kfrac, base.centres, base.seed + 1000 * rank)
+    phi, psi = W.make_pair(w, device=dev)
+    phi, psi = W.storage(phi, w).contiguous(), W.storage(psi, w).contiguous()
+    shape, cell = (w.n,) * 3, (w.L,) * 3
+    wbuf = torch.empty(w.n_r, dtype=torch.float64, device=dev)
+    isdf.weights(phi, psi, out=wbuf)
+    init = torch.from_numpy(W.init_indices(wbuf.cpu().numpy(), w.n_mu, 1000 + w.seed))
+    ws = torch.empty(isdf.kmeans_workspace_bytes(shape, w.n_mu), dtype=torch.uint8, device=dev)
+    flops = algorithmic_flops(w)
+    pk = peaks()
+
+    def run_mode(mode):
+        theta = torch.empty((w.n_r, w.n_mu), dtype=torch.complex64 if mode == "mixed" else torch.complex128,
+                            device=dev)
+        km0 = isdf.kmeans(wbuf, shape, cell, w.n_mu, init, w.iters, workspace=ws)
+        plan = isdf.Plan(phi, psi, km0["idx"], mode=mode, max_rows=min(w.n_r, 262144))
+
+        def step(p_in=phi, q_in=psi):
+            isdf.weights(p_in, q_in, out=wbuf)
+            km = isdf.kmeans(wbuf, shape, cell, w.n_mu, init, w.iters, workspace=ws, labels=False, objective=False)
+            plan.update(km["idx"])
+            plan.fit_theta(out=theta)
+            return km
+
+        for _ in range(args.warmup):
+            step()
+        plan.check()
+        torch.cuda.synchronize()
+        plan.enable_timing(4096)
+        # per-stage breakdown (one untimed step with events between stages)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        ev[0].record()
+        isdf.weights(phi, psi, out=wbuf)
+        ev[1].record()
+        km = isdf.kmeans(wbuf, shape, cell, w.n_mu, init, w.iters, workspace=ws, labels=False, objective=False)
+        ev[2].record()
+        plan.update(km["idx"])
+        ev[3].record()
+        plan.fit_theta(out=theta)
+        ev[4].record()
+        torch.cuda.synchronize()
+        stages = {k: ev[i].elapsed_time(ev[i + 1]) for i, k in enumerate(["weights", "kmeans", "plan_update",
+                                                                          "fit_theta"])}
+        for kind in ("gram", "apply"):
+            plan.kernel_time(kind)  # reset
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local)
+        clocks.start()
+        l0 = isdf.kernel_launches()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            km = step()
+        e1.record()
+        torch.cuda.synchronize()
+        launches = isdf.kernel_launches() - l0
+        clk = clocks.stop()
+        ms = barrier_max(e0.elapsed_time(e1)) / args.steps
+        kt = {k: plan.kernel_time(k) for k in ("gram", "apply")}
+        plan.check()
+        stats = km["stats"].cpu().tolist()
+        return {"ms": ms, "stages": stages, "kt": kt, "launches": launches // args.steps, "clocks": clk,
+                "theta": theta, "plan": plan, "idx": km["idx"], "stats": stats}
+
+    res = {}
+    res["mixed"] = run_mode("mixed")
+    if not args.no_fp64:
+        res["fp64"] = run_mode("fp64")
+
+    def roof(r, mode):
+        ms_apply, n_apply, rows_apply = r["kt"]["apply"]
+        ms_gram, n_gram, rows_gram = r["kt"]["gram"]
+        out = {}
+        for name, (ms_k, n_k, rows_k) in (("apply", r["kt"]["apply"]), ("gram", r["kt"]["gram"])):
+            if n_k == 0:
+                continue
+            per_launch_flops = flops[name] * rows_k / n_k
+            achieved = per_launch_flops / (ms_k / n_k * 1e-3) / 1e12
+            if mode == "mixed":
+                peak = pk.get("bf16_tflops_sustained", 1700.0)
+                bound, src = "tensor", "measured cuBLAS bf16 sustained (fp16 dense = bf16 dense)"
+            else:
+                peak = 1.25
+                bound, src = "alu", "FP64 pipe, nominal 1.25 TFLOP/s (no FP64 tensor-core MMA on GB300)"
+            out[name] = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None, "peak_source": src,
+                         "launches": n_k, "ms_per_launch": ms_k / n_k,
+                         "algorithmic_flops_per_launch": per_launch_flops}
+        return out
+
+    mixed = res["mixed"]
+    rf = roof(mixed, "mixed")
+    line = {"metric": METRIC, "value": world * 1e3 / mixed["ms"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": mixed["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f16 hi+lo split x3 on tcgen05 (f32 accumulate) for the Gram and M^-1 GEMMs; f64 for weights, "
+                     "K-means decisions, M, Cholesky, M^-1",
+            "data": "synthetic: seeded random plane-wave Bloch orbitals, orthonormalised (no DFT data available)",
+            "config": {"workload": w.name, "grid": f"{w.n}^3", "n_r": w.n_r, "L_bohr": w.L, "n_orb": w.n_orb,
+                       "n_mu": w.n_mu, "lloyd_iters": w.iters, "orbital_dtype": w.dtype, "mode": "mixed",
+                       "l2": f"inputs larger than L2: Phi+Psi {2 * phi.numel() * phi.element_size() / 1e6:.0f} MB, "
+                             f"Theta {w.n_r * w.n_mu * 8 / 1e6:.0f} MB written per step"},
+            "roofline": rf.get("apply"), "roofline_gram": rf.get("gram"),
+            "stages_ms": mixed["stages"], "gpu_launches": mixed["launches"], "clocks": mixed["clocks"],
+            "kmeans_stats": dict(zip(["updates", "near_ties", "empty", "fp64_decided"], mixed["stats"]))}
+    if "fp64" in res:
+        f = res["fp64"]
+        a = mixed["theta"].to(torch.complex128)
+        b = f["theta"]
+        err = (torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)).item()
+        same_idx = bool(torch.equal(mixed["idx"], f["idx"]))
+        rf64 = roof(f, "fp64")
+        line["fp64"] = {"value": world * 1e3 / f["ms"], "unit": UNIT, "ms_per_step": f["ms"],
+                        "roofline": rf64.get("apply"), "roofline_gram": rf64.get("gram"), "stages_ms": f["stages"],
+                        "gpu_launches": f["launches"], "clocks": f["clocks"]}
+        line["theta_rel_err"] = {"mixed_vs_fp64_gpu": err, "same_idx": same_idx}
+        line["speedup_mixed_vs_fp64"] = f["ms"] / mixed["ms"]
+        del a
+
+    # end to end through the public API: pinned host orbitals in, Theta and idx back to pinned host, every step
+    plan = mixed["plan"]
+    ph_h = phi.cpu().pin_memory()
+    qh_h = psi.cpu().pin_memory()
+    th_h = torch.empty(mixed["theta"].shape, dtype=mixed["theta"].dtype).pin_memory()
+    idx_h = torch.empty(w.n_mu, dtype=torch.int64).pin_memory()
+    p_dev, q_dev = torch.empty_like(phi), torch.empty_like(psi)
+    plan_e2e = isdf.Plan(p_dev.copy_(phi), q_dev.copy_(psi), mixed["idx"], mode="mixed",
+                         max_rows=min(w.n_r, 262144))
+    theta_e2e = mixed["theta"]
+
+    def e2e_step():
+        p_dev.copy_(ph_h, non_blocking=True)
+        q_dev.copy_(qh_h, non_blocking=True)
+        isdf.weights(p_dev, q_dev, out=wbuf)
+        km = isdf.kmeans(wbuf, shape, cell, w.n_mu, init, w.iters, workspace=ws, labels=False, objective=False)
+        plan_e2e.update(km["idx"])
+        plan_e2e.fit_theta(out=theta_e2e)
+        th_h.copy_(theta_e2e, non_blocking=True)
+        idx_h.copy_(km["idx"], non_blocking=True)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = barrier_max(e0.elapsed_time(e1)) / args.steps
+    line["e2e"] = {"value": world * 1e3 / e2e_ms, "unit": UNIT, "ms_per_step": e2e_ms,
+                   "h2d_bytes_per_step": 2 * phi.numel() * phi.element_size(),
+                   "d2h_bytes_per_step": th_h.numel() * th_h.element_size() + idx_h.numel() * 8}
+    plan_e2e.close()
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle as O
+        O.load()
+        phi_h, psi_h = phi.cpu().numpy(), psi.cpu().numpy()
+        total, parts, sample = oracle_sample(w, phi_h, psi_h, init.numpy())
+        line["cpu_baseline"] = {"value": 1.0 / total, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": sample, "seconds_by_stage": parts}
+        # Theta error of both GPU modes against the oracle on a row sample
+        idx = mixed["idx"].cpu().numpy()
+        phi_mu, psi_mu = O.gather(phi_h, psi_h, idx)
+        L = O.cholesky(O.form_M(phi_mu, psi_mu))
+        rows = W.subsample_rows(w.n_r, 4096, 2000 + w.seed)
+        ref = O.theta_rows(phi_h, psi_h, phi_mu, psi_mu, L, rows)
+        rt = torch.from_numpy(rows).to(dev)
+        errs = {"mixed_vs_oracle_rows": float(np.linalg.norm(
+            mixed["theta"][rt].cpu().numpy().astype(np.complex128) - ref) / np.linalg.norm(ref))}
+        if "fp64" in res:
+            errs["fp64_vs_oracle_rows"] = float(np.linalg.norm(res["fp64"]["theta"][rt].cpu().numpy() - ref)
+                                                / np.linalg.norm(ref))
+        line.setdefault("theta_rel_err", {}).update(errs)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -187,6 +187,14 @@ ISDF_API isdf_status isdf_fit_theta_backward(isdf_plan *plan, int64_t row_begin,
 ISDF_API isdf_status isdf_fit_theta_backward_finalize(isdf_plan *plan, void *grad_phi, int64_t ld_gphi,
                                              void *grad_psi, int64_t ld_gpsi, void *stream);
 
+/* Recomputes the plan for new interpolation points idx (n_mu distinct
+ * indices) and the current contents of the orbitals it was created with:
+ * gather, M, Cholesky factor and M^-1 (and, in ISDF_MIXED mode, the split
+ * tensor-core operands), reusing the plan's memory. This is the per-step call
+ * of an MD loop where the orbitals and the K-means points change but the
+ * sizes do not. */
+ISDF_API isdf_status isdf_plan_update(isdf_plan *plan, const int64_t *idx, void *stream);
+
 /* Synchronises the plan's last stream and returns the first device-side
  * failure (ISDF_OK, ISDF_ERR_NOT_HPD with *detail = failing pivot index,
  * ISDF_ERR_NONFINITE, ISDF_ERR_TIMEOUT). detail may be NULL. */
@@ -199,6 +207,21 @@ ISDF_API isdf_status isdf_plan_status(isdf_plan *plan, int32_t *detail);
 ISDF_API isdf_status isdf_plan_copy_matrix(const isdf_plan *plan, int32_t which, void *dst, void *stream);
 
 ISDF_API void isdf_plan_destroy(isdf_plan *plan);
+
+/* Benchmark instrumentation.
+ * isdf_plan_enable_timing(plan, capacity): when capacity > 0, the plan records
+ * CUDA events on the launching stream around each launch of its Gram-Hadamard
+ * kernel (kind 0) and its M^-1 application kernel (kind 1), for up to
+ * `capacity` launches per kind; 0 switches timing off.
+ * isdf_plan_kernel_time(plan, kind, &ms, &launches, &rows): waits for those
+ * events and returns the summed kernel time, the number of launches and the
+ * grid rows they processed since the previous query, then resets the count.
+ * isdf_kernel_launches(): number of kernels this library has launched in the
+ * process so far (host-side counter). */
+ISDF_API isdf_status isdf_plan_enable_timing(isdf_plan *plan, int32_t capacity);
+ISDF_API isdf_status isdf_plan_kernel_time(isdf_plan *plan, int32_t kind, double *total_ms, int64_t *launches,
+                                           int64_t *rows);
+ISDF_API unsigned long long isdf_kernel_launches(void);
 
 /* Human-readable name of a status code (static storage). */
 ISDF_API const char *isdf_status_string(isdf_status s);

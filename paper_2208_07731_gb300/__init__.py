@@ -58,12 +58,17 @@ def lib():
         L.isdf_fit_theta_backward_finalize.argtypes = [P, P, I64, P, I64, P]
         L.isdf_plan_status.argtypes = [P, P]
         L.isdf_plan_copy_matrix.argtypes = [P, I32, P, P]
+        L.isdf_plan_update.argtypes = [P, P, P]
+        L.isdf_plan_enable_timing.argtypes = [P, I32]
+        L.isdf_plan_kernel_time.argtypes = [P, I32, P, P, P]
+        L.isdf_kernel_launches.argtypes = []
+        L.isdf_kernel_launches.restype = ctypes.c_ulonglong
         L.isdf_plan_destroy.argtypes = [P]
         L.isdf_status_string.argtypes = [I32]
         L.isdf_status_string.restype = ctypes.c_char_p
         for f in ("isdf_weights", "isdf_kmeans_workspace", "isdf_kmeans", "isdf_plan_create", "isdf_fit_theta",
                   "isdf_fit_theta_backward", "isdf_fit_theta_backward_finalize", "isdf_plan_status",
-                  "isdf_plan_copy_matrix"):
+                  "isdf_plan_copy_matrix", "isdf_plan_update", "isdf_plan_enable_timing", "isdf_plan_kernel_time"):
             getattr(L, f).restype = ctypes.c_int32
         _lib = L
     return _lib
@@ -193,6 +198,23 @@ class Plan:
         _check(lib().isdf_plan_copy_matrix(self._h, code, _ptr(out), _stream(stream)), "isdf_plan_copy_matrix")
         return out
 
+    def update(self, idx: torch.Tensor, stream=None):
+        """Recompute the plan for new interpolation points (and the current orbitals) without reallocating."""
+        self.idx = idx.to(device=self.phi.device, dtype=torch.int64).contiguous()
+        if self.idx.numel() != self.n_mu:
+            raise ValueError("update needs the plan's n_mu points")
+        _check(lib().isdf_plan_update(self._h, _ptr(self.idx), _stream(stream)), "isdf_plan_update")
+
+    def enable_timing(self, capacity: int = 4096):
+        _check(lib().isdf_plan_enable_timing(self._h, int(capacity)), "isdf_plan_enable_timing")
+
+    def kernel_time(self, kind: str):
+        """(total ms, launches, rows) of the timed 'gram' or 'apply' launches since the last query."""
+        ms, n, rows = ctypes.c_double(0), ctypes.c_int64(0), ctypes.c_int64(0)
+        _check(lib().isdf_plan_kernel_time(self._h, {"gram": 0, "apply": 1}[kind], ctypes.byref(ms), ctypes.byref(n),
+                                           ctypes.byref(rows)), "isdf_plan_kernel_time")
+        return ms.value, n.value, rows.value
+
     def fit_theta(self, row_begin: int = 0, row_count: int | None = None, out=None, stream=None):
         if row_count is None:
             row_count = self.n_r - row_begin
@@ -224,6 +246,11 @@ class Plan:
         _check(lib().isdf_fit_theta_backward_finalize(self._h, _ptr(grad_phi), grad_phi.stride(0), _ptr(grad_psi),
                                                       grad_psi.stride(0), _stream(stream)),
                "isdf_fit_theta_backward_finalize")
+
+
+def kernel_launches() -> int:
+    """Kernels launched by libisdf in this process so far."""
+    return int(lib().isdf_kernel_launches())
 
 
 def decompose(phi, psi, shape, cell, n_mu, init_idx, iters, mode="fp64", kind="ssm", alpha=2.0,

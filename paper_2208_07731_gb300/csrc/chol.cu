@@ -153,7 +153,7 @@ isdf_status cholesky_inverse(const double2 *M0, double2 *L, double2 *Linv, doubl
     ISDF_CUDA_TRY(cudaMemsetAsync(Linv, 0, sizeof(double2) * (size_t)n * n, stream));
     for (int k = 0; k < n; k += NB) {
         const int nb = n - k < NB ? n - k : NB;
-        potrf_diag<<<1, 256, 0, stream>>>(L, ld, M0, Linv, ld, k, nb, st);
+        potrf_diag<<<1, 256, 0, stream>>>(L, ld, M0, Linv, ld, k, nb, st); isdf_note_launch();
         ISDF_LAUNCH_CHECK();
         const int rest = n - k - nb;
         if (rest <= 0) break;
@@ -171,7 +171,7 @@ isdf_status cholesky_inverse(const double2 *M0, double2 *L, double2 *Linv, doubl
     {
         const int64_t total = (int64_t)n * n;
         const unsigned gr = (unsigned)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
-        zero_strict_upper<<<gr, 256, 0, stream>>>(L, n, ld);
+        zero_strict_upper<<<gr, 256, 0, stream>>>(L, n, ld); isdf_note_launch();
         ISDF_LAUNCH_CHECK();
     }
     ISDF_TRY(tri_inv(L, Linv, tmp, ld, 0, n, stream));

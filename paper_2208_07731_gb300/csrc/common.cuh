@@ -25,6 +25,9 @@
         if (s_ != ISDF_OK) return s_;                         \
     } while (0)
 
+// host-side count of the kernels this library has launched (for benchmarks)
+void isdf_note_launch();
+
 static inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
 static inline bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }

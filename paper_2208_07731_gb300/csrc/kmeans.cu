@@ -569,18 +569,18 @@ extern "C" isdf_status isdf_kmeans(const double *w, int32_t nx, int32_t ny, int3
                                        (int)(sizeof(float4) * kMaxMu)));
     const int64_t nmax = n_r > n_mu ? n_r : n_mu;
     const unsigned ginit = (unsigned)((nmax + 255) / 256 < 4096 ? (nmax + 255) / 256 : 4096);
-    km_init<<<ginit, 256, 0, st>>>(a, init_idx, n_r);
-    km_wmax<<<(unsigned)((n_r + 255) / 256 < 1024 ? (n_r + 255) / 256 : 1024), 256, 0, st>>>(a, n_r);
-    km_check_scale<<<1, 32, 0, st>>>(a);
+    km_init<<<ginit, 256, 0, st>>>(a, init_idx, n_r); isdf_note_launch();
+    km_wmax<<<(unsigned)((n_r + 255) / 256 < 1024 ? (n_r + 255) / 256 : 1024), 256, 0, st>>>(a, n_r); isdf_note_launch();
+    km_check_scale<<<1, 32, 0, st>>>(a); isdf_note_launch();
     ISDF_LAUNCH_CHECK();
     const unsigned gmu = (unsigned)((n_mu + 255) / 256);
     for (int t = 0; t < max_iter; ++t) {
-        km_assign<false><<<n_tiles, kThreads, smem, st>>>(a, t);
-        km_update<<<gmu, 256, 0, st>>>(a, t, n_tiles, objective);
+        km_assign<false><<<n_tiles, kThreads, smem, st>>>(a, t); isdf_note_launch();
+        km_update<<<gmu, 256, 0, st>>>(a, t, n_tiles, objective); isdf_note_launch();
     }
-    km_assign<true><<<n_tiles, kThreads, smem, st>>>(a, max_iter);
-    km_snap<<<(unsigned)((n_r + 255) / 256 < 4096 ? (n_r + 255) / 256 : 4096), 256, 0, st>>>(a, n_r);
-    km_finish<<<1, 256, 0, st>>>(a, max_iter, n_tiles, idx, centroids, objective, stats);
+    km_assign<true><<<n_tiles, kThreads, smem, st>>>(a, max_iter); isdf_note_launch();
+    km_snap<<<(unsigned)((n_r + 255) / 256 < 4096 ? (n_r + 255) / 256 : 4096), 256, 0, st>>>(a, n_r); isdf_note_launch();
+    km_finish<<<1, 256, 0, st>>>(a, max_iter, n_tiles, idx, centroids, objective, stats); isdf_note_launch();
     ISDF_LAUNCH_CHECK();
     return ISDF_OK;
 }

@@ -357,7 +357,7 @@ bool mixed_supported(int n, int n_mu, int64_t, int64_t, int)
     return n % 32 == 0 && n_mu % 64 == 0 && n >= 32 && n_mu >= 64;
 }
 
-isdf_status mixed_prepare(isdf_plan *p, cudaStream_t st)
+static isdf_status mixed_alloc(isdf_plan *p)
 {
     MixedBuffers *b = static_cast<MixedBuffers *>(calloc(1, sizeof(MixedBuffers)));
     if (!b) return ISDF_ERR_CUDA;
@@ -377,40 +377,6 @@ isdf_status mixed_prepare(isdf_plan *p, cudaStream_t st)
     ISDF_TRY(halloc(&b->yh, (size_t)p->max_rows * 2 * nm));
     ISDF_TRY(halloc(&b->yl, (size_t)p->max_rows * 2 * nm));
     ISDF_TRY(halloc(&b->sc, 1));
-    ISDF_CUDA_TRY(cudaMemsetAsync(b->sc, 0, sizeof(MixScales), st));
-
-    const unsigned g = 152 * 8;
-    if (p->dtype == ISDF_C128) {
-        absmax_rows<double2><<<g, 256, 0, st>>>(static_cast<const double2 *>(p->phi), p->ld_phi, n, p->n_r,
-                                                &b->sc->maxabs_phi, &b->sc->maxrho_phi);
-        absmax_rows<double2><<<g, 256, 0, st>>>(static_cast<const double2 *>(p->psi), p->ld_psi, n, p->n_r,
-                                                &b->sc->maxabs_psi, &b->sc->maxrho_psi);
-    } else {
-        absmax_rows<float2><<<g, 256, 0, st>>>(static_cast<const float2 *>(p->phi), p->ld_phi, n, p->n_r,
-                                               &b->sc->maxabs_phi, &b->sc->maxrho_phi);
-        absmax_rows<float2><<<g, 256, 0, st>>>(static_cast<const float2 *>(p->psi), p->ld_psi, n, p->n_r,
-                                               &b->sc->maxabs_psi, &b->sc->maxrho_psi);
-    }
-    absmax_rows<double2><<<grid_for((int64_t)nm * 32), 256, 0, st>>>(p->W, nm, nm, nm, &b->sc->maxabs_w, nullptr);
-    compute_scales<<<1, 1, 0, st>>>(b->sc);
-    ISDF_LAUNCH_CHECK();
-    const int64_t tot = p->n_r * n;
-    if (p->dtype == ISDF_C128) {
-        split_orbitals<double2><<<grid_for(tot, 152 * 64), 256, 0, st>>>(
-            static_cast<const double2 *>(p->phi), p->ld_phi, n, p->n_r, &b->sc->s_phi, b->a1h, b->a1l);
-        split_orbitals<double2><<<grid_for(tot, 152 * 64), 256, 0, st>>>(
-            static_cast<const double2 *>(p->psi), p->ld_psi, n, p->n_r, &b->sc->s_psi, b->a2h, b->a2l);
-    } else {
-        split_orbitals<float2><<<grid_for(tot, 152 * 64), 256, 0, st>>>(
-            static_cast<const float2 *>(p->phi), p->ld_phi, n, p->n_r, &b->sc->s_phi, b->a1h, b->a1l);
-        split_orbitals<float2><<<grid_for(tot, 152 * 64), 256, 0, st>>>(
-            static_cast<const float2 *>(p->psi), p->ld_psi, n, p->n_r, &b->sc->s_psi, b->a2h, b->a2l);
-    }
-    build_rotated<<<grid_for((int64_t)nm * n), 256, 0, st>>>(p->phi_mu, n, nm, n, &b->sc->s_phi, b->b1h, b->b1l);
-    build_rotated<<<grid_for((int64_t)nm * n), 256, 0, st>>>(p->psi_mu, n, nm, n, &b->sc->s_psi, b->b2h, b->b2l);
-    build_rotated<<<grid_for((int64_t)nm * nm), 256, 0, st>>>(p->W, nm, nm, nm, &b->sc->s_w, b->bwh, b->bwl);
-    ISDF_LAUNCH_CHECK();
-
     bool ok = true;
     ok &= make_map(&b->m_a1h, b->a1h, 2 * n, p->n_r);
     ok &= make_map(&b->m_a1l, b->a1l, 2 * n, p->n_r);
@@ -427,6 +393,47 @@ isdf_status mixed_prepare(isdf_plan *p, cudaStream_t st)
     if (!ok) return ISDF_ERR_CUDA;
     ISDF_CUDA_TRY(cudaFuncSetAttribute(tc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     ISDF_CUDA_TRY(cudaFuncSetAttribute(tc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    return ISDF_OK;
+}
+
+isdf_status mixed_prepare(isdf_plan *p, cudaStream_t st)
+{
+    if (!p->mixed) ISDF_TRY(mixed_alloc(p));
+    MixedBuffers *b = p->mixed;
+    const int n = p->n_phi, nm = p->n_mu;
+    ISDF_CUDA_TRY(cudaMemsetAsync(b->sc, 0, sizeof(MixScales), st));
+
+    const unsigned g = 152 * 8;
+    if (p->dtype == ISDF_C128) {
+        absmax_rows<double2><<<g, 256, 0, st>>>(static_cast<const double2 *>(p->phi), p->ld_phi, n, p->n_r,
+                                                &b->sc->maxabs_phi, &b->sc->maxrho_phi); isdf_note_launch();
+        absmax_rows<double2><<<g, 256, 0, st>>>(static_cast<const double2 *>(p->psi), p->ld_psi, n, p->n_r,
+                                                &b->sc->maxabs_psi, &b->sc->maxrho_psi); isdf_note_launch();
+    } else {
+        absmax_rows<float2><<<g, 256, 0, st>>>(static_cast<const float2 *>(p->phi), p->ld_phi, n, p->n_r,
+                                               &b->sc->maxabs_phi, &b->sc->maxrho_phi); isdf_note_launch();
+        absmax_rows<float2><<<g, 256, 0, st>>>(static_cast<const float2 *>(p->psi), p->ld_psi, n, p->n_r,
+                                               &b->sc->maxabs_psi, &b->sc->maxrho_psi); isdf_note_launch();
+    }
+    absmax_rows<double2><<<grid_for((int64_t)nm * 32), 256, 0, st>>>(p->W, nm, nm, nm, &b->sc->maxabs_w, nullptr); isdf_note_launch();
+    compute_scales<<<1, 1, 0, st>>>(b->sc); isdf_note_launch();
+    ISDF_LAUNCH_CHECK();
+    const int64_t tot = p->n_r * n;
+    if (p->dtype == ISDF_C128) {
+        split_orbitals<double2><<<grid_for(tot, 152 * 64), 256, 0, st>>>(
+            static_cast<const double2 *>(p->phi), p->ld_phi, n, p->n_r, &b->sc->s_phi, b->a1h, b->a1l); isdf_note_launch();
+        split_orbitals<double2><<<grid_for(tot, 152 * 64), 256, 0, st>>>(
+            static_cast<const double2 *>(p->psi), p->ld_psi, n, p->n_r, &b->sc->s_psi, b->a2h, b->a2l); isdf_note_launch();
+    } else {
+        split_orbitals<float2><<<grid_for(tot, 152 * 64), 256, 0, st>>>(
+            static_cast<const float2 *>(p->phi), p->ld_phi, n, p->n_r, &b->sc->s_phi, b->a1h, b->a1l); isdf_note_launch();
+        split_orbitals<float2><<<grid_for(tot, 152 * 64), 256, 0, st>>>(
+            static_cast<const float2 *>(p->psi), p->ld_psi, n, p->n_r, &b->sc->s_psi, b->a2h, b->a2l); isdf_note_launch();
+    }
+    build_rotated<<<grid_for((int64_t)nm * n), 256, 0, st>>>(p->phi_mu, n, nm, n, &b->sc->s_phi, b->b1h, b->b1l); isdf_note_launch();
+    build_rotated<<<grid_for((int64_t)nm * n), 256, 0, st>>>(p->psi_mu, n, nm, n, &b->sc->s_psi, b->b2h, b->b2l); isdf_note_launch();
+    build_rotated<<<grid_for((int64_t)nm * nm), 256, 0, st>>>(p->W, nm, nm, nm, &b->sc->s_w, b->bwh, b->bwl); isdf_note_launch();
+    ISDF_LAUNCH_CHECK();
     return ISDF_OK;
 }
 
@@ -447,14 +454,18 @@ isdf_status mixed_fit(isdf_plan *p, int64_t row_begin, int64_t row_count, void *
         ep.err = err;
         dim3 grid((2 * nm) / TN, (rows + TM - 1) / TM);
         // a10: Y_b = (Phi_b Phi_mu^H) o conj(Psi_b Psi_mu^H), written split for the next GEMM
+        timer_start(p, 0, st);
         tc_gemm<true><<<grid, 128, SMEM_BYTES, st>>>(b->m_a1h, b->m_a1l, b->m_b1h, b->m_b1l, b->m_a2h, b->m_a2l,
-                                                     b->m_b2h, b->m_b2l, (2 * n) / TK, (int)r0, rows, ep);
+                                                     b->m_b2h, b->m_b2l, (2 * n) / TK, (int)r0, rows, ep); isdf_note_launch();
+        timer_stop(p, 0, st, rows);
         ISDF_LAUNCH_CHECK();
         // a11: Theta_b = Y_b M^-1
         ep.theta = static_cast<float2 *>(theta) + (r0 - row_begin) * ld_theta;
         ep.ld_theta = ld_theta;
+        timer_start(p, 1, st);
         tc_gemm<false><<<grid, 128, SMEM_BYTES, st>>>(b->m_yh, b->m_yl, b->m_bwh, b->m_bwl, b->m_yh, b->m_yl,
-                                                      b->m_bwh, b->m_bwl, (2 * nm) / TK, 0, rows, ep);
+                                                      b->m_bwh, b->m_bwl, (2 * nm) / TK, 0, rows, ep); isdf_note_launch();
+        timer_stop(p, 1, st, rows);
         ISDF_LAUNCH_CHECK();
     }
     return ISDF_OK;

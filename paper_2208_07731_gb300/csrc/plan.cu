@@ -169,6 +169,49 @@ isdf_status gram_hadamard_fp64(isdf_plan *p, int64_t r0, int rows, double2 *Y, d
     return zgemm(g, st);
 }
 
+// a7-a9 for the current orbitals and interpolation points (no allocation)
+isdf_status plan_compute(isdf_plan *p, const int64_t *idx, cudaStream_t st)
+{
+    const int n_mu = p->n_mu, n_phi = p->n_phi, n_psi = p->n_psi;
+    const size_t nn = (size_t)n_mu * n_mu;
+    ISDF_CUDA_TRY(cudaMemsetAsync(p->status, 0, sizeof(DeviceStatus), st));
+    ISDF_CUDA_TRY(cudaMemcpyAsync(p->idx, idx, sizeof(int64_t) * n_mu, cudaMemcpyDeviceToDevice, st));
+    ISDF_CUDA_TRY(cudaMemsetAsync(p->Mbar, 0, sizeof(double2) * nn, st));
+    ISDF_CUDA_TRY(cudaMemsetAsync(p->gphi_mu, 0, sizeof(double2) * n_mu * n_phi, st));
+    ISDF_CUDA_TRY(cudaMemsetAsync(p->gpsi_mu, 0, sizeof(double2) * n_mu * n_psi, st));
+    // a7: Phi_mu = Phi[idx], Psi_mu = Psi[idx]  (Eq. Cmu)
+    gather_rows<<<grid_for((int64_t)n_mu * n_phi), 256, 0, st>>>(p->phi, p->ld_phi, p->dtype, n_phi, p->idx, n_mu,
+                                                                 p->n_r, p->phi_mu, p->status); isdf_note_launch();
+    gather_rows<<<grid_for((int64_t)n_mu * n_psi), 256, 0, st>>>(p->psi, p->ld_psi, p->dtype, n_psi, p->idx, n_mu,
+                                                                 p->n_r, p->psi_mu, p->status); isdf_note_launch();
+    ISDF_LAUNCH_CHECK();
+    // a8: M = (Phi_mu Phi_mu^H) o conj(Psi_mu Psi_mu^H), FP64, lower tiles then mirrored
+    ZGemm g{};
+    g.M = n_mu;
+    g.N = n_mu;
+    g.K = n_phi;
+    g.dual = 1;
+    g.A1 = opnd(p->phi_mu, n_phi, 1, 0, ZG_C128);
+    g.B1 = opnd(p->phi_mu, 1, n_phi, 1, ZG_C128);
+    g.A2 = opnd(p->psi_mu, n_psi, 1, 0, ZG_C128);
+    g.B2 = opnd(p->psi_mu, 1, n_psi, 1, ZG_C128);
+    g.C = p->M;
+    g.scm = n_mu;
+    g.scn = 1;
+    g.ctype = ZG_C128;
+    g.C1 = p->Amu;
+    g.C2 = p->Bmu;
+    g.lower_only = 1;
+    g.splits = 1;
+    ISDF_TRY(zgemm(g, st));
+    for (double2 *m : {p->M, p->Amu, p->Bmu}) ISDF_TRY(hermitian_mirror(m, n_mu, n_mu, st));
+    // a9: M = L L^H, L^-1, M^-1 (FP64)
+    ISDF_CUDA_TRY(cudaMemcpyAsync(p->L, p->M, sizeof(double2) * nn, cudaMemcpyDeviceToDevice, st));
+    ISDF_TRY(cholesky_inverse(p->M, p->L, p->Linv, p->W, p->tmp, n_mu, p->status, st));
+    if (p->mode == ISDF_MIXED) ISDF_TRY(mixed_prepare(p, st));
+    return ISDF_OK;
+}
+
 }  // namespace
 
 extern "C" isdf_status isdf_plan_create(isdf_plan **plan, const void *phi, int64_t ld_phi, const void *psi,
@@ -235,57 +278,11 @@ extern "C" isdf_status isdf_plan_create(isdf_plan **plan, const void *phi, int64
     if (mode == ISDF_FP64) {
         PLAN_ALLOC(p->blkT, blk);
     }
-    p->partial_elems = 64 * (size_t)n_mu * (n_mu > n_phi ? n_mu : n_phi);
+    // split-K is used only while tiles * splits < 2 * 304, so 608 tiles of 64 x 64 bound the partials
+    p->partial_elems = (size_t)608 * 64 * 64;
     PLAN_ALLOC(p->partial, p->partial_elems);
 #undef PLAN_ALLOC
-    ISDF_CUDA_TRY(cudaMemsetAsync(p->status, 0, sizeof(DeviceStatus), st));
-    ISDF_CUDA_TRY(cudaMemcpyAsync(p->idx, idx, sizeof(int64_t) * n_mu, cudaMemcpyDeviceToDevice, st));
-    ISDF_CUDA_TRY(cudaMemsetAsync(p->Mbar, 0, sizeof(double2) * nn, st));
-    ISDF_CUDA_TRY(cudaMemsetAsync(p->gphi_mu, 0, sizeof(double2) * n_mu * n_phi, st));
-    ISDF_CUDA_TRY(cudaMemsetAsync(p->gpsi_mu, 0, sizeof(double2) * n_mu * n_psi, st));
-
-    // a7: Phi_mu = Phi[idx], Psi_mu = Psi[idx]  (Eq. Cmu)
-    gather_rows<<<grid_for((int64_t)n_mu * n_phi), 256, 0, st>>>(phi, ld_phi, dtype, n_phi, p->idx, n_mu, n_r,
-                                                                 p->phi_mu, p->status);
-    gather_rows<<<grid_for((int64_t)n_mu * n_psi), 256, 0, st>>>(psi, ld_psi, dtype, n_psi, p->idx, n_mu, n_r,
-                                                                 p->psi_mu, p->status);
-    ISDF_LAUNCH_CHECK();
-    // a8: M = (Phi_mu Phi_mu^H) o conj(Psi_mu Psi_mu^H), FP64, lower tiles then mirrored
-    {
-        ZGemm g{};
-        g.M = n_mu;
-        g.N = n_mu;
-        g.K = n_phi;
-        g.dual = 1;
-        g.A1 = opnd(p->phi_mu, n_phi, 1, 0, ZG_C128);
-        g.B1 = opnd(p->phi_mu, 1, n_phi, 1, ZG_C128);
-        g.A2 = opnd(p->psi_mu, n_psi, 1, 0, ZG_C128);
-        g.B2 = opnd(p->psi_mu, 1, n_psi, 1, ZG_C128);
-        g.C = p->M;
-        g.scm = n_mu;
-        g.scn = 1;
-        g.ctype = ZG_C128;
-        g.C1 = p->Amu;
-        g.C2 = p->Bmu;
-        g.lower_only = 1;
-        g.splits = 1;
-        if ((s = zgemm(g, st)) != ISDF_OK) {
-            isdf_plan_destroy(p);
-            return s;
-        }
-        for (double2 *m : {p->M, p->Amu, p->Bmu})
-            if ((s = hermitian_mirror(m, n_mu, n_mu, st)) != ISDF_OK) {
-                isdf_plan_destroy(p);
-                return s;
-            }
-    }
-    // a9: M = L L^H, L^-1, M^-1 (FP64)
-    ISDF_CUDA_TRY(cudaMemcpyAsync(p->L, p->M, sizeof(double2) * nn, cudaMemcpyDeviceToDevice, st));
-    if ((s = cholesky_inverse(p->M, p->L, p->Linv, p->W, p->tmp, n_mu, p->status, st)) != ISDF_OK) {
-        isdf_plan_destroy(p);
-        return s;
-    }
-    if (mode == ISDF_MIXED && (s = mixed_prepare(p, st)) != ISDF_OK) {
+    if ((s = plan_compute(p, idx, st)) != ISDF_OK) {
         isdf_plan_destroy(p);
         return s;
     }
@@ -306,12 +303,16 @@ extern "C" isdf_status isdf_fit_theta(isdf_plan *p, int64_t row_begin, int64_t r
     for (int64_t r0 = row_begin; r0 < row_begin + row_count; r0 += p->max_rows) {
         const int rows = (int)((row_begin + row_count - r0) < p->max_rows ? (row_begin + row_count - r0) : p->max_rows);
         // a10: Y_b = (Phi_b Phi_mu^H) o conj(Psi_b Psi_mu^H)
+        timer_start(p, 0, st);
         ISDF_TRY(gram_hadamard_fp64(p, r0, rows, p->blkY, nullptr, nullptr, st));
+        timer_stop(p, 0, st, rows);
         // a11: Theta_b = Y_b M^-1
         double2 *out = static_cast<double2 *>(theta) + (r0 - row_begin) * ld_theta;
         ZGemm g = gemm1(rows, p->n_mu, p->n_mu, opnd(p->blkY, p->n_mu, 1, 0, ZG_C128),
                         opnd(p->W, p->n_mu, 1, 0, ZG_C128), out, ld_theta, ZG_C128, 1.0, 0);
+        timer_start(p, 1, st);
         ISDF_TRY(zgemm(g, st));
+        timer_stop(p, 1, st, rows);
     }
     return ISDF_OK;
 }
@@ -365,7 +366,7 @@ extern "C" isdf_status isdf_fit_theta_backward(isdf_plan *p, int64_t row_begin, 
             ldg = nm;
             if (loss) {
                 surrogate_loss_kernel<double2><<<grid_for((int64_t)rows * nm, 2048), 256, 0, st>>>(
-                    p->blkT, nm, p->blkG, nm, rows, nm, loss);
+                    p->blkT, nm, p->blkG, nm, rows, nm, loss); isdf_note_launch();
                 ISDF_LAUNCH_CHECK();
             }
         }
@@ -381,7 +382,7 @@ extern "C" isdf_status isdf_fit_theta_backward(isdf_plan *p, int64_t row_begin, 
             ISDF_TRY(zgemm(g, st));
         }
         // Abar = Ybar o B, Bbar = conj(Ybar) o A
-        hadamard_adjoint<<<grid_for((int64_t)rows * nm), 256, 0, st>>>(p->blkY, p->blkA, p->blkB, (int64_t)rows * nm);
+        hadamard_adjoint<<<grid_for((int64_t)rows * nm), 256, 0, st>>>(p->blkY, p->blkA, p->blkB, (int64_t)rows * nm); isdf_note_launch();
         ISDF_LAUNCH_CHECK();
         // grad_phi[rows] += Abar Phi_mu, grad_psi[rows] += Bbar Psi_mu
         double2 *gp = static_cast<double2 *>(grad_phi) + r0 * ld_gphi;
@@ -416,16 +417,16 @@ isdf_status backward_finalize_common(isdf_plan *p, void *grad_phi, int64_t ld_gp
     const size_t nn = (size_t)nm * nm;
     // X = Abar_mu + Abar_mu^H with Abar_mu = Mbar o B_mu; X2 likewise with Bbar_mu = conj(Mbar) o A_mu
     double2 *X = p->tmp, *X2 = p->tmp2;
-    hermitian_parts<<<grid_for((int64_t)nn), 256, 0, st>>>(p->Mbar, p->Amu, p->Bmu, X, X2, nm);
+    hermitian_parts<<<grid_for((int64_t)nn), 256, 0, st>>>(p->Mbar, p->Amu, p->Bmu, X, X2, nm); isdf_note_launch();
     ISDF_LAUNCH_CHECK();
     ISDF_TRY(zgemm(gemm1(nm, p->n_phi, nm, opnd(X, nm, 1, 0, ZG_C128), opnd(p->phi_mu, p->n_phi, 1, 0, ZG_C128),
                          p->gphi_mu, p->n_phi, ZG_C128, 1.0, 1), st));
     ISDF_TRY(zgemm(gemm1(nm, p->n_psi, nm, opnd(X2, nm, 1, 0, ZG_C128), opnd(p->psi_mu, p->n_psi, 1, 0, ZG_C128),
                          p->gpsi_mu, p->n_psi, ZG_C128, 1.0, 1), st));
     scatter_add_rows<<<grid_for((int64_t)nm * p->n_phi), 256, 0, st>>>(p->gphi_mu, p->n_phi, p->idx, nm,
-                                                                       static_cast<double2 *>(grad_phi), ld_gphi);
+                                                                       static_cast<double2 *>(grad_phi), ld_gphi); isdf_note_launch();
     scatter_add_rows<<<grid_for((int64_t)nm * p->n_psi), 256, 0, st>>>(p->gpsi_mu, p->n_psi, p->idx, nm,
-                                                                       static_cast<double2 *>(grad_psi), ld_gpsi);
+                                                                       static_cast<double2 *>(grad_psi), ld_gpsi); isdf_note_launch();
     ISDF_LAUNCH_CHECK();
     ISDF_CUDA_TRY(cudaMemsetAsync(p->Mbar, 0, sizeof(double2) * nn, st));
     ISDF_CUDA_TRY(cudaMemsetAsync(p->gphi_mu, 0, sizeof(double2) * nm * p->n_phi, st));
@@ -440,6 +441,81 @@ extern "C" isdf_status isdf_fit_theta_backward_finalize(isdf_plan *p, void *grad
     cudaStream_t st = as_stream(stream);
     p->last_stream = st;
     return backward_finalize_common(p, grad_phi, ld_gphi, grad_psi, ld_gpsi, st);
+}
+
+extern "C" isdf_status isdf_plan_update(isdf_plan *p, const int64_t *idx, void *stream)
+{
+    if (!p || !idx) return ISDF_ERR_INVALID_ARG;
+    cudaStream_t st = as_stream(stream);
+    p->last_stream = st;
+    return plan_compute(p, idx, st);
+}
+
+void timer_start(isdf_plan *p, int kind, cudaStream_t st)
+{
+    if (!p->timing || p->tused[kind] >= p->tcap) return;
+    cudaEventRecord(p->tev[kind][2 * p->tused[kind]], st);
+}
+
+void timer_stop(isdf_plan *p, int kind, cudaStream_t st, int64_t rows)
+{
+    if (!p->timing || p->tused[kind] >= p->tcap) return;
+    cudaEventRecord(p->tev[kind][2 * p->tused[kind] + 1], st);
+    p->trows[kind][p->tused[kind]] = rows;
+    p->tused[kind] += 1;
+}
+
+static void timing_free(isdf_plan *p)
+{
+    for (int k = 0; k < 2; ++k) {
+        if (p->tev[k]) {
+            for (int i = 0; i < 2 * p->tcap; ++i) cudaEventDestroy(p->tev[k][i]);
+            free(p->tev[k]);
+            p->tev[k] = nullptr;
+        }
+        free(p->trows[k]);
+        p->trows[k] = nullptr;
+        p->tused[k] = 0;
+    }
+    p->tcap = 0;
+    p->timing = 0;
+}
+
+extern "C" isdf_status isdf_plan_enable_timing(isdf_plan *p, int32_t capacity)
+{
+    if (!p || capacity < 0) return ISDF_ERR_INVALID_ARG;
+    if (p->last_stream) cudaStreamSynchronize(p->last_stream);
+    timing_free(p);
+    if (capacity == 0) return ISDF_OK;
+    p->tcap = capacity;
+    for (int k = 0; k < 2; ++k) {
+        p->tev[k] = static_cast<cudaEvent_t *>(calloc(2 * (size_t)capacity, sizeof(cudaEvent_t)));
+        p->trows[k] = static_cast<int64_t *>(calloc((size_t)capacity, sizeof(int64_t)));
+        if (!p->tev[k] || !p->trows[k]) return ISDF_ERR_CUDA;
+        for (int i = 0; i < 2 * capacity; ++i) ISDF_CUDA_TRY(cudaEventCreate(&p->tev[k][i]));
+    }
+    p->timing = 1;
+    return ISDF_OK;
+}
+
+extern "C" isdf_status isdf_plan_kernel_time(isdf_plan *p, int32_t kind, double *total_ms, int64_t *launches,
+                                             int64_t *rows)
+{
+    if (!p || kind < 0 || kind > 1 || !total_ms || !launches || !rows) return ISDF_ERR_INVALID_ARG;
+    *total_ms = 0.0;
+    *launches = 0;
+    *rows = 0;
+    if (!p->timing) return ISDF_OK;
+    for (int i = 0; i < p->tused[kind]; ++i) {
+        float ms = 0.f;
+        ISDF_CUDA_TRY(cudaEventSynchronize(p->tev[kind][2 * i + 1]));
+        ISDF_CUDA_TRY(cudaEventElapsedTime(&ms, p->tev[kind][2 * i], p->tev[kind][2 * i + 1]));
+        *total_ms += ms;
+        *rows += p->trows[kind][i];
+    }
+    *launches = p->tused[kind];
+    p->tused[kind] = 0;
+    return ISDF_OK;
 }
 
 extern "C" isdf_status isdf_plan_status(isdf_plan *p, int32_t *detail)
@@ -484,5 +560,6 @@ extern "C" void isdf_plan_destroy(isdf_plan *p)
     for (void *b : bufs)
         if (b) cudaFree(b);
     mixed_release(p);
+    timing_free(p);
     free(p);
 }

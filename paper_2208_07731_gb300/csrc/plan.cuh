@@ -22,4 +22,15 @@ struct isdf_plan {
     double2 *partial;                         // split-K partials
     size_t partial_elems;
     MixedBuffers *mixed;                      // tensor-core path (ISDF_MIXED)
+    // optional per-launch event timing of the Gram (0) and M^-1 application (1) kernels
+    int timing;
+    int tcap;
+    int tused[2];
+    cudaEvent_t *tev[2];   // 2 * tcap events per kind: (start, stop) pairs
+    int64_t *trows[2];     // grid rows processed by each timed launch
 };
+
+// record a start event before a timed launch (no-op unless timing is enabled)
+void timer_start(isdf_plan *p, int kind, cudaStream_t st);
+// record the stop event after the launch of `rows` grid rows
+void timer_stop(isdf_plan *p, int kind, cudaStream_t st, int64_t rows);

@@ -123,6 +123,7 @@ isdf_status launch_weights(const void *phi, int64_t ld_phi, int n_phi, const voi
         weights_kernel<T, 4><<<grid, kRows, 0, st>>>(a, ld_phi, n_phi, b, ld_psi, n_psi, n_r, 0, ha, w);
     else
         weights_kernel<T, 0><<<grid, kRows, 0, st>>>(a, ld_phi, n_phi, b, ld_psi, n_psi, n_r, 0, ha, w);
+    isdf_note_launch();
     ISDF_LAUNCH_CHECK();
     return ISDF_OK;
 }
@@ -146,6 +147,12 @@ extern "C" isdf_status isdf_weights(const void *phi, int64_t ld_phi, int32_t n_p
         return launch_weights<double2>(phi, ld_phi, n_phi, psi, ld_psi, n_psi, n_r, kind == ISDF_W_PSM, alpha, w, st);
     return launch_weights<float2>(phi, ld_phi, n_phi, psi, ld_psi, n_psi, n_r, kind == ISDF_W_PSM, alpha, w, st);
 }
+
+static unsigned long long g_launches = 0;
+
+void isdf_note_launch() { __atomic_add_fetch(&g_launches, 1ull, __ATOMIC_RELAXED); }
+
+extern "C" unsigned long long isdf_kernel_launches(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 
 extern "C" const char *isdf_status_string(isdf_status s)
 {

@@ -177,12 +177,12 @@ isdf_status launch(const ZGemm &g, cudaStream_t st)
     const int splits = g.splits > 1 ? g.splits : 1;
     dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, splits);
     if (grid.y > 65535u) return ISDF_ERR_UNSUPPORTED;
-    zgemm_kernel<TA, TB, TC, DUAL><<<grid, 256, 0, st>>>(g);
+    zgemm_kernel<TA, TB, TC, DUAL><<<grid, 256, 0, st>>>(g); isdf_note_launch();
     ISDF_LAUNCH_CHECK();
     if (splits > 1) {
         const int64_t total = (int64_t)g.M * g.N;
         const unsigned gr = (unsigned)((total + 255) / 256 < 8192 ? (total + 255) / 256 : 8192);
-        splitk_reduce<TC><<<gr, 256, 0, st>>>(g);
+        splitk_reduce<TC><<<gr, 256, 0, st>>>(g); isdf_note_launch();
         ISDF_LAUNCH_CHECK();
     }
     return ISDF_OK;
@@ -223,7 +223,7 @@ isdf_status hermitian_mirror(double2 *C, int n, int64_t ld, cudaStream_t st)
 {
     const int64_t total = (int64_t)n * n;
     const unsigned gr = (unsigned)((total + 255) / 256 < 8192 ? (total + 255) / 256 : 8192);
-    mirror_kernel<<<gr, 256, 0, st>>>(C, n, ld);
+    mirror_kernel<<<gr, 256, 0, st>>>(C, n, ld); isdf_note_launch();
     ISDF_LAUNCH_CHECK();
     return ISDF_OK;
 }
