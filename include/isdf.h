@@ -133,6 +133,34 @@ ISDF_API isdf_status isdf_kmeans(const double *w, int32_t nx, int32_t ny, int32_
                         int64_t *stats, void *ws, size_t ws_bytes, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * K-means without allocation (no counterpart in the paper: an interface for
+ * callers that cannot allocate device memory).
+ * Callers inside another framework whose allocator already owns the device
+ * memory, or loops that must not allocate mid-step, cannot call cudaMalloc for
+ * the workspace isdf_kmeans needs. isdf_kmeans_noalloc takes the same
+ * arguments as isdf_kmeans without ws/ws_bytes and computes the same result,
+ * with its workspace in a fixed array of ISDF_KMEANS_NOALLOC_SCRATCH_BYTES
+ * (32 MiB) of device memory that the library holds on every GPU that loads it
+ * until the process exits. It calls no cudaMalloc, cudaFree or other
+ * allocating routine. Inputs and outputs are still the caller's device buffers.
+ *  - Problems whose isdf_kmeans_workspace() exceeds the array size return
+ *    ISDF_ERR_UNSUPPORTED before anything is launched (32 MiB covers a
+ *    128^3 grid with 4096 points).
+ *  - The first call on a device looks up the array's device address with that
+ *    device current (cudaGetSymbolAddress) and keeps it; make that first call
+ *    before any stream capture on the device.
+ *  - Every call, on every stream, uses the same array, and the array keeps the
+ *    last call's contents (each call re-initialises what it reads). Calls that
+ *    overlap on the GPU (different streams, or different host threads without
+ *    ordering) race on the array and give wrong results: order them.
+ * ------------------------------------------------------------------------- */
+#define ISDF_KMEANS_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+ISDF_API isdf_status isdf_kmeans_noalloc(const double *w, int32_t nx, int32_t ny, int32_t nz, const double *cell,
+                                         int32_t n_mu, const int64_t *init_idx, int32_t max_iter, int32_t flags,
+                                         int64_t *idx, double *centroids, double *objective, int32_t *labels,
+                                         int64_t *stats, void *stream);
+
+/* ---------------------------------------------------------------------------
  * Step 3: the interpolation-vector fit (Sec. 2.1, Eq. theta with the
  * Hermitian adjoint for complex orbitals; Eqs. muRownuCol, muRownuColden).
  *
