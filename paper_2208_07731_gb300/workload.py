@@ -12,7 +12,8 @@ not available, so the orbitals here are random plane-wave expansions with the
 paper's grids and cutoffs: coefficients c_iG = (a + i b)/sqrt(2), a, b ~ N(0, 1),
 damped by exp(-|G|^2/4) over the sphere |G|^2/2 <= E_cut, optionally plus
 Gaussian-localised density centres, times the Bloch phase exp(i k.r), then
-orthonormalised (Householder QR with a real positive R diagonal) and scaled
+orthonormalised (the Q of A = QR with a real positive R diagonal, by
+Cholesky-QR applied twice) and scaled
 so that sum_r conj(phi_i) phi_j dV = delta_ij.
 
 Grid convention: n^3 points, linear index r = (ix*n + iy)*n + iz, coordinates
@@ -137,11 +138,25 @@ def make_orbitals(w: Workload, seed_offset: int, device="cpu") -> torch.Tensor:
     ph = [torch.exp(1j * (2.0 * math.pi * kf / n) * idx) for kf in w.kfrac]
     phase = ph[0][:, None, None] * ph[1][None, :, None] * ph[2][None, None, :]
     psi = (psi * phase[None]).reshape(w.n_orb, w.n_r).transpose(0, 1).contiguous()
-    Q, R = torch.linalg.qr(psi)
+    Q = _orthonormalise(psi)
     del psi
-    d = torch.diagonal(R)
-    Q = Q * (d / d.abs())[None, :]
     return (Q / math.sqrt(w.dV)).contiguous()
+
+
+def _orthonormalise(A: torch.Tensor) -> torch.Tensor:
+    """Q of the QR factorisation A = QR with a real positive R diagonal.
+
+    Cholesky-QR applied twice: G = A^H A = R^H R (the small N x N Gram matrix is
+    factored on the host), A <- A R^-1. Only matrix products run on the
+    device, so no GPU linear-algebra library is needed.
+    """
+    for _ in range(2):
+        G = (A.conj().transpose(0, 1) @ A).cpu().numpy()
+        G = 0.5 * (G + G.conj().T)
+        R = np.linalg.cholesky(G).conj().T
+        Rinv = np.linalg.solve(R, np.eye(R.shape[0], dtype=R.dtype))
+        A = A @ torch.from_numpy(np.triu(Rinv)).to(A.device)
+    return A
 
 
 def make_pair(w: Workload, device="cpu"):
