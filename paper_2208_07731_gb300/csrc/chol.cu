@@ -2,7 +2,7 @@
 // normal equations with a linear solver, Sec. 2.4), the inverse of the
 // Cholesky factor and M^-1 = L^-H L^-1.
 //
-// Right-looking Cholesky with 64-wide panels: one CTA factors the diagonal
+// Right-looking Cholesky with 32-wide panels: one CTA factors the diagonal
 // block in shared memory and also inverts it; the panel below is L21 =
 // A21 L11^-H (a GEMM with the inverted diagonal block); the trailing lower
 // triangle is updated by A22 -= L21 L21^H. L^-1 is built recursively from the
@@ -12,12 +12,14 @@
 
 namespace {
 
-constexpr int NB = 64;
+constexpr int NB = 32;    // diagonal block edge
+constexpr int DT = 128;   // threads of the diagonal-block kernel
 
 // Factor the nb x nb diagonal block at (k, k) of A (lower triangle used),
 // write L_kk back (upper part zeroed) and L_kk^-1 into Linv at (k, k).
-__global__ void __launch_bounds__(256) potrf_diag(double2 *A, int64_t lda, const double2 *M0, double2 *Linv,
-                                                 int64_t ldi, int k, int nb, DeviceStatus *st)
+// A pivot not above 1e-13 of M's original diagonal entry (M0) is reported.
+__global__ void __launch_bounds__(DT) potrf_diag(double2 *A, int64_t lda, const double2 *M0, double2 *Linv,
+                                                int64_t ldi, int k, int nb, DeviceStatus *st)
 {
     __shared__ double2 T[NB][NB + 1];
     __shared__ double2 I[NB][NB + 1];
@@ -25,17 +27,16 @@ __global__ void __launch_bounds__(256) potrf_diag(double2 *A, int64_t lda, const
     if (st->code != 0) return;
     const int tid = threadIdx.x;
     if (tid == 0) fail = 0;
-    for (int e = tid; e < NB * NB; e += 256) {
+    for (int e = tid; e < NB * NB; e += DT) {
         const int i = e / NB, j = e % NB;
-        double2 v = make_double2(0.0, 0.0);
-        if (i < nb && j <= i) v = A[(int64_t)(k + i) * lda + (k + j)];
-        T[i][j] = v;
+        T[i][j] = (i < nb && j <= i) ? A[(int64_t)(k + i) * lda + (k + j)] : make_double2(0.0, 0.0);
     }
     __syncthreads();
+    // right-looking factorisation; thread t owns rows i = t % NB and column slice t / NB
+    const int my_row = tid % NB, slice = tid / NB;   // 4 slices of the columns
     for (int j = 0; j < nb; ++j) {
         if (tid == 0) {
             const double d = T[j][j].x;
-            // a pivot below 1e-13 of the original diagonal means cond(M) >~ 1e13: not usable as HPD
             const double d0 = M0[(int64_t)(k + j) * lda + (k + j)].x;
             if (!(d > 1e-13 * d0) || isinf(d)) {
                 set_status(st, isnan(d) ? ISDF_ERR_NONFINITE : ISDF_ERR_NOT_HPD, k + j);
@@ -47,39 +48,48 @@ __global__ void __launch_bounds__(256) potrf_diag(double2 *A, int64_t lda, const
         __syncthreads();
         if (fail) return;
         const double ljj = T[j][j].x;
-        for (int i = j + 1 + tid; i < nb; i += 256) T[i][j] = make_double2(T[i][j].x / ljj, T[i][j].y / ljj);
+        if (slice == 0 && my_row > j && my_row < nb) T[my_row][j] = make_double2(T[my_row][j].x / ljj, T[my_row][j].y / ljj);
         __syncthreads();
-        // trailing update of the lower triangle: T[i][c] -= T[i][j] conj(T[c][j]), j < c <= i
-        const int rem = nb - j - 1;
-        for (int e = tid; e < rem * rem; e += 256) {
-            const int i = j + 1 + e / rem, c = j + 1 + e % rem;
-            if (c <= i) {
-                const double2 a = T[i][j], b = T[c][j];
-                T[i][c].x -= a.x * b.x + a.y * b.y;
-                T[i][c].y -= a.y * b.x - a.x * b.y;
+        // T[i][c] -= T[i][j] conj(T[c][j]) for j < c <= i
+        if (my_row > j && my_row < nb) {
+            const double2 a = T[my_row][j];
+            for (int c = j + 1 + slice; c <= my_row; c += DT / NB) {
+                const double2 b = T[c][j];
+                T[my_row][c].x -= a.x * b.x + a.y * b.y;
+                T[my_row][c].y -= a.y * b.x - a.x * b.y;
             }
         }
         __syncthreads();
     }
-    // inverse of the lower-triangular T by forward substitution, one column per thread
-    for (int c = tid; c < nb; c += 256) {
-        for (int i = 0; i < nb; ++i) {
-            if (i < c) {
-                I[i][c] = make_double2(0.0, 0.0);
-                continue;
+    // inverse by forward substitution, row by row:
+    // I[i][c] = (delta_ic - sum_{c <= l < i} T[i][l] I[l][c]) / T[i][i];
+    // the columns of a row are independent and each sum is split over 4 threads
+    {
+        const int c = tid >> 2, part = tid & 3;
+        for (int i = 0; i < NB; ++i) {
+            double2 s = make_double2(0.0, 0.0);
+            if (i < nb && c < i)
+                for (int l = c + part; l < i; l += 4) {
+                    const double2 a = T[i][l], b = I[l][c];
+                    s.x += a.x * b.x - a.y * b.y;
+                    s.y += a.x * b.y + a.y * b.x;
+                }
+            s.x += __shfl_xor_sync(0xffffffffu, s.x, 1);
+            s.y += __shfl_xor_sync(0xffffffffu, s.y, 1);
+            s.x += __shfl_xor_sync(0xffffffffu, s.x, 2);
+            s.y += __shfl_xor_sync(0xffffffffu, s.y, 2);
+            if (part == 0) {
+                double2 v = make_double2(0.0, 0.0);
+                if (i < nb && c <= i) {
+                    const double d = T[i][i].x;
+                    v = make_double2(((i == c ? 1.0 : 0.0) - s.x) / d, -s.y / d);
+                }
+                I[i][c] = v;
             }
-            double2 s = make_double2(i == c ? 1.0 : 0.0, 0.0);
-            for (int l = c; l < i; ++l) {
-                const double2 a = T[i][l], b = I[l][c];
-                s.x -= a.x * b.x - a.y * b.y;
-                s.y -= a.x * b.y + a.y * b.x;
-            }
-            const double d = T[i][i].x;
-            I[i][c] = make_double2(s.x / d, s.y / d);
+            __syncthreads();
         }
     }
-    __syncthreads();
-    for (int e = tid; e < nb * nb; e += 256) {
+    for (int e = tid; e < nb * nb; e += DT) {
         const int i = e / nb, j = e % nb;
         A[(int64_t)(k + i) * lda + (k + j)] = j <= i ? T[i][j] : make_double2(0.0, 0.0);
         Linv[(int64_t)(k + i) * ldi + (k + j)] = j <= i ? I[i][j] : make_double2(0.0, 0.0);
@@ -126,47 +136,49 @@ ZGemm single(int M, int N, int K, ZOperand A, ZOperand B, double2 *C, int64_t ld
 
 // Linv[o:o+n, o:o+n] = inverse of the lower-triangular L block (its 64-wide
 // diagonal blocks are already inverted in Linv).
-isdf_status tri_inv(const double2 *L, double2 *Linv, double2 *tmp, int64_t ld, int o, int n, cudaStream_t st)
+isdf_status tri_inv(const double2 *L, double2 *Linv, double2 *tmp, int64_t ld, int o, int n, double2 *part,
+                    size_t part_n, cudaStream_t st)
 {
     if (n <= NB) return ISDF_OK;
     const int h = ((n / 2 + NB - 1) / NB) * NB;
-    ISDF_TRY(tri_inv(L, Linv, tmp, ld, o, h, st));
-    ISDF_TRY(tri_inv(L, Linv, tmp, ld, o + h, n - h, st));
+    ISDF_TRY(tri_inv(L, Linv, tmp, ld, o, h, part, part_n, st));
+    ISDF_TRY(tri_inv(L, Linv, tmp, ld, o + h, n - h, part, part_n, st));
     // tmp = L[o+h:o+n, o:o+h] * Linv[o:o+h, o:o+h]   (Linv lower: k >= n)
     ZGemm g1 = single(n - h, h, h, op(L + (int64_t)(o + h) * ld + o, ld, 1, 0),
                       op(Linv + (int64_t)o * ld + o, ld, 1, 0), tmp, h, 1.0, 0);
     g1.kmode = ZG_K_FROM_N0;
-    ISDF_TRY(zgemm(g1, st));
+    ISDF_TRY(zgemm_auto(g1, part, part_n, st));
     // Linv[o+h:o+n, o:o+h] = -Linv[o+h:o+n, o+h:o+n] * tmp   (A lower: k <= m)
     ZGemm g2 = single(n - h, h, n - h, op(Linv + (int64_t)(o + h) * ld + (o + h), ld, 1, 0),
                       op(tmp, h, 1, 0), Linv + (int64_t)(o + h) * ld + o, ld, -1.0, 0);
     g2.k_to_m_end = 1;
-    return zgemm(g2, st);
+    return zgemm_auto(g2, part, part_n, st);
 }
 
 }  // namespace
 
 isdf_status cholesky_inverse(const double2 *M0, double2 *L, double2 *Linv, double2 *W, double2 *tmp, int n,
-                             DeviceStatus *st, cudaStream_t stream)
+                             double2 *part, size_t part_n, DeviceStatus *st, cudaStream_t stream)
 {
     const int64_t ld = n;
     ISDF_CUDA_TRY(cudaMemsetAsync(Linv, 0, sizeof(double2) * (size_t)n * n, stream));
     for (int k = 0; k < n; k += NB) {
         const int nb = n - k < NB ? n - k : NB;
-        potrf_diag<<<1, 256, 0, stream>>>(L, ld, M0, Linv, ld, k, nb, st); isdf_note_launch();
+        potrf_diag<<<1, DT, 0, stream>>>(L, ld, M0, Linv, ld, k, nb, st); isdf_note_launch();
         ISDF_LAUNCH_CHECK();
         const int rest = n - k - nb;
         if (rest <= 0) break;
-        // L21 = A21 * Lkk^-H  (in place: one CTA column per row block)
+        // L21 = A21 * Lkk^-H  (in place: one 64-wide CTA column per row block, no split-K)
         ZGemm p = single(rest, nb, nb, op(L + (int64_t)(k + nb) * ld + k, ld, 1, 0),
                          op(Linv + (int64_t)k * ld + k, 1, ld, 1), L + (int64_t)(k + nb) * ld + k, ld, 1.0, 0);
+        p.tile = 32;  // N = nb fits one tile column, so the in-place update is race-free
         ISDF_TRY(zgemm(p, stream));
         // A22 -= L21 L21^H (lower tiles)
         ZGemm u = single(rest, rest, nb, op(L + (int64_t)(k + nb) * ld + k, ld, 1, 0),
                          op(L + (int64_t)(k + nb) * ld + k, 1, ld, 1), L + (int64_t)(k + nb) * ld + (k + nb), ld,
                          -1.0, 1);
         u.lower_only = 1;
-        ISDF_TRY(zgemm(u, stream));
+        ISDF_TRY(zgemm_auto(u, part, part_n, stream));
     }
     {
         const int64_t total = (int64_t)n * n;
@@ -174,11 +186,11 @@ isdf_status cholesky_inverse(const double2 *M0, double2 *L, double2 *Linv, doubl
         zero_strict_upper<<<gr, 256, 0, stream>>>(L, n, ld); isdf_note_launch();
         ISDF_LAUNCH_CHECK();
     }
-    ISDF_TRY(tri_inv(L, Linv, tmp, ld, 0, n, stream));
+    ISDF_TRY(tri_inv(L, Linv, tmp, ld, 0, n, part, part_n, stream));
     // W = Linv^H Linv: W_ij = sum_{k >= max(i, j)} conj(Linv_ki) Linv_kj (lower tiles, then mirrored)
     ZGemm w = single(n, n, n, op(Linv, 1, ld, 1), op(Linv, ld, 1, 0), W, ld, 1.0, 0);
     w.kmode = ZG_K_FROM_MAX_MN;
     w.lower_only = 1;
-    ISDF_TRY(zgemm(w, stream));
+    ISDF_TRY(zgemm_auto(w, part, part_n, stream));
     return hermitian_mirror(W, n, ld, stream);
 }

@@ -125,11 +125,12 @@ ZGemm gemm1(int M, int N, int K, ZOperand A, ZOperand B, void *C, int64_t ldc, i
     return g;
 }
 
-int split_count(int M, int N, int K)
+// split-K factor for an M x N product over K grid rows that fits `cap` partial elements
+int split_count(int M, int N, int K, size_t cap)
 {
     const int tiles = ((M + 63) / 64) * ((N + 63) / 64);
     int s = 1;
-    while (s < 64 && tiles * s < 2 * 152 && K / (s * 2) >= 256) s *= 2;
+    while (s < 64 && tiles * s < 2 * 152 && K / (s * 2) >= 256 && (size_t)(s * 2) * M * N <= cap) s *= 2;
     return s;
 }
 
@@ -203,11 +204,11 @@ isdf_status plan_compute(isdf_plan *p, const int64_t *idx, cudaStream_t st)
     g.C2 = p->Bmu;
     g.lower_only = 1;
     g.splits = 1;
-    ISDF_TRY(zgemm(g, st));
+    ISDF_TRY(zgemm_auto(g, nullptr, 0, st));
     for (double2 *m : {p->M, p->Amu, p->Bmu}) ISDF_TRY(hermitian_mirror(m, n_mu, n_mu, st));
     // a9: M = L L^H, L^-1, M^-1 (FP64)
     ISDF_CUDA_TRY(cudaMemcpyAsync(p->L, p->M, sizeof(double2) * nn, cudaMemcpyDeviceToDevice, st));
-    ISDF_TRY(cholesky_inverse(p->M, p->L, p->Linv, p->W, p->tmp, n_mu, p->status, st));
+    ISDF_TRY(cholesky_inverse(p->M, p->L, p->Linv, p->W, p->tmp, n_mu, p->partial, p->partial_elems, p->status, st));
     if (p->mode == ISDF_MIXED) ISDF_TRY(mixed_prepare(p, st));
     return ISDF_OK;
 }
@@ -279,7 +280,7 @@ extern "C" isdf_status isdf_plan_create(isdf_plan **plan, const void *phi, int64
         PLAN_ALLOC(p->blkT, blk);
     }
     // split-K is used only while tiles * splits < 2 * 304, so 608 tiles of 64 x 64 bound the partials
-    p->partial_elems = (size_t)608 * 64 * 64;
+    p->partial_elems = (size_t)4 * 608 * 64 * 64;
     PLAN_ALLOC(p->partial, p->partial_elems);
 #undef PLAN_ALLOC
     if ((s = plan_compute(p, idx, st)) != ISDF_OK) {
@@ -377,7 +378,7 @@ extern "C" isdf_status isdf_fit_theta_backward(isdf_plan *p, int64_t row_begin, 
         {
             ZGemm g = gemm1(nm, nm, rows, opnd(p->blkT, 1, nm, 1, ZG_C128), opnd(p->blkY, nm, 1, 0, ZG_C128), p->Mbar,
                             nm, ZG_C128, -1.0, 1);
-            g.splits = split_count(nm, nm, rows);
+            g.splits = split_count(nm, nm, rows, p->partial_elems);
             g.partial = p->partial;
             ISDF_TRY(zgemm(g, st));
         }
@@ -396,13 +397,13 @@ extern "C" isdf_status isdf_fit_theta_backward(isdf_plan *p, int64_t row_begin, 
             ZGemm g = gemm1(nm, p->n_phi, rows, opnd(p->blkA, 1, nm, 1, ZG_C128),
                             opnd(static_cast<const char *>(p->phi) + r0 * p->ld_phi * es, p->ld_phi, 1, 0, t),
                             p->gphi_mu, p->n_phi, ZG_C128, 1.0, 1);
-            g.splits = split_count(nm, p->n_phi, rows);
+            g.splits = split_count(nm, p->n_phi, rows, p->partial_elems);
             g.partial = p->partial;
             ISDF_TRY(zgemm(g, st));
             ZGemm h = gemm1(nm, p->n_psi, rows, opnd(p->blkB, 1, nm, 1, ZG_C128),
                             opnd(static_cast<const char *>(p->psi) + r0 * p->ld_psi * es, p->ld_psi, 1, 0, t),
                             p->gpsi_mu, p->n_psi, ZG_C128, 1.0, 1);
-            h.splits = split_count(nm, p->n_psi, rows);
+            h.splits = split_count(nm, p->n_psi, rows, p->partial_elems);
             h.partial = p->partial;
             ISDF_TRY(zgemm(h, st));
         }

@@ -9,7 +9,7 @@
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 8;
+constexpr int BK = 8;
 
 template <typename T>
 __device__ __forceinline__ double2 ld_c(const void *p, int64_t i)
@@ -17,7 +17,7 @@ __device__ __forceinline__ double2 ld_c(const void *p, int64_t i)
     return cload(static_cast<const T *>(p), i);
 }
 
-template <typename TA, typename TB, bool DUAL>
+template <typename TA, typename TB, bool DUAL, int BM, int BN>
 __device__ __forceinline__ void load_tiles(const ZGemm &g, int m0, int n0, int k0, int kend,
                                            double2 (*As)[BK][BM + 1], double2 (*Bs)[BK][BN + 1])
 {
@@ -59,9 +59,11 @@ __device__ __forceinline__ void load_tiles(const ZGemm &g, int m0, int n0, int k
     }
 }
 
-template <typename TA, typename TB, typename TC, bool DUAL>
+// T x T complex output tile (T = 64 or 32), 256 threads, (T/16) x (T/16) outputs per thread
+template <typename TA, typename TB, typename TC, bool DUAL, int T>
 __global__ void __launch_bounds__(256) zgemm_kernel(ZGemm g)
 {
+    constexpr int BM = T, BN = T, R = T / 16;
     __shared__ double2 As[DUAL ? 2 : 1][BK][BM + 1];
     __shared__ double2 Bs[DUAL ? 2 : 1][BK][BN + 1];
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
@@ -77,33 +79,33 @@ __global__ void __launch_bounds__(256) zgemm_kernel(ZGemm g)
         ke = min(ke, kb + chunk);
     }
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    double2 acc1[4][4], acc2[DUAL ? 4 : 1][DUAL ? 4 : 1];
+    double2 acc1[R][R], acc2[DUAL ? R : 1][DUAL ? R : 1];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < R; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc1[i][j] = make_double2(0.0, 0.0);
+        for (int j = 0; j < R; ++j) acc1[i][j] = make_double2(0.0, 0.0);
     if (DUAL) {
 #pragma unroll
-        for (int i = 0; i < (DUAL ? 4 : 1); ++i)
+        for (int i = 0; i < (DUAL ? R : 1); ++i)
 #pragma unroll
-            for (int j = 0; j < (DUAL ? 4 : 1); ++j) acc2[i][j] = make_double2(0.0, 0.0);
+            for (int j = 0; j < (DUAL ? R : 1); ++j) acc2[i][j] = make_double2(0.0, 0.0);
     }
     for (int k0 = kb; k0 < ke; k0 += BK) {
-        load_tiles<TA, TB, DUAL>(g, m0, n0, k0, ke, As, Bs);
+        load_tiles<TA, TB, DUAL, BM, BN>(g, m0, n0, k0, ke, As, Bs);
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
 #pragma unroll
             for (int pr = 0; pr < (DUAL ? 2 : 1); ++pr) {
-                double2 a[4], b[4];
+                double2 a[R], b[R];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) a[i] = As[pr][kk][ty + 16 * i];
+                for (int i = 0; i < R; ++i) a[i] = As[pr][kk][ty + 16 * i];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) b[j] = Bs[pr][kk][tx + 16 * j];
+                for (int j = 0; j < R; ++j) b[j] = Bs[pr][kk][tx + 16 * j];
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
+                for (int i = 0; i < R; ++i)
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
+                    for (int j = 0; j < R; ++j) {
                         double2 &c = (DUAL && pr) ? acc2[DUAL ? i : 0][DUAL ? j : 0] : acc1[i][j];
                         c.x = fma(a[i].x, b[j].x, c.x);
                         c.x = fma(-a[i].y, b[j].y, c.x);
@@ -116,11 +118,11 @@ __global__ void __launch_bounds__(256) zgemm_kernel(ZGemm g)
     }
     // epilogue
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < R; ++i) {
         const int m = m0 + ty + 16 * i;
         if (m >= g.M) continue;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < R; ++j) {
             const int n = n0 + tx + 16 * j;
             if (n >= g.N) continue;
             if (g.splits > 1) {
@@ -153,7 +155,7 @@ __global__ void splitk_reduce(ZGemm g)
     const int64_t total = (int64_t)g.M * g.N;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int m = (int)(e / g.N), n = (int)(e % g.N);
-        if (g.lower_only && (m / BM) < (n / BN)) continue;
+        if (g.lower_only && (m / g.tile) < (n / g.tile)) continue;
         double2 s = make_double2(0.0, 0.0);
         for (int z = 0; z < g.splits; ++z) {
             const double2 v = g.partial[(int64_t)z * total + e];
@@ -175,9 +177,14 @@ template <typename TA, typename TB, typename TC, bool DUAL>
 isdf_status launch(const ZGemm &g, cudaStream_t st)
 {
     const int splits = g.splits > 1 ? g.splits : 1;
-    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, splits);
+    const int T = g.tile == 32 ? 32 : 64;
+    dim3 grid((g.N + T - 1) / T, (g.M + T - 1) / T, splits);
     if (grid.y > 65535u) return ISDF_ERR_UNSUPPORTED;
-    zgemm_kernel<TA, TB, TC, DUAL><<<grid, 256, 0, st>>>(g); isdf_note_launch();
+    if (T == 32)
+        zgemm_kernel<TA, TB, TC, DUAL, 32><<<grid, 256, 0, st>>>(g);
+    else
+        zgemm_kernel<TA, TB, TC, DUAL, 64><<<grid, 256, 0, st>>>(g);
+    isdf_note_launch();
     ISDF_LAUNCH_CHECK();
     if (splits > 1) {
         const int64_t total = (int64_t)g.M * g.N;
@@ -202,9 +209,11 @@ __global__ void mirror_kernel(double2 *C, int n, int64_t ld)
 
 }  // namespace
 
-isdf_status zgemm(const ZGemm &g, cudaStream_t st)
+isdf_status zgemm(const ZGemm &g_in, cudaStream_t st)
 {
+    ZGemm g = g_in;
     if (g.M <= 0 || g.N <= 0) return ISDF_OK;
+    if (g.tile != 32) g.tile = 64;
     if (g.splits > 1 && (g.dual || !g.partial)) return ISDF_ERR_INVALID_ARG;
     const int a = g.A1.type, b = g.B1.type, c = g.ctype;
     if (g.dual) {
@@ -217,6 +226,28 @@ isdf_status zgemm(const ZGemm &g, cudaStream_t st)
     if (a == ZG_C128 && b == ZG_C64 && c == ZG_C128) return launch<double2, float2, double2, false>(g, st);
     if (a == ZG_C128 && b == ZG_C128 && c == ZG_C64) return launch<double2, double2, float2, false>(g, st);
     return ISDF_ERR_UNSUPPORTED;
+}
+
+isdf_status zgemm_auto(const ZGemm &g_in, double2 *partial, size_t partial_elems, cudaStream_t st)
+{
+    ZGemm g = g_in;
+    const int sms = 152;
+    auto tiles = [&](int t) {
+        const int tm = (g.M + t - 1) / t, tn = (g.N + t - 1) / t;
+        return g.lower_only ? (tm * (tn + 1)) / 2 : tm * tn;
+    };
+    g.tile = tiles(64) >= 2 * sms ? 64 : 32;
+    const int nt = tiles(g.tile);
+    g.splits = 1;
+    if (!g.dual && partial) {
+        int s = 1;
+        while (nt * s * 2 <= 4 * sms && g.K / (s * 2) >= 64 && (size_t)(s * 2) * g.M * g.N <= partial_elems) s *= 2;
+        if (s > 1) {
+            g.splits = s;
+            g.partial = partial;
+        }
+    }
+    return zgemm(g, st);
 }
 
 isdf_status hermitian_mirror(double2 *C, int n, int64_t ld, cudaStream_t st)

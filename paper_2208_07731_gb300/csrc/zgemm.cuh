@@ -33,9 +33,14 @@ struct ZGemm {
     int k_to_m_end;           // stop k at the tile's last row (A lower triangular)
     int splits;               // > 1: split-K into `partial`, then reduced
     double2 *partial;         // splits * M * N complex128
+    int tile;                 // output tile edge: 64 (default) or 32
 };
 
 isdf_status zgemm(const ZGemm &g, cudaStream_t st);
+
+// zgemm with the tile edge and split-K chosen from the problem shape so that
+// small M x N products with deep K still fill the GPU (partial may be NULL).
+isdf_status zgemm_auto(const ZGemm &g, double2 *partial, size_t partial_elems, cudaStream_t st);
 
 // C = conj(C)^T in the strict upper triangle (completes a Hermitian matrix
 // whose lower triangle was computed); n x n, row-major complex128, ld.
