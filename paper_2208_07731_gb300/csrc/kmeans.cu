@@ -573,10 +573,11 @@ extern "C" isdf_status isdf_kmeans(const double *w, int32_t nx, int32_t ny, int3
     km_wmax<<<(unsigned)((n_r + 255) / 256 < 1024 ? (n_r + 255) / 256 : 1024), 256, 0, st>>>(a, n_r); isdf_note_launch();
     km_check_scale<<<1, 32, 0, st>>>(a); isdf_note_launch();
     ISDF_LAUNCH_CHECK();
-    const unsigned gmu = (unsigned)((n_mu + 255) / 256);
+    // small blocks spread the FP64 divisions of the update over many SMs
+    const unsigned gmu = (unsigned)((n_mu + 63) / 64);
     for (int t = 0; t < max_iter; ++t) {
         km_assign<false><<<n_tiles, kThreads, smem, st>>>(a, t); isdf_note_launch();
-        km_update<<<gmu, 256, 0, st>>>(a, t, n_tiles, objective); isdf_note_launch();
+        km_update<<<gmu, 64, 0, st>>>(a, t, n_tiles, objective); isdf_note_launch();
     }
     km_assign<true><<<n_tiles, kThreads, smem, st>>>(a, max_iter); isdf_note_launch();
     km_snap<<<(unsigned)((n_r + 255) / 256 < 4096 ? (n_r + 255) / 256 : 4096), 256, 0, st>>>(a, n_r); isdf_note_launch();

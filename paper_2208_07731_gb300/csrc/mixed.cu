@@ -309,6 +309,221 @@ __global__ void __launch_bounds__(128, 1)
     if (warp == 0) tc::tmem_dealloc(tmem, NCOLS);
 }
 
+// Persistent variant: one CTA per SM walks the output tiles (row-block
+// major, so concurrently running CTAs share A tiles in L2). Warp 0 lane 0
+// feeds the 3-stage shared-memory ring with TMA, warp 1 lane 0 issues the
+// MMAs, warps 2-5 run the epilogue. The TMEM accumulator is double-buffered
+// (tfull / tempty barriers), so the epilogue of one tile overlaps the MMAs of
+// the next.
+constexpr int EPI_WARPS = 4;
+
+template <bool DUAL>
+__global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
+    tc_gemm_persist(const __grid_constant__ CUtensorMap a1h, const __grid_constant__ CUtensorMap a1l,
+                    const __grid_constant__ CUtensorMap b1h, const __grid_constant__ CUtensorMap b1l,
+                    const __grid_constant__ CUtensorMap a2h, const __grid_constant__ CUtensorMap a2l,
+                    const __grid_constant__ CUtensorMap b2h, const __grid_constant__ CUtensorMap b2l, int kchunks,
+                    int a_row0, int rows, int n_tiles_n, int n_tiles, EpiParams ep)
+{
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full_bar[STAGES];
+    __shared__ __align__(8) uint64_t empty_bar[STAGES];
+    __shared__ __align__(8) uint64_t tfull[2];
+    __shared__ __align__(8) uint64_t tempty[2];
+    __shared__ __align__(8) uint64_t drain_bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int failed;
+
+    if (*(volatile int *)ep.err) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t raw = tc::smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t *sbase = smem_raw + (base - raw);
+    constexpr uint32_t ACC = DUAL ? 2 * TN : TN;   // TMEM columns of one accumulator stage
+    constexpr uint32_t NCOLS = 2 * ACC;
+    const int total = (DUAL ? 2 : 1) * kchunks;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            tc::mbar_init(&full_bar[s], 1);
+            tc::mbar_init(&empty_bar[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            tc::mbar_init(&tfull[a], 1);
+            tc::mbar_init(&tempty[a], EPI_WARPS);
+        }
+        tc::mbar_init(&drain_bar, 1);
+        failed = 0;
+        tc::fence_barrier_init();
+    }
+    if (warp == 0) tc::tmem_alloc(&tmem_slot, NCOLS);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            const CUtensorMap *maps[8] = {&a1h, &a1l, &b1h, &b1l, &a2h, &a2l, &b2h, &b2l};
+            for (int i = 0; i < (DUAL ? 8 : 4); ++i) tc::prefetch_map(maps[i]);
+            int c = 0, issued = 0;
+            for (int tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
+                const int m0 = (tile / n_tiles_n) * TM, n0 = (tile % n_tiles_n) * TN;
+                for (int q = 0; q < total; ++q, ++c) {
+                    const int s = c % STAGES, it = c / STAGES;
+                    if (!tc::mbar_wait(&empty_bar[s], (it & 1) ^ 1, WAIT_BUDGET)) {
+                        atomicExch(ep.err, 1);
+                        failed = 1;
+                        break;
+                    }
+                    const bool second = DUAL && q >= kchunks;
+                    const int kc = second ? q - kchunks : q;
+                    const CUtensorMap *const *mp = maps + (second ? 4 : 0);
+                    uint8_t *st = sbase + s * STAGE_BYTES;
+                    tc::mbar_expect_tx(&full_bar[s], STAGE_BYTES);
+                    tc::tma_load_2d(st, mp[0], &full_bar[s], kc * TK, a_row0 + m0);
+                    tc::tma_load_2d(st + TILE_A, mp[1], &full_bar[s], kc * TK, a_row0 + m0);
+                    tc::tma_load_2d(st + 2 * TILE_A, mp[2], &full_bar[s], kc * TK, n0);
+                    tc::tma_load_2d(st + 2 * TILE_A + TILE_B, mp[3], &full_bar[s], kc * TK, n0);
+                    issued = c + 1;
+                }
+            }
+            for (int c2 = issued - STAGES > 0 ? issued - STAGES : 0; c2 < issued; ++c2)
+                tc::mbar_wait(&full_bar[c2 % STAGES], (c2 / STAGES) & 1, WAIT_BUDGET);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = tc::idesc_f16(TM, TN);
+            int c = 0, tl = 0;
+            for (int tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x, ++tl) {
+                const int acc = tl & 1, use = tl >> 1;
+                if (!tc::mbar_wait(&tempty[acc], (use & 1) ^ 1, WAIT_BUDGET)) {
+                    atomicExch(ep.err, 1);
+                    failed = 1;
+                    break;
+                }
+                tc::fence_after();
+                const uint32_t dbase = tmem + (uint32_t)acc * ACC;
+                bool ok = true;
+                for (int q = 0; q < total; ++q, ++c) {
+                    const int s = c % STAGES, it = c / STAGES;
+                    if (!tc::mbar_wait(&full_bar[s], it & 1, WAIT_BUDGET)) {
+                        atomicExch(ep.err, 1);
+                        failed = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after();
+                    const bool second = DUAL && q >= kchunks;
+                    const int kc = second ? q - kchunks : q;
+                    const uint32_t d = dbase + (second ? (uint32_t)TN : 0u);
+                    const uint32_t sa = base + s * STAGE_BYTES;
+                    const uint64_t dah = tc::desc_sw128(sa), dal = tc::desc_sw128(sa + TILE_A);
+                    const uint64_t dbh = tc::desc_sw128(sa + 2 * TILE_A), dbl = tc::desc_sw128(sa + 2 * TILE_A + TILE_B);
+#pragma unroll
+                    for (int kk = 0; kk < TK / 16; ++kk) {
+                        const uint64_t o = (uint64_t)(2 * kk);
+                        tc::mma_f16(d, dah + o, dbh + o, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+                        tc::mma_f16(d, dah + o, dbl + o, idesc, 1u);
+                        tc::mma_f16(d, dal + o, dbh + o, idesc, 1u);
+                    }
+                    tc::mma_commit(&empty_bar[s]);
+                }
+                if (!ok) break;
+                tc::mma_commit(&tfull[acc]);
+            }
+            // no MMA may still be running when the TMEM is released
+            tc::mma_commit(&drain_bar);
+            tc::mbar_wait(&drain_bar, 0, WAIT_BUDGET);
+        }
+        __syncwarp();
+    } else {
+        const int quarter = warp & 3;
+        int tl = 0;
+        for (int tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x, ++tl) {
+            const int acc = tl & 1, use = tl >> 1;
+            const int m0 = (tile / n_tiles_n) * TM, n0 = (tile % n_tiles_n) * TN;
+            if (!tc::mbar_wait(&tfull[acc], use & 1, WAIT_BUDGET)) {
+                atomicExch(ep.err, 1);
+                failed = 1;
+                break;
+            }
+            tc::fence_after();
+            const int row = m0 + quarter * 32 + lane;
+            const uint32_t tl_addr = tmem + (uint32_t)acc * ACC + ((uint32_t)(quarter * 32) << 16);
+            if (DUAL) {
+                const float fy = ep.sc->fy;
+#pragma unroll 1
+                for (int j = 0; j < TN / 32; ++j) {
+                    uint32_t r1[32], r2[32];
+                    tc::tmem_ld32(tl_addr + 32 * j, r1);
+                    tc::tmem_ld32(tl_addr + TN + 32 * j, r2);
+                    tc::tmem_wait_ld();
+                    if (j == TN / 32 - 1) {
+                        tc::fence_before();
+                        __syncwarp();
+                        if (lane == 0) tc::mbar_arrive(&tempty[acc]);
+                    }
+                    if (row < rows) {
+                        __half2 hv[16], lv[16];
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) {
+                            const float ar = __uint_as_float(r1[2 * q]), ai = __uint_as_float(r1[2 * q + 1]);
+                            const float br = __uint_as_float(r2[2 * q]), bi = __uint_as_float(r2[2 * q + 1]);
+                            const float yr = (ar * br + ai * bi) * fy, yi = (ai * br - ar * bi) * fy;
+                            const __half2 h = __floats2half2_rn(yr, yi);
+                            const float2 hf = __half22float2(h);
+                            hv[q] = h;
+                            lv[q] = __floats2half2_rn(yr - hf.x, yi - hf.y);
+                        }
+                        uint4 *dh = reinterpret_cast<uint4 *>(ep.yh + row * ep.ldy + n0 + 32 * j);
+                        uint4 *dl = reinterpret_cast<uint4 *>(ep.yl + row * ep.ldy + n0 + 32 * j);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            dh[q] = reinterpret_cast<const uint4 *>(hv)[q];
+                            dl[q] = reinterpret_cast<const uint4 *>(lv)[q];
+                        }
+                    }
+                }
+            } else {
+                const float ft = ep.sc->ftheta;
+#pragma unroll 1
+                for (int j = 0; j < TN / 32; ++j) {
+                    uint32_t r[32];
+                    tc::tmem_ld32(tl_addr + 32 * j, r);
+                    tc::tmem_wait_ld();
+                    if (j == TN / 32 - 1) {
+                        tc::fence_before();
+                        __syncwarp();
+                        if (lane == 0) tc::mbar_arrive(&tempty[acc]);
+                    }
+                    if (row < rows) {
+                        float2 *dst = ep.theta + row * ep.ld_theta + (n0 >> 1) + 16 * j;
+#pragma unroll
+                        for (int q = 0; q < 16; ++q)
+                            dst[q] = make_float2(__uint_as_float(r[2 * q]) * ft, __uint_as_float(r[2 * q + 1]) * ft);
+                    }
+                }
+            }
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, NCOLS);
+}
+
+int num_sms()
+{
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+    }
+    return n;
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -393,6 +608,10 @@ static isdf_status mixed_alloc(isdf_plan *p)
     if (!ok) return ISDF_ERR_CUDA;
     ISDF_CUDA_TRY(cudaFuncSetAttribute(tc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     ISDF_CUDA_TRY(cudaFuncSetAttribute(tc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    ISDF_CUDA_TRY(
+        cudaFuncSetAttribute(tc_gemm_persist<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    ISDF_CUDA_TRY(
+        cudaFuncSetAttribute(tc_gemm_persist<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     return ISDF_OK;
 }
 
@@ -452,19 +671,24 @@ isdf_status mixed_fit(isdf_plan *p, int64_t row_begin, int64_t row_count, void *
         ep.ldy = 2 * nm;
         ep.sc = b->sc;
         ep.err = err;
-        dim3 grid((2 * nm) / TN, (rows + TM - 1) / TM);
+        const int n_tiles_n = (2 * nm) / TN, m_tiles = (rows + TM - 1) / TM;
+        const int n_tiles = n_tiles_n * m_tiles;
+        const unsigned grid = (unsigned)(n_tiles < num_sms() ? n_tiles : num_sms());
+        const unsigned threads = 64 + 32 * EPI_WARPS;
         // a10: Y_b = (Phi_b Phi_mu^H) o conj(Psi_b Psi_mu^H), written split for the next GEMM
         timer_start(p, 0, st);
-        tc_gemm<true><<<grid, 128, SMEM_BYTES, st>>>(b->m_a1h, b->m_a1l, b->m_b1h, b->m_b1l, b->m_a2h, b->m_a2l,
-                                                     b->m_b2h, b->m_b2l, (2 * n) / TK, (int)r0, rows, ep); isdf_note_launch();
+        tc_gemm_persist<true><<<grid, threads, SMEM_BYTES, st>>>(b->m_a1h, b->m_a1l, b->m_b1h, b->m_b1l, b->m_a2h,
+                                                                 b->m_a2l, b->m_b2h, b->m_b2l, (2 * n) / TK, (int)r0,
+                                                                 rows, n_tiles_n, n_tiles, ep); isdf_note_launch();
         timer_stop(p, 0, st, rows);
         ISDF_LAUNCH_CHECK();
         // a11: Theta_b = Y_b M^-1
         ep.theta = static_cast<float2 *>(theta) + (r0 - row_begin) * ld_theta;
         ep.ld_theta = ld_theta;
         timer_start(p, 1, st);
-        tc_gemm<false><<<grid, 128, SMEM_BYTES, st>>>(b->m_yh, b->m_yl, b->m_bwh, b->m_bwl, b->m_yh, b->m_yl,
-                                                      b->m_bwh, b->m_bwl, (2 * nm) / TK, 0, rows, ep); isdf_note_launch();
+        tc_gemm_persist<false><<<grid, threads, SMEM_BYTES, st>>>(b->m_yh, b->m_yl, b->m_bwh, b->m_bwl, b->m_yh,
+                                                                  b->m_yl, b->m_bwh, b->m_bwl, (2 * nm) / TK, 0, rows,
+                                                                  n_tiles_n, n_tiles, ep); isdf_note_launch();
         timer_stop(p, 1, st, rows);
         ISDF_LAUNCH_CHECK();
     }
