@@ -239,7 +239,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         stages = {k: ev[i].elapsed_time(ev[i + 1]) for i, k in enumerate(["weights", "kmeans", "plan_update",
                                                                           "fit_theta"])}
-        for kind in ("gram", "apply"):
+        for kind in isdf.TIMER_KINDS:
             plan.kernel_time(kind)  # reset
         if world > 1:
             dist.barrier()
@@ -256,9 +256,12 @@ def run_ours(args):
         launches = isdf.kernel_launches() - l0
         clk = clocks.stop()
         ms = barrier_max(e0.elapsed_time(e1)) / args.steps
-        kt = {k: plan.kernel_time(k) for k in ("gram", "apply")}
+        kt = {k: plan.kernel_time(k) for k in isdf.TIMER_KINDS}
         plan.check()
         stats = km["stats"].cpu().tolist()
+        plan_stages = {k: kt[k][0] / args.steps for k in ("gather_M", "cholesky", "tri_inverse", "minv", "mixed_prep")
+                       if kt[k][1]}
+        stages["plan_update_parts"] = plan_stages
         return {"ms": ms, "stages": stages, "kt": kt, "launches": launches // args.steps, "clocks": clk,
                 "theta": theta, "plan": plan, "idx": km["idx"], "stats": stats}
 

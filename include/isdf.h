@@ -239,8 +239,11 @@ ISDF_API void isdf_plan_destroy(isdf_plan *plan);
 /* Benchmark instrumentation.
  * isdf_plan_enable_timing(plan, capacity): when capacity > 0, the plan records
  * CUDA events on the launching stream around each launch of its Gram-Hadamard
- * kernel (kind 0) and its M^-1 application kernel (kind 1), for up to
- * `capacity` launches per kind; 0 switches timing off.
+ * kernel (kind 0) and its M^-1 application kernel (kind 1), and around the
+ * stages of isdf_plan_create / isdf_plan_update: gather + M (2), Cholesky
+ * factor (3), triangular inverse (4), M^-1 = L^-H L^-1 (5) and the tensor-core
+ * operand preparation (6), for up to `capacity` records per kind; 0 switches
+ * timing off. Kinds are 0..6.
  * isdf_plan_kernel_time(plan, kind, &ms, &launches, &rows): waits for those
  * events and returns the summed kernel time, the number of launches and the
  * grid rows they processed since the previous query, then resets the count.

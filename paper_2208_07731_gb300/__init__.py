@@ -26,6 +26,7 @@ C128, C64 = 0, 1
 SSM, PSM = 0, 1
 FP64, MIXED = 0, 1
 EARLY_STOP = 1
+TIMER_KINDS = {"gram": 0, "apply": 1, "gather_M": 2, "cholesky": 3, "tri_inverse": 4, "minv": 5, "mixed_prep": 6}
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA runtime error", 3: "C C^H is not Hermitian positive definite",
           4: "empty K-means cluster", 5: "non-finite value", 6: "bounded device wait timed out",
           7: "workspace missing or too small", 8: "unsupported size"}
@@ -209,9 +210,10 @@ class Plan:
         _check(lib().isdf_plan_enable_timing(self._h, int(capacity)), "isdf_plan_enable_timing")
 
     def kernel_time(self, kind: str):
-        """(total ms, launches, rows) of the timed 'gram' or 'apply' launches since the last query."""
+        """(total ms, launches, rows) of a timed kind since the last query: 'gram', 'apply' (the two
+        GEMM kernels) or a plan stage 'gather_M', 'cholesky', 'tri_inverse', 'minv', 'mixed_prep'."""
         ms, n, rows = ctypes.c_double(0), ctypes.c_int64(0), ctypes.c_int64(0)
-        _check(lib().isdf_plan_kernel_time(self._h, {"gram": 0, "apply": 1}[kind], ctypes.byref(ms), ctypes.byref(n),
+        _check(lib().isdf_plan_kernel_time(self._h, TIMER_KINDS[kind], ctypes.byref(ms), ctypes.byref(n),
                                            ctypes.byref(rows)), "isdf_plan_kernel_time")
         return ms.value, n.value, rows.value
 

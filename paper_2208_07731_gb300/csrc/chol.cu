@@ -8,6 +8,7 @@
 // triangle is updated by A22 -= L21 L21^H. L^-1 is built recursively from the
 // inverted diagonal blocks: inv([[A, 0], [B, C]]) = [[A^-1, 0], [-C^-1 B A^-1, C^-1]].
 #include "chol.cuh"
+#include "plan.cuh"
 #include "zgemm.cuh"
 
 namespace {
@@ -158,9 +159,11 @@ isdf_status tri_inv(const double2 *L, double2 *Linv, double2 *tmp, int64_t ld, i
 }  // namespace
 
 isdf_status cholesky_inverse(const double2 *M0, double2 *L, double2 *Linv, double2 *W, double2 *tmp, int n,
-                             double2 *part, size_t part_n, DeviceStatus *st, cudaStream_t stream)
+                             double2 *part, size_t part_n, DeviceStatus *st, cudaStream_t stream,
+                             isdf_plan *tp)
 {
     const int64_t ld = n;
+    if (tp) timer_start(tp, 3, stream);
     ISDF_CUDA_TRY(cudaMemsetAsync(Linv, 0, sizeof(double2) * (size_t)n * n, stream));
     for (int k = 0; k < n; k += NB) {
         const int nb = n - k < NB ? n - k : NB;
@@ -186,11 +189,21 @@ isdf_status cholesky_inverse(const double2 *M0, double2 *L, double2 *Linv, doubl
         zero_strict_upper<<<gr, 256, 0, stream>>>(L, n, ld); isdf_note_launch();
         ISDF_LAUNCH_CHECK();
     }
+    if (tp) {
+        timer_stop(tp, 3, stream, n);
+        timer_start(tp, 4, stream);
+    }
     ISDF_TRY(tri_inv(L, Linv, tmp, ld, 0, n, part, part_n, stream));
+    if (tp) {
+        timer_stop(tp, 4, stream, n);
+        timer_start(tp, 5, stream);
+    }
     // W = Linv^H Linv: W_ij = sum_{k >= max(i, j)} conj(Linv_ki) Linv_kj (lower tiles, then mirrored)
     ZGemm w = single(n, n, n, op(Linv, 1, ld, 1), op(Linv, ld, 1, 0), W, ld, 1.0, 0);
     w.kmode = ZG_K_FROM_MAX_MN;
     w.lower_only = 1;
     ISDF_TRY(zgemm_auto(w, part, part_n, stream));
-    return hermitian_mirror(W, n, ld, stream);
+    ISDF_TRY(hermitian_mirror(W, n, ld, stream));
+    if (tp) timer_stop(tp, 5, stream, n);
+    return ISDF_OK;
 }

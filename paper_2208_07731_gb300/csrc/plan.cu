@@ -181,6 +181,7 @@ isdf_status plan_compute(isdf_plan *p, const int64_t *idx, cudaStream_t st)
     ISDF_CUDA_TRY(cudaMemsetAsync(p->gphi_mu, 0, sizeof(double2) * n_mu * n_phi, st));
     ISDF_CUDA_TRY(cudaMemsetAsync(p->gpsi_mu, 0, sizeof(double2) * n_mu * n_psi, st));
     // a7: Phi_mu = Phi[idx], Psi_mu = Psi[idx]  (Eq. Cmu)
+    timer_start(p, 2, st);
     gather_rows<<<grid_for((int64_t)n_mu * n_phi), 256, 0, st>>>(p->phi, p->ld_phi, p->dtype, n_phi, p->idx, n_mu,
                                                                  p->n_r, p->phi_mu, p->status); isdf_note_launch();
     gather_rows<<<grid_for((int64_t)n_mu * n_psi), 256, 0, st>>>(p->psi, p->ld_psi, p->dtype, n_psi, p->idx, n_mu,
@@ -206,10 +207,16 @@ isdf_status plan_compute(isdf_plan *p, const int64_t *idx, cudaStream_t st)
     g.splits = 1;
     ISDF_TRY(zgemm_auto(g, nullptr, 0, st));
     for (double2 *m : {p->M, p->Amu, p->Bmu}) ISDF_TRY(hermitian_mirror(m, n_mu, n_mu, st));
+    timer_stop(p, 2, st, n_mu);
     // a9: M = L L^H, L^-1, M^-1 (FP64)
     ISDF_CUDA_TRY(cudaMemcpyAsync(p->L, p->M, sizeof(double2) * nn, cudaMemcpyDeviceToDevice, st));
-    ISDF_TRY(cholesky_inverse(p->M, p->L, p->Linv, p->W, p->tmp, n_mu, p->partial, p->partial_elems, p->status, st));
-    if (p->mode == ISDF_MIXED) ISDF_TRY(mixed_prepare(p, st));
+    ISDF_TRY(cholesky_inverse(p->M, p->L, p->Linv, p->W, p->tmp, n_mu, p->partial, p->partial_elems, p->status, st,
+                              p));
+    if (p->mode == ISDF_MIXED) {
+        timer_start(p, 6, st);
+        ISDF_TRY(mixed_prepare(p, st));
+        timer_stop(p, 6, st, p->n_r);
+    }
     return ISDF_OK;
 }
 
@@ -468,7 +475,7 @@ void timer_stop(isdf_plan *p, int kind, cudaStream_t st, int64_t rows)
 
 static void timing_free(isdf_plan *p)
 {
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < ISDF_TIMER_KINDS; ++k) {
         if (p->tev[k]) {
             for (int i = 0; i < 2 * p->tcap; ++i) cudaEventDestroy(p->tev[k][i]);
             free(p->tev[k]);
@@ -489,7 +496,7 @@ extern "C" isdf_status isdf_plan_enable_timing(isdf_plan *p, int32_t capacity)
     timing_free(p);
     if (capacity == 0) return ISDF_OK;
     p->tcap = capacity;
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < ISDF_TIMER_KINDS; ++k) {
         p->tev[k] = static_cast<cudaEvent_t *>(calloc(2 * (size_t)capacity, sizeof(cudaEvent_t)));
         p->trows[k] = static_cast<int64_t *>(calloc((size_t)capacity, sizeof(int64_t)));
         if (!p->tev[k] || !p->trows[k]) return ISDF_ERR_CUDA;
@@ -502,7 +509,7 @@ extern "C" isdf_status isdf_plan_enable_timing(isdf_plan *p, int32_t capacity)
 extern "C" isdf_status isdf_plan_kernel_time(isdf_plan *p, int32_t kind, double *total_ms, int64_t *launches,
                                              int64_t *rows)
 {
-    if (!p || kind < 0 || kind > 1 || !total_ms || !launches || !rows) return ISDF_ERR_INVALID_ARG;
+    if (!p || kind < 0 || kind >= ISDF_TIMER_KINDS || !total_ms || !launches || !rows) return ISDF_ERR_INVALID_ARG;
     *total_ms = 0.0;
     *launches = 0;
     *rows = 0;

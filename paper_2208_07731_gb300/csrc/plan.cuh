@@ -6,6 +6,8 @@
 
 struct MixedBuffers;
 
+#define ISDF_TIMER_KINDS 7
+
 struct isdf_plan {
     const void *phi, *psi;
     int64_t ld_phi, ld_psi, n_r;
@@ -22,12 +24,14 @@ struct isdf_plan {
     double2 *partial;                         // split-K partials
     size_t partial_elems;
     MixedBuffers *mixed;                      // tensor-core path (ISDF_MIXED)
-    // optional per-launch event timing of the Gram (0) and M^-1 application (1) kernels
+    // optional event timing: kinds 0 Gram kernel, 1 M^-1 application kernel,
+    // 2 gather + M, 3 Cholesky factor, 4 triangular inverse, 5 M^-1 = L^-H L^-1,
+    // 6 tensor-core operand preparation
     int timing;
     int tcap;
-    int tused[2];
-    cudaEvent_t *tev[2];   // 2 * tcap events per kind: (start, stop) pairs
-    int64_t *trows[2];     // grid rows processed by each timed launch
+    int tused[ISDF_TIMER_KINDS];
+    cudaEvent_t *tev[ISDF_TIMER_KINDS];   // 2 * tcap events per kind: (start, stop) pairs
+    int64_t *trows[ISDF_TIMER_KINDS];     // grid rows processed by each timed launch
 };
 
 // record a start event before a timed launch (no-op unless timing is enabled)
