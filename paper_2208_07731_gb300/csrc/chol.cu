@@ -24,6 +24,7 @@ __global__ void __launch_bounds__(DT) potrf_diag(double2 *A, int64_t lda, const 
 {
     __shared__ double2 T[NB][NB + 1];
     __shared__ double2 I[NB][NB + 1];
+    __shared__ double rdiag[NB];   // 1 / L_jj (FP64 division is slow on this part: one per pivot)
     __shared__ int fail;
     if (st->code != 0) return;
     const int tid = threadIdx.x;
@@ -43,13 +44,15 @@ __global__ void __launch_bounds__(DT) potrf_diag(double2 *A, int64_t lda, const 
                 set_status(st, isnan(d) ? ISDF_ERR_NONFINITE : ISDF_ERR_NOT_HPD, k + j);
                 fail = 1;
             } else {
-                T[j][j] = make_double2(sqrt(d), 0.0);
+                const double l = sqrt(d);
+                T[j][j] = make_double2(l, 0.0);
+                rdiag[j] = 1.0 / l;
             }
         }
         __syncthreads();
         if (fail) return;
-        const double ljj = T[j][j].x;
-        if (slice == 0 && my_row > j && my_row < nb) T[my_row][j] = make_double2(T[my_row][j].x / ljj, T[my_row][j].y / ljj);
+        const double rj = rdiag[j];
+        if (slice == 0 && my_row > j && my_row < nb) T[my_row][j] = make_double2(T[my_row][j].x * rj, T[my_row][j].y * rj);
         __syncthreads();
         // T[i][c] -= T[i][j] conj(T[c][j]) for j < c <= i
         if (my_row > j && my_row < nb) {
@@ -82,8 +85,8 @@ __global__ void __launch_bounds__(DT) potrf_diag(double2 *A, int64_t lda, const 
             if (part == 0) {
                 double2 v = make_double2(0.0, 0.0);
                 if (i < nb && c <= i) {
-                    const double d = T[i][i].x;
-                    v = make_double2(((i == c ? 1.0 : 0.0) - s.x) / d, -s.y / d);
+                    const double r = rdiag[i];
+                    v = make_double2(((i == c ? 1.0 : 0.0) - s.x) * r, -s.y * r);
                 }
                 I[i][c] = v;
             }

@@ -14,13 +14,13 @@
 // A B^T ~ Ahi Bhi^T + Ahi Blo^T + Alo Bhi^T, each product exact in the FP32
 // accumulator (11 + 11 significant bits), leaving ~2^-22 relative error.
 //
-// GEMM kernel: one 128 x 128 output tile per CTA, 4 warps: warp 0 lane 0
-// issues TMA loads (128-byte swizzle) into a 3-stage mbarrier ring, warp 1
-// lane 0 issues tcgen05.mma into TMEM, and all 4 warps run the epilogue from
-// TMEM (warp w owns TMEM lanes 32w..32w+31). The Gram variant accumulates
-// Phi_b Phi_mu^H and Psi_b Psi_mu^H into two TMEM accumulators and writes
-// Y = P^phi o conj(P^psi), already scaled and split, as the A operand of the
-// second GEMM Theta_b = Y_b M^-1.
+// GEMM kernel (tc_gemm_persist): 128 x 128 output tiles, K in chunks of 64
+// FP16 (one 128-byte swizzle row), a 3-stage TMA/mbarrier ring, tcgen05.mma
+// into a double-buffered TMEM accumulator and a TMEM epilogue. The Gram
+// variant accumulates Phi_b Phi_mu^H and Psi_b Psi_mu^H into two TMEM
+// accumulators and writes Y = P^phi o conj(P^psi), already scaled and split,
+// as the A operand of the second GEMM Theta_b = Y_b M^-1, whose K loop runs
+// in segments summed in registers.
 #include <cudaTypedefs.h>
 
 #include "mixed.cuh"
@@ -34,7 +34,8 @@ constexpr int TILE_A = TM * TK * 2;
 constexpr int TILE_B = TN * TK * 2;
 constexpr int STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
-constexpr long long WAIT_BUDGET = 200000000LL;  // SM cycles (~0.1 s); normal waits take microseconds
+constexpr long long WAIT_BUDGET = 200000000LL;
+constexpr int kApplySegment = 8;   // K chunks (of 64) per TMEM accumulation segment in the M^-1 GEMM  // SM cycles (~0.1 s); normal waits take microseconds
 
 struct MixScales {
     unsigned int maxabs_phi, maxrho_phi, maxabs_psi, maxrho_psi, maxabs_w;  // float bits
@@ -157,159 +158,7 @@ struct EpiParams {
     int *err;
 };
 
-template <bool DUAL>
-__global__ void __launch_bounds__(128, 1)
-    tc_gemm(const __grid_constant__ CUtensorMap a1h, const __grid_constant__ CUtensorMap a1l,
-            const __grid_constant__ CUtensorMap b1h, const __grid_constant__ CUtensorMap b1l,
-            const __grid_constant__ CUtensorMap a2h, const __grid_constant__ CUtensorMap a2l,
-            const __grid_constant__ CUtensorMap b2h, const __grid_constant__ CUtensorMap b2l, int kchunks,
-            int a_row0, int rows, EpiParams ep)
-{
-    extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t full_bar[STAGES];
-    __shared__ __align__(8) uint64_t empty_bar[STAGES];
-    __shared__ __align__(8) uint64_t done_bar;
-    __shared__ uint32_t tmem_slot;
-    __shared__ int failed;
-
-    // once any CTA has given up, the rest of the grid leaves at once
-    if (*(volatile int *)ep.err) return;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t raw = tc::smem_u32(smem_raw);
-    const uint32_t base = (raw + 1023u) & ~1023u;
-    uint8_t *sbase = smem_raw + (base - raw);
-    const int n0 = blockIdx.x * TN, m0 = blockIdx.y * TM;
-    constexpr uint32_t NCOLS = DUAL ? 2 * TN : TN;
-    const int total = (DUAL ? 2 : 1) * kchunks;
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
-            tc::mbar_init(&full_bar[s], 1);
-            tc::mbar_init(&empty_bar[s], 1);
-        }
-        tc::mbar_init(&done_bar, 1);
-        failed = 0;
-        tc::fence_barrier_init();
-    }
-    if (warp == 0) tc::tmem_alloc(&tmem_slot, NCOLS);
-    tc::fence_before();
-    __syncthreads();
-    tc::fence_after();
-    const uint32_t tmem = tmem_slot;
-
-    if (warp == 0 && lane == 0) {
-        // TMA producer
-        const CUtensorMap *maps[8] = {&a1h, &a1l, &b1h, &b1l, &a2h, &a2l, &b2h, &b2l};
-        for (int i = 0; i < (DUAL ? 8 : 4); ++i) tc::prefetch_map(maps[i]);
-        int issued = 0;
-        for (int c = 0; c < total; ++c) {
-            const int s = c % STAGES, it = c / STAGES;
-            if (!tc::mbar_wait(&empty_bar[s], (it & 1) ^ 1, WAIT_BUDGET)) {
-                atomicExch(ep.err, 1);
-                failed = 1;
-                break;
-            }
-            const bool second = DUAL && c >= kchunks;
-            const int kc = second ? c - kchunks : c;
-            const CUtensorMap *const *mp = maps + (second ? 4 : 0);
-            uint8_t *st = sbase + s * STAGE_BYTES;
-            tc::mbar_expect_tx(&full_bar[s], STAGE_BYTES);
-            tc::tma_load_2d(st, mp[0], &full_bar[s], kc * TK, a_row0 + m0);
-            tc::tma_load_2d(st + TILE_A, mp[1], &full_bar[s], kc * TK, a_row0 + m0);
-            tc::tma_load_2d(st + 2 * TILE_A, mp[2], &full_bar[s], kc * TK, n0);
-            tc::tma_load_2d(st + 2 * TILE_A + TILE_B, mp[3], &full_bar[s], kc * TK, n0);
-            issued = c + 1;
-        }
-        // do not leave with copies in flight: wait (bounded) for the last issued stages
-        for (int c = issued - STAGES > 0 ? issued - STAGES : 0; c < issued; ++c)
-            tc::mbar_wait(&full_bar[c % STAGES], (c / STAGES) & 1, WAIT_BUDGET);
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer
-        constexpr uint32_t idesc = tc::idesc_f16(TM, TN);
-        for (int c = 0; c < total; ++c) {
-            const int s = c % STAGES, it = c / STAGES;
-            if (!tc::mbar_wait(&full_bar[s], it & 1, WAIT_BUDGET)) {
-                atomicExch(ep.err, 1);
-                failed = 1;
-                break;
-            }
-            tc::fence_after();
-            const bool second = DUAL && c >= kchunks;
-            const int kc = second ? c - kchunks : c;
-            const uint32_t d = tmem + (second ? (uint32_t)TN : 0u);
-            const uint32_t sa = base + s * STAGE_BYTES;
-            const uint64_t dah = tc::desc_sw128(sa), dal = tc::desc_sw128(sa + TILE_A);
-            const uint64_t dbh = tc::desc_sw128(sa + 2 * TILE_A), dbl = tc::desc_sw128(sa + 2 * TILE_A + TILE_B);
-#pragma unroll
-            for (int kk = 0; kk < TK / 16; ++kk) {
-                const uint64_t o = (uint64_t)(2 * kk);  // 32 bytes further along K
-                tc::mma_f16(d, dah + o, dbh + o, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
-                tc::mma_f16(d, dah + o, dbl + o, idesc, 1u);
-                tc::mma_f16(d, dal + o, dbh + o, idesc, 1u);
-            }
-            tc::mma_commit(&empty_bar[s]);
-        }
-        tc::mma_commit(&done_bar);
-    }
-    __syncwarp();
-
-    // epilogue: all four warps
-    const bool ok = tc::mbar_wait(&done_bar, 0, WAIT_BUDGET);
-    tc::fence_after();
-    if (!ok) atomicExch(ep.err, 1);
-    const bool store = ok && !failed;
-    const int row = m0 + warp * 32 + lane;
-    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
-    if (DUAL) {
-        const float fy = ep.sc->fy;
-#pragma unroll 1
-        for (int j = 0; j < TN / 32; ++j) {
-            uint32_t r1[32], r2[32];
-            tc::tmem_ld32(tl + 32 * j, r1);
-            tc::tmem_ld32(tl + TN + 32 * j, r2);
-            tc::tmem_wait_ld();
-            if (store && row < rows) {
-                __half2 hv[16], lv[16];
-#pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const float ar = __uint_as_float(r1[2 * q]), ai = __uint_as_float(r1[2 * q + 1]);
-                    const float br = __uint_as_float(r2[2 * q]), bi = __uint_as_float(r2[2 * q + 1]);
-                    const float yr = (ar * br + ai * bi) * fy, yi = (ai * br - ar * bi) * fy;
-                    const __half2 h = __floats2half2_rn(yr, yi);
-                    const float2 hf = __half22float2(h);
-                    hv[q] = h;
-                    lv[q] = __floats2half2_rn(yr - hf.x, yi - hf.y);
-                }
-                uint4 *dh = reinterpret_cast<uint4 *>(ep.yh + row * ep.ldy + n0 + 32 * j);
-                uint4 *dl = reinterpret_cast<uint4 *>(ep.yl + row * ep.ldy + n0 + 32 * j);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    dh[q] = reinterpret_cast<const uint4 *>(hv)[q];
-                    dl[q] = reinterpret_cast<const uint4 *>(lv)[q];
-                }
-            }
-        }
-    } else {
-        const float ft = ep.sc->ftheta;
-#pragma unroll 1
-        for (int j = 0; j < TN / 32; ++j) {
-            uint32_t r[32];
-            tc::tmem_ld32(tl + 32 * j, r);
-            tc::tmem_wait_ld();
-            if (store && row < rows) {
-                float2 *dst = ep.theta + row * ep.ld_theta + (n0 >> 1) + 16 * j;
-#pragma unroll
-                for (int q = 0; q < 16; ++q)
-                    dst[q] = make_float2(__uint_as_float(r[2 * q]) * ft, __uint_as_float(r[2 * q + 1]) * ft);
-            }
-        }
-    }
-    tc::fence_before();
-    __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, NCOLS);
-}
-
-// Persistent variant: one CTA per SM walks the output tiles (row-block
+// One persistent CTA per SM walks the output tiles (row-block
 // major, so concurrently running CTAs share A tiles in L2). Warp 0 lane 0
 // feeds the 3-stage shared-memory ring with TMA, warp 1 lane 0 issues the
 // MMAs, warps 2-5 run the epilogue. The TMEM accumulator is double-buffered
@@ -323,7 +172,7 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
                     const __grid_constant__ CUtensorMap b1h, const __grid_constant__ CUtensorMap b1l,
                     const __grid_constant__ CUtensorMap a2h, const __grid_constant__ CUtensorMap a2l,
                     const __grid_constant__ CUtensorMap b2h, const __grid_constant__ CUtensorMap b2l, int kchunks,
-                    int a_row0, int rows, int n_tiles_n, int n_tiles, EpiParams ep)
+                    int a_row0, int rows, int n_tiles_n, int n_tiles, int seg, EpiParams ep)
 {
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[STAGES];
@@ -395,43 +244,54 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             constexpr uint32_t idesc = tc::idesc_f16(TM, TN);
+            // the K loop of a tile is cut into segments of `seg` chunks (DUAL: one segment per
+            // product); every segment starts a fresh TMEM accumulator, so the tensor cores'
+            // internal FP32 accumulation never runs over more than `seg` chunks
+            const int nseg = DUAL ? 1 : (total + seg - 1) / seg;
+            const int seg_len = DUAL ? total : seg;
             int c = 0, tl = 0;
-            for (int tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x, ++tl) {
-                const int acc = tl & 1, use = tl >> 1;
-                if (!tc::mbar_wait(&tempty[acc], (use & 1) ^ 1, WAIT_BUDGET)) {
-                    atomicExch(ep.err, 1);
-                    failed = 1;
-                    break;
-                }
-                tc::fence_after();
-                const uint32_t dbase = tmem + (uint32_t)acc * ACC;
-                bool ok = true;
-                for (int q = 0; q < total; ++q, ++c) {
-                    const int s = c % STAGES, it = c / STAGES;
-                    if (!tc::mbar_wait(&full_bar[s], it & 1, WAIT_BUDGET)) {
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < n_tiles && !failed && ok; tile += gridDim.x) {
+                for (int sg = 0; sg < nseg && ok; ++sg, ++tl) {
+                    const int acc = tl & 1, use = tl >> 1;
+                    if (!tc::mbar_wait(&tempty[acc], (use & 1) ^ 1, WAIT_BUDGET)) {
                         atomicExch(ep.err, 1);
                         failed = 1;
                         ok = false;
                         break;
                     }
                     tc::fence_after();
-                    const bool second = DUAL && q >= kchunks;
-                    const int kc = second ? q - kchunks : q;
-                    const uint32_t d = dbase + (second ? (uint32_t)TN : 0u);
-                    const uint32_t sa = base + s * STAGE_BYTES;
-                    const uint64_t dah = tc::desc_sw128(sa), dal = tc::desc_sw128(sa + TILE_A);
-                    const uint64_t dbh = tc::desc_sw128(sa + 2 * TILE_A), dbl = tc::desc_sw128(sa + 2 * TILE_A + TILE_B);
+                    const uint32_t dbase = tmem + (uint32_t)acc * ACC;
+                    const int q0 = sg * seg_len, q1 = min(total, q0 + seg_len);
+                    for (int q = q0; q < q1; ++q, ++c) {
+                        const int s = c % STAGES, it = c / STAGES;
+                        if (!tc::mbar_wait(&full_bar[s], it & 1, WAIT_BUDGET)) {
+                            atomicExch(ep.err, 1);
+                            failed = 1;
+                            ok = false;
+                            break;
+                        }
+                        tc::fence_after();
+                        const bool second = DUAL && q >= kchunks;
+                        const int kc = second ? q - kchunks : q;
+                        const bool first = DUAL ? (kc == 0) : (q == q0);
+                        const uint32_t d = dbase + (second ? (uint32_t)TN : 0u);
+                        const uint32_t sa = base + s * STAGE_BYTES;
+                        const uint64_t dah = tc::desc_sw128(sa), dal = tc::desc_sw128(sa + TILE_A);
+                        const uint64_t dbh = tc::desc_sw128(sa + 2 * TILE_A),
+                                       dbl = tc::desc_sw128(sa + 2 * TILE_A + TILE_B);
 #pragma unroll
-                    for (int kk = 0; kk < TK / 16; ++kk) {
-                        const uint64_t o = (uint64_t)(2 * kk);
-                        tc::mma_f16(d, dah + o, dbh + o, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
-                        tc::mma_f16(d, dah + o, dbl + o, idesc, 1u);
-                        tc::mma_f16(d, dal + o, dbh + o, idesc, 1u);
+                        for (int kk = 0; kk < TK / 16; ++kk) {
+                            const uint64_t o = (uint64_t)(2 * kk);
+                            tc::mma_f16(d, dah + o, dbh + o, idesc, (!first || kk > 0) ? 1u : 0u);
+                            tc::mma_f16(d, dah + o, dbl + o, idesc, 1u);
+                            tc::mma_f16(d, dal + o, dbh + o, idesc, 1u);
+                        }
+                        tc::mma_commit(&empty_bar[s]);
                     }
-                    tc::mma_commit(&empty_bar[s]);
+                    if (!ok) break;
+                    tc::mma_commit(&tfull[acc]);
                 }
-                if (!ok) break;
-                tc::mma_commit(&tfull[acc]);
             }
             // no MMA may still be running when the TMEM is released
             tc::mma_commit(&drain_bar);
@@ -440,19 +300,21 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
         __syncwarp();
     } else {
         const int quarter = warp & 3;
+        const int nseg = DUAL ? 1 : (total + seg - 1) / seg;
         int tl = 0;
-        for (int tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x, ++tl) {
-            const int acc = tl & 1, use = tl >> 1;
+        for (int tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
             const int m0 = (tile / n_tiles_n) * TM, n0 = (tile % n_tiles_n) * TN;
-            if (!tc::mbar_wait(&tfull[acc], use & 1, WAIT_BUDGET)) {
-                atomicExch(ep.err, 1);
-                failed = 1;
-                break;
-            }
-            tc::fence_after();
             const int row = m0 + quarter * 32 + lane;
-            const uint32_t tl_addr = tmem + (uint32_t)acc * ACC + ((uint32_t)(quarter * 32) << 16);
             if (DUAL) {
+                const int acc = tl & 1, use = tl >> 1;
+                ++tl;
+                if (!tc::mbar_wait(&tfull[acc], use & 1, WAIT_BUDGET)) {
+                    atomicExch(ep.err, 1);
+                    failed = 1;
+                    break;
+                }
+                tc::fence_after();
+                const uint32_t tl_addr = tmem + (uint32_t)acc * ACC + ((uint32_t)(quarter * 32) << 16);
                 const float fy = ep.sc->fy;
 #pragma unroll 1
                 for (int j = 0; j < TN / 32; ++j) {
@@ -487,23 +349,39 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
                     }
                 }
             } else {
-                const float ft = ep.sc->ftheta;
-#pragma unroll 1
-                for (int j = 0; j < TN / 32; ++j) {
-                    uint32_t r[32];
-                    tc::tmem_ld32(tl_addr + 32 * j, r);
-                    tc::tmem_wait_ld();
-                    if (j == TN / 32 - 1) {
-                        tc::fence_before();
-                        __syncwarp();
-                        if (lane == 0) tc::mbar_arrive(&tempty[acc]);
-                    }
-                    if (row < rows) {
-                        float2 *dst = ep.theta + row * ep.ld_theta + (n0 >> 1) + 16 * j;
+                // sum the segments of this tile in registers (IEEE FP32 adds), then store
+                float sum[TN];
 #pragma unroll
-                        for (int q = 0; q < 16; ++q)
-                            dst[q] = make_float2(__uint_as_float(r[2 * q]) * ft, __uint_as_float(r[2 * q + 1]) * ft);
+                for (int i = 0; i < TN; ++i) sum[i] = 0.f;
+                bool ok = true;
+                for (int sg = 0; sg < nseg; ++sg, ++tl) {
+                    const int acc = tl & 1, use = tl >> 1;
+                    if (!tc::mbar_wait(&tfull[acc], use & 1, WAIT_BUDGET)) {
+                        atomicExch(ep.err, 1);
+                        failed = 1;
+                        ok = false;
+                        break;
                     }
+                    tc::fence_after();
+                    const uint32_t tl_addr = tmem + (uint32_t)acc * ACC + ((uint32_t)(quarter * 32) << 16);
+#pragma unroll
+                    for (int j = 0; j < TN / 32; ++j) {
+                        uint32_t r[32];
+                        tc::tmem_ld32(tl_addr + 32 * j, r);
+                        tc::tmem_wait_ld();
+#pragma unroll
+                        for (int q = 0; q < 32; ++q) sum[32 * j + q] += __uint_as_float(r[q]);
+                    }
+                    tc::fence_before();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&tempty[acc]);
+                }
+                if (!ok) break;
+                if (row < rows) {
+                    const float ft = ep.sc->ftheta;
+                    float2 *dst = ep.theta + row * ep.ld_theta + (n0 >> 1);
+#pragma unroll
+                    for (int q = 0; q < TN / 2; ++q) dst[q] = make_float2(sum[2 * q] * ft, sum[2 * q + 1] * ft);
                 }
             }
         }
@@ -606,8 +484,6 @@ static isdf_status mixed_alloc(isdf_plan *p)
     ok &= make_map(&b->m_yh, b->yh, 2 * nm, p->max_rows);
     ok &= make_map(&b->m_yl, b->yl, 2 * nm, p->max_rows);
     if (!ok) return ISDF_ERR_CUDA;
-    ISDF_CUDA_TRY(cudaFuncSetAttribute(tc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-    ISDF_CUDA_TRY(cudaFuncSetAttribute(tc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     ISDF_CUDA_TRY(
         cudaFuncSetAttribute(tc_gemm_persist<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     ISDF_CUDA_TRY(
@@ -679,7 +555,7 @@ isdf_status mixed_fit(isdf_plan *p, int64_t row_begin, int64_t row_count, void *
         timer_start(p, 0, st);
         tc_gemm_persist<true><<<grid, threads, SMEM_BYTES, st>>>(b->m_a1h, b->m_a1l, b->m_b1h, b->m_b1l, b->m_a2h,
                                                                  b->m_a2l, b->m_b2h, b->m_b2l, (2 * n) / TK, (int)r0,
-                                                                 rows, n_tiles_n, n_tiles, ep); isdf_note_launch();
+                                                                 rows, n_tiles_n, n_tiles, 0, ep); isdf_note_launch();
         timer_stop(p, 0, st, rows);
         ISDF_LAUNCH_CHECK();
         // a11: Theta_b = Y_b M^-1
@@ -688,7 +564,7 @@ isdf_status mixed_fit(isdf_plan *p, int64_t row_begin, int64_t row_count, void *
         timer_start(p, 1, st);
         tc_gemm_persist<false><<<grid, threads, SMEM_BYTES, st>>>(b->m_yh, b->m_yl, b->m_bwh, b->m_bwl, b->m_yh,
                                                                   b->m_yl, b->m_bwh, b->m_bwl, (2 * nm) / TK, 0, rows,
-                                                                  n_tiles_n, n_tiles, ep); isdf_note_launch();
+                                                                  n_tiles_n, n_tiles, kApplySegment, ep); isdf_note_launch();
         timer_stop(p, 1, st, rows);
         ISDF_LAUNCH_CHECK();
     }
