@@ -1,27 +1,32 @@
 // Step 2: weighted Lloyd K-means on the real-space grid (Sec. 2.2,
 // Eq. opt second form, Eq. r_k, Algorithm 1).
 //
-// Design (one CTA per 4 x 8 x 8 sub-box of the grid, one thread per point):
-//  * exact pruning: the CTA bounds every centroid's squared distance to its
-//    box from below (LB) and above (UB); only centroids with LB <= min UB can
-//    be the nearest one of any point in the box (margins cover rounding);
-//  * FP32 screen: each point evaluates its candidates in FP32 in box-local
-//    coordinates and keeps the two smallest values; when their gap exceeds a
-//    rigorous bound E on |d_fp32 - d_exact| (+ FP64 rounding) the FP32 winner
-//    is the FP64 winner. Otherwise the point re-evaluates the close candidates
-//    with the FP64 formula ((dx*dx + dy*dy) + dz*dz) and takes the smallest
-//    (distance, mu) pair - exactly the brute-force FP64 decision;
+// Design (one CTA of 8 warps per 8 x 8 x 8 tile of the grid; each warp owns a
+// 4 x 4 x 4 sub-cube, two points per lane):
+//  * exact two-level pruning: the CTA bounds every centroid's squared
+//    distance to its tile from below (LB) and above (UB) in FP32 with error
+//    margins and keeps those with LB <= min UB (only they can be the nearest
+//    centroid of a point in the tile); each warp prunes that list again
+//    against its own sub-cube;
+//  * FP32 screen: each point evaluates its warp's candidates in FP32 in
+//    tile-local coordinates and keeps the two smallest values; when their gap
+//    exceeds a rigorous bound E on |d_fp32 - d_exact| (+ FP64 rounding) the
+//    FP32 winner is the FP64 winner. Otherwise the point re-evaluates the close
+//    candidates with the FP64 formula ((dx*dx + dy*dy) + dz*dz) and takes the
+//    smallest (distance, mu) pair - exactly the brute-force FP64 decision;
 //  * exact update: each FP64 product w*x enters as the 128-bit integer
 //    floor(w*x*2^s); sums are integer (associative, so the result does not
-//    depend on thread or block order), first per CTA in shared memory, then in
-//    global memory, with the carry of the low word detected by the adding
-//    thread; the update kernel rounds each sum to FP64 and divides once.
+//    depend on thread or block order): per warp by shuffles for each distinct
+//    winner, then per CTA in shared memory, then in global memory, with the
+//    carry of the low word detected by the adding thread; the update kernel
+//    rounds each sum to FP64 and divides once.
 #include "common.cuh"
 
 namespace {
 
-constexpr int TX = 4, TY = 8, TZ = 8;
-constexpr int kThreads = TX * TY * TZ;   // 256
+constexpr int TX = 8, TY = 8, TZ = 8;    // CTA tile
+constexpr int kThreads = 256;            // 8 warps x (4 x 4 x 4 sub-cube, 2 points per lane)
+constexpr int kWarpCap = 256;            // per-warp candidate list capacity (else the CTA list is used)
 constexpr int kSlots = 256;              // per-CTA shared accumulators (first candidates)
 constexpr int kMaxMu = 8192;
 
@@ -45,6 +50,10 @@ struct KmArgs {
     int s_base;           // 126 - bits(N_r) - e(max(L, 1))
     int ntx, nty, ntz;    // tiles per axis
     double *cent;         // n_mu x 3
+    float4 *c32;          // n_mu: FP32 copies of the centroids for the conservative tile scan
+    float scan_err;       // bound on the FP32 error of a tile-local centroid coordinate in the scan
+    double lmax;          // max(Lx, Ly, Lz)
+    int want_obj;         // objective requested: FP64 distance of every winner
     unsigned long long *acc;  // n_mu x 8: (w, wx, wy, wz) x (lo, hi)
     int32_t *labels;
     double *dist;
@@ -175,6 +184,7 @@ __global__ void km_init(KmArgs a, const int64_t *__restrict__ init_idx, int64_t 
         a.cent[3 * i + 0] = __dmul_rn((double)ix, a.hx);
         a.cent[3 * i + 1] = __dmul_rn((double)iy, a.hy);
         a.cent[3 * i + 2] = __dmul_rn((double)iz, a.hz);
+        a.c32[i] = make_float4((float)a.cent[3 * i], (float)a.cent[3 * i + 1], (float)a.cent[3 * i + 2], 0.f);
 #pragma unroll
         for (int k = 0; k < 8; ++k) a.acc[8 * i + k] = 0ull;
         a.best[i] = ~0ull;
@@ -207,65 +217,106 @@ __global__ void km_check_scale(KmArgs a)
     if (threadIdx.x == 0 && fixed_scale(a) < 0) atomicExch(&a.ctl->error, 1);
 }
 
+__device__ __forceinline__ U128 shfl_down_u128(U128 v, int o)
+{
+    U128 r;
+    r.lo = __shfl_down_sync(0xffffffffu, v.lo, o);
+    r.hi = __shfl_down_sync(0xffffffffu, v.hi, o);
+    return r;
+}
+
+__device__ __forceinline__ U128 add_u128(U128 a, U128 b)
+{
+    U128 r;
+    r.lo = a.lo + b.lo;
+    r.hi = a.hi + b.hi + (r.lo < a.lo ? 1ull : 0ull);
+    return r;
+}
+
+// Sum the (w, wx, wy, wz) integers of the lanes that share a winner, one
+// distinct winner at a time, and add each sum once (lane 0) to its slot.
+__device__ __forceinline__ void warp_accumulate(int key, const U128 (&v)[4], unsigned long long (*slot)[8],
+                                                unsigned long long *acc, const float4 *cand, int lane)
+{
+    unsigned pending = __ballot_sync(0xffffffffu, key >= 0);
+    while (pending) {
+        const int leader = __ffs(pending) - 1;
+        const int k = __shfl_sync(0xffffffffu, key, leader);
+        const bool mine = (key == k);
+        pending &= ~__ballot_sync(0xffffffffu, mine);
+        U128 s[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) s[q] = mine ? v[q] : U128{0ull, 0ull};
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) s[q] = add_u128(s[q], shfl_down_u128(s[q], o));
+        if (lane == 0) {
+            unsigned long long *dst = (k < kSlots) ? &slot[k][0] : &acc[8 * (int64_t)__float_as_int(cand[k].w)];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) atomic_add_u128(dst + 2 * q, s[q]);
+        }
+    }
+}
+
 template <bool FINAL>
-__global__ void __launch_bounds__(kThreads) km_assign(KmArgs a, int t)
+__global__ void __launch_bounds__(kThreads, 1) km_assign(KmArgs a, int t)
 {
     if (a.ctl->error) return;
     if (!FINAL && a.ctl->converged) return;
 
-    extern __shared__ float4 cand[];  // n_mu entries: (qx, qy, qz, mu bits)
+    extern __shared__ float4 cand[];  // n_mu entries: (qx, qy, qz, mu bits), tile-local FP32 coordinates
     __shared__ unsigned long long slot[kSlots][8];
+    __shared__ unsigned short wlist[kThreads / 32][kWarpCap];
+    __shared__ int wcount[kThreads / 32];
     __shared__ unsigned int n_cand;
-    __shared__ unsigned int qmax_bits;
     __shared__ float minub_sh[kThreads / 32];
     __shared__ double red[kThreads / 32];
     __shared__ unsigned long long redu[kThreads / 32];
 
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int b = blockIdx.x;
     const int tz = b % a.ntz, ty = (b / a.ntz) % a.nty, tx = b / (a.ntz * a.nty);
     const int ix0 = tx * TX, iy0 = ty * TY, iz0 = tz * TZ;
     const int ex = min(TX, a.nx - ix0), ey = min(TY, a.ny - iy0), ez = min(TZ, a.nz - iz0);
     const double ox = __dmul_rn((double)ix0, a.hx), oy = __dmul_rn((double)iy0, a.hy), oz = __dmul_rn((double)iz0, a.hz);
+    const float hx = (float)a.hx, hy = (float)a.hy, hz = (float)a.hz;
     const float Px = (float)((ex - 1) * a.hx), Py = (float)((ey - 1) * a.hy), Pz = (float)((ez - 1) * a.hz);
 
-    if (tid == 0) {
-        n_cand = 0u;
-        qmax_bits = 0u;
-    }
-    // pass 1: min over centroids of the largest squared distance to the box
+    if (tid == 0) n_cand = 0u;
+    // ---- tile scan (FP32, conservative): min over centroids of the largest squared distance to the tile
+    const float ox32 = (float)ox, oy32 = (float)oy, oz32 = (float)oz;
+    const float dq = a.scan_err;
     float mub = INFINITY;
     for (int m = tid; m < a.n_mu; m += kThreads) {
-        const float qx = (float)__dsub_rn(a.cent[3 * m + 0], ox);
-        const float qy = (float)__dsub_rn(a.cent[3 * m + 1], oy);
-        const float qz = (float)__dsub_rn(a.cent[3 * m + 2], oz);
+        const float4 c = a.c32[m];
+        const float qx = c.x - ox32, qy = c.y - oy32, qz = c.z - oz32;
         const float ux = fmaxf(fabsf(qx), fabsf(Px - qx));
         const float uy = fmaxf(fabsf(qy), fabsf(Py - qy));
         const float uz = fmaxf(fabsf(qz), fabsf(Pz - qz));
         mub = fminf(mub, ux * ux + uy * uy + uz * uz);
     }
     for (int o = 16; o > 0; o >>= 1) mub = fminf(mub, __shfl_xor_sync(0xffffffffu, mub, o));
-    if ((tid & 31) == 0) minub_sh[tid >> 5] = mub;
+    if (lane == 0) minub_sh[warp] = mub;
     __syncthreads();
     float minub = minub_sh[0];
     for (int i = 1; i < kThreads / 32; ++i) minub = fminf(minub, minub_sh[i]);
-    // generous margins: rounding of q and of the float sums is ~1e-7 relative
-    const float cut = minub * 1.0001f + 1e-6f * (Px * Px + Py * Py + Pz * Pz) + 1e-30f;
-
-    // pass 2: keep centroids whose smallest squared distance to the box can win
+    const float sminub = sqrtf(minub);
+    // keep every centroid whose smallest squared distance to the tile can reach min UB: each
+    // coordinate carries an error <= dq, so LB and UB move by <= dq (2 sqrt(3) sqrt(.) + 3 dq)
     for (int m = tid; m < a.n_mu; m += kThreads) {
-        const float qx = (float)__dsub_rn(a.cent[3 * m + 0], ox);
-        const float qy = (float)__dsub_rn(a.cent[3 * m + 1], oy);
-        const float qz = (float)__dsub_rn(a.cent[3 * m + 2], oz);
+        const float4 c = a.c32[m];
+        const float qx = c.x - ox32, qy = c.y - oy32, qz = c.z - oz32;
         const float lx = fmaxf(0.f, fmaxf(-qx, qx - Px));
         const float ly = fmaxf(0.f, fmaxf(-qy, qy - Py));
         const float lz = fmaxf(0.f, fmaxf(-qz, qz - Pz));
-        const float lb = (lx * lx + ly * ly + lz * lz) * 0.9999f;
-        if (lb <= cut) {
+        const float lb = lx * lx + ly * ly + lz * lz;
+        const float margin = dq * (3.5f * (sqrtf(lb) + sminub) + 6.f * dq) + 1e-6f * (lb + minub) + 1e-30f;
+        if (lb <= minub + margin) {
             const unsigned j = atomicAdd(&n_cand, 1u);
-            cand[j] = make_float4(qx, qy, qz, __int_as_float(m));
-            const float qm = fmaxf(fabsf(qx), fmaxf(fabsf(qy), fabsf(qz)));
-            atomicMax(&qmax_bits, __float_as_uint(qm));
+            // accurate tile-local coordinates of the kept centroids (one FP64 subtraction each)
+            cand[j] = make_float4((float)__dsub_rn(a.cent[3 * m + 0], ox), (float)__dsub_rn(a.cent[3 * m + 1], oy),
+                                  (float)__dsub_rn(a.cent[3 * m + 2], oz), __int_as_float(m));
         }
     }
     __syncthreads();
@@ -274,89 +325,164 @@ __global__ void __launch_bounds__(kThreads) km_assign(KmArgs a, int t)
     if (!FINAL)
         for (int i = tid; i < ns * 8; i += kThreads) slot[i >> 3][i & 7] = 0ull;
 
-    // rigorous bound on |d_fp32 - d_exact| (+ FP64 rounding) for this box
-    const float Pmax = fmaxf(Px, fmaxf(Py, Pz));
-    const float Qmax = __uint_as_float(qmax_bits);
+    // ---- this warp's 4 x 4 x 4 sub-cube and its candidate list
+    const int sx = (warp >> 2) & 1, sy = (warp >> 1) & 1, sz = warp & 1;
+    const int bx = 4 * sx, by = 4 * sy, bz = 4 * sz;
+    const int wex = min(4, ex - bx), wey = min(4, ey - by), wez = min(4, ez - bz);
+    const bool wvalid = wex > 0 && wey > 0 && wez > 0;
+    const float Sx0 = bx * hx, Sy0 = by * hy, Sz0 = bz * hz;
+    const float Sx1 = Sx0 + (wex - 1) * hx, Sy1 = Sy0 + (wey - 1) * hy, Sz1 = Sz0 + (wez - 1) * hz;
+    float wub = INFINITY;
+    for (int j = lane; j < nc; j += 32) {
+        const float4 q = cand[j];
+        const float ux = fmaxf(fabsf(q.x - Sx0), fabsf(Sx1 - q.x));
+        const float uy = fmaxf(fabsf(q.y - Sy0), fabsf(Sy1 - q.y));
+        const float uz = fmaxf(fabsf(q.z - Sz0), fabsf(Sz1 - q.z));
+        wub = fminf(wub, ux * ux + uy * uy + uz * uz);
+    }
+    for (int o = 16; o > 0; o >>= 1) wub = fminf(wub, __shfl_xor_sync(0xffffffffu, wub, o));
+    // tile-local coordinates are accurate to ~1e-7 relative; the margin covers them and the float sums
+    const float Tmx = fmaxf(Px, fmaxf(Py, Pz));
+    const float wcut = wub * 1.0001f + 4e-6f * (Tmx * Tmx + wub) + 1e-30f;
+    int wn = 0;
+    float wq = 0.f;
+    for (int base = 0; base < nc; base += 32) {
+        const int j = base + lane;
+        bool keep = false;
+        if (j < nc) {
+            const float4 q = cand[j];
+            const float lx = fmaxf(0.f, fmaxf(Sx0 - q.x, q.x - Sx1));
+            const float ly = fmaxf(0.f, fmaxf(Sy0 - q.y, q.y - Sy1));
+            const float lz = fmaxf(0.f, fmaxf(Sz0 - q.z, q.z - Sz1));
+            keep = (lx * lx + ly * ly + lz * lz) * 0.9999f <= wcut;
+            if (keep) wq = fmaxf(wq, fmaxf(fabsf(q.x), fmaxf(fabsf(q.y), fabsf(q.z))));
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        const int pos = wn + __popc(bal & ((1u << lane) - 1u));
+        if (keep && pos < kWarpCap) wlist[warp][pos] = (unsigned short)j;
+        wn += __popc(bal);
+    }
+    for (int o = 16; o > 0; o >>= 1) wq = fmaxf(wq, __shfl_xor_sync(0xffffffffu, wq, o));
+    const bool use_w = wn <= kWarpCap;          // overflow: scan the whole tile list instead
+    const int cnt = use_w ? wn : nc;
+    if (!use_w) wq = 0.f;
+    if (!use_w)
+        for (int j = lane; j < nc; j += 32) {
+            const float4 q = cand[j];
+            wq = fmaxf(wq, fmaxf(fabsf(q.x), fmaxf(fabsf(q.y), fabsf(q.z))));
+        }
+    for (int o = 16; o > 0; o >>= 1) wq = fmaxf(wq, __shfl_xor_sync(0xffffffffu, wq, o));
+
+    // rigorous bound on |d_fp32 - d_exact| (+ FP64 rounding) for this warp: the point coordinates
+    // (integer offset x FP32 spacing) carry <= 2.01 u32 |p|, the candidates <= 1.0001 u32 |q|,
+    // their difference one more rounding, then three FP32 products and two FP32 additions
     const double u32 = 5.9604644775390625e-8;  // 2^-24
-    const double Tm = ((double)Pmax + (double)Qmax) * (1.0 + 4.0 * u32);
-    const double del = 2.0003 * u32 * ((double)Pmax + (double)Qmax);
+    const double Pm = (double)Tmx, Qm = (double)wq;
+    const double Tm = (Pm + Qm) * (1.0 + 4.0 * u32);
+    const double del = 1.01 * u32 * (2.01 * Pm + 1.0001 * Qm + (Pm + Qm)) + 8e-16 * a.lmax;
     const double E = 1.01 * (3.0 * del * (2.0 * Tm + del) + 9.001 * u32 * Tm * Tm + 1.6e-15 * 3.0 * Tm * Tm);
 
-    // this thread's point
-    const int lz = tid % TZ, ly = (tid / TZ) % TY, lx = tid / (TZ * TY);
-    const bool valid = lx < ex && ly < ey && lz < ez;
-    const int ix = ix0 + lx, iy = iy0 + ly, iz = iz0 + lz;
-    const int64_t r = ((int64_t)ix * a.ny + iy) * a.nz + iz;
+    // ---- the two points of this lane
+    const int lx2 = lane >> 4, ly = (lane >> 2) & 3, lz = lane & 3;
+    float px[2], py[2], pz[2], d1[2], d2[2];
+    int j1[2];
+    bool valid[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int dxl = lx2 + 2 * h;
+        valid[h] = wvalid && dxl < wex && ly < wey && lz < wez;
+        px[h] = (float)(bx + dxl) * hx;
+        py[h] = (float)(by + ly) * hy;
+        pz[h] = (float)(bz + lz) * hz;
+        d1[h] = INFINITY;
+        d2[h] = INFINITY;
+        j1[h] = 0;
+    }
+    __syncthreads();   // slots cleared
+    for (int i = 0; i < cnt; ++i) {
+        const int j = use_w ? (int)wlist[warp][i] : i;
+        const float4 q = cand[j];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float dx = px[h] - q.x, dy = py[h] - q.y, dz = pz[h] - q.z;
+            const float d = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            if (d < d1[h]) {
+                d2[h] = d1[h];
+                d1[h] = d;
+                j1[h] = j;
+            } else if (d < d2[h]) {
+                d2[h] = d;
+            }
+        }
+    }
+
     double jv = 0.0;
     unsigned long long my_ties = 0, my_ref = 0;
     unsigned int my_changed = 0;
-    __syncthreads();
-    if (valid && nc > 0) {
-        const double x = __dmul_rn((double)ix, a.hx), y = __dmul_rn((double)iy, a.hy), z = __dmul_rn((double)iz, a.hz);
-        const float px = (float)__dsub_rn(x, ox), py = (float)__dsub_rn(y, oy), pz = (float)__dsub_rn(z, oz);
-        float d1 = INFINITY, d2 = INFINITY;
-        int j1 = 0;
-        for (int j = 0; j < nc; ++j) {
-            const float4 q = cand[j];
-            const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
-            const float d = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            if (d < d1) {
-                d2 = d1;
-                d1 = d;
-                j1 = j;
-            } else if (d < d2) {
-                d2 = d;
-            }
-        }
-        const double dd1 = (double)d1;
-        const double gap = 2.0 * E + 2.0e-12 * fmax(dd1 + E, a.tie_floor) + 1.0e-14 * (dd1 + E);
-        int win_j = j1, win_mu = __float_as_int(cand[j1].w);
-        double win_d;
-        if ((double)d2 - dd1 > gap) {
-            win_d = dist2_fp64(x, y, z, a.cent[3 * win_mu], a.cent[3 * win_mu + 1], a.cent[3 * win_mu + 2]);
-        } else {
-            // FP64 decision over the candidates that can still win
-            my_ref = 1;
-            double b1 = INFINITY, b2 = INFINITY;
-            int bm = 0x7fffffff, bj = 0;
-            const double lim = dd1 + gap;
-            for (int j = 0; j < nc; ++j) {
-                const float4 q = cand[j];
-                const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
-                const float d = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                if ((double)d > lim) continue;
-                const int m = __float_as_int(q.w);
-                const double e = dist2_fp64(x, y, z, a.cent[3 * m], a.cent[3 * m + 1], a.cent[3 * m + 2]);
-                if (e < b1 || (e == b1 && m < bm)) {
-                    b2 = b1;
-                    b1 = e;
-                    bm = m;
-                    bj = j;
-                } else if (e < b2) {
-                    b2 = e;
+    const int s_fix = FINAL ? 0 : fixed_scale(a);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        int key = -1;
+        U128 v[4] = {{0ull, 0ull}, {0ull, 0ull}, {0ull, 0ull}, {0ull, 0ull}};
+        if (valid[h]) {
+            const int ix = ix0 + bx + lx2 + 2 * h, iy = iy0 + by + ly, iz = iz0 + bz + lz;
+            const int64_t r = ((int64_t)ix * a.ny + iy) * a.nz + iz;
+            const double x = __dmul_rn((double)ix, a.hx), y = __dmul_rn((double)iy, a.hy),
+                         z = __dmul_rn((double)iz, a.hz);
+            const double dd1 = (double)d1[h];
+            const double gap = 2.0 * E + 2.0e-12 * fmax(dd1 + E, a.tie_floor) + 1.0e-14 * (dd1 + E);
+            int win_j = j1[h], win_mu = __float_as_int(cand[j1[h]].w);
+            double win_d = 0.0;
+            if ((double)d2[h] - dd1 > gap) {
+                if (FINAL || a.want_obj)
+                    win_d = dist2_fp64(x, y, z, a.cent[3 * win_mu], a.cent[3 * win_mu + 1], a.cent[3 * win_mu + 2]);
+            } else {
+                // FP64 decision over the candidates that can still win
+                my_ref += 1;
+                double b1 = INFINITY, b2 = INFINITY;
+                int bm = 0x7fffffff, bj = 0;
+                const double lim = dd1 + gap;
+                for (int i = 0; i < cnt; ++i) {
+                    const int j = use_w ? (int)wlist[warp][i] : i;
+                    const float4 q = cand[j];
+                    const float dx = px[h] - q.x, dy = py[h] - q.y, dz = pz[h] - q.z;
+                    const float d = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                    if ((double)d > lim) continue;
+                    const int m = __float_as_int(q.w);
+                    const double e = dist2_fp64(x, y, z, a.cent[3 * m], a.cent[3 * m + 1], a.cent[3 * m + 2]);
+                    if (e < b1 || (e == b1 && m < bm)) {
+                        b2 = b1;
+                        b1 = e;
+                        bm = m;
+                        bj = j;
+                    } else if (e < b2) {
+                        b2 = e;
+                    }
                 }
+                win_j = bj;
+                win_mu = bm;
+                win_d = b1;
+                if (a.n_mu > 1 && __dsub_rn(b2, b1) <= 1e-12 * fmax(b1, a.tie_floor)) my_ties += 1;
             }
-            win_j = bj;
-            win_mu = bm;
-            win_d = b1;
-            if (a.n_mu > 1 && __dsub_rn(b2, b1) <= 1e-12 * fmax(b1, a.tie_floor)) my_ties = 1;
+            const double wr = a.w[r];
+            if (FINAL || a.want_obj) jv = __dadd_rn(jv, __dmul_rn(wr, win_d));
+            if (!FINAL) {
+                if (a.early_stop) {
+                    my_changed += (a.labels[r] != win_mu) ? 1u : 0u;
+                    a.labels[r] = win_mu;
+                }
+                key = win_j;
+                v[0] = fixed_of(wr, s_fix);
+                v[1] = fixed_of(__dmul_rn(wr, x), s_fix);
+                v[2] = fixed_of(__dmul_rn(wr, y), s_fix);
+                v[3] = fixed_of(__dmul_rn(wr, z), s_fix);
+            } else {
+                a.labels[r] = win_mu;
+                a.dist[r] = win_d;
+                atomicMin(&a.best[win_mu], (unsigned long long)__double_as_longlong(win_d));
+            }
         }
-        const double wr = a.w[r];
-        jv = __dmul_rn(wr, win_d);
-        if (!FINAL) {
-            my_changed = (a.labels[r] != win_mu) ? 1u : 0u;
-            a.labels[r] = win_mu;
-            const int s = fixed_scale(a);
-            unsigned long long *dst = (win_j < kSlots) ? &slot[win_j][0] : &a.acc[8 * (int64_t)win_mu];
-            atomic_add_u128(dst + 0, fixed_of(wr, s));
-            atomic_add_u128(dst + 2, fixed_of(__dmul_rn(wr, x), s));
-            atomic_add_u128(dst + 4, fixed_of(__dmul_rn(wr, y), s));
-            atomic_add_u128(dst + 6, fixed_of(__dmul_rn(wr, z), s));
-        } else {
-            a.labels[r] = win_mu;
-            a.dist[r] = win_d;
-            atomicMin(&a.best[win_mu], (unsigned long long)__double_as_longlong(win_d));
-        }
+        if (!FINAL) warp_accumulate(key, v, slot, a.acc, cand, lane);
     }
     const double jt = block_sum(jv, red);
     if (tid == 0) a.jpart[b] = jt;
@@ -417,6 +543,7 @@ __global__ void km_update(KmArgs a, int t, int n_tiles, double *objective)
         a.cent[3 * m + 0] = __ddiv_rn(u128_to_double(q[2], q[3]), sw);
         a.cent[3 * m + 1] = __ddiv_rn(u128_to_double(q[4], q[5]), sw);
         a.cent[3 * m + 2] = __ddiv_rn(u128_to_double(q[6], q[7]), sw);
+        a.c32[m] = make_float4((float)a.cent[3 * m], (float)a.cent[3 * m + 1], (float)a.cent[3 * m + 2], 0.f);
     }
 #pragma unroll
     for (int k = 0; k < 8; ++k) q[k] = 0ull;
@@ -473,7 +600,7 @@ __global__ void km_finish(KmArgs a, int max_iter, int n_tiles, int64_t *idx, dou
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 struct WsLayout {
-    size_t cent, acc, labels, dist, jpart, best, idx_u, ctl, total;
+    size_t cent, c32, acc, labels, dist, jpart, best, idx_u, ctl, total;
 };
 
 WsLayout ws_layout(int64_t n_r, int n_mu, int n_tiles)
@@ -481,6 +608,7 @@ WsLayout ws_layout(int64_t n_r, int n_mu, int n_tiles)
     WsLayout L;
     size_t o = 0;
     L.cent = o; o = align256(o + sizeof(double) * 3 * n_mu);
+    L.c32 = o; o = align256(o + sizeof(float4) * n_mu);
     L.acc = o; o = align256(o + sizeof(unsigned long long) * 8 * n_mu);
     L.labels = o; o = align256(o + sizeof(int32_t) * n_r);
     L.dist = o; o = align256(o + sizeof(double) * n_r);
@@ -552,6 +680,7 @@ extern "C" isdf_status isdf_kmeans(const double *w, int32_t nx, int32_t ny, int3
     a.nty = nty;
     a.ntz = ntz;
     a.cent = reinterpret_cast<double *>(base + L.cent);
+    a.c32 = reinterpret_cast<float4 *>(base + L.c32);
     a.acc = reinterpret_cast<unsigned long long *>(base + L.acc);
     a.labels = labels ? labels : reinterpret_cast<int32_t *>(base + L.labels);
     a.dist = reinterpret_cast<double *>(base + L.dist);
@@ -560,6 +689,10 @@ extern "C" isdf_status isdf_kmeans(const double *w, int32_t nx, int32_t ny, int3
     a.idx_u = reinterpret_cast<unsigned long long *>(base + L.idx_u);
     a.ctl = reinterpret_cast<KmCtl *>(base + L.ctl);
     a.early_stop = (flags & ISDF_KMEANS_EARLY_STOP) ? 1 : 0;
+    a.want_obj = objective ? 1 : 0;
+    a.lmax = lmax;
+    // |float(c) - c| + |float(o) - o| + rounding of their difference, for |c|, |o| <= L
+    a.scan_err = (float)(4.0 * 5.9604644775390625e-8 * lmax * 1.01);
 
     cudaStream_t st = as_stream(stream);
     const size_t smem = sizeof(float4) * (size_t)n_mu;

@@ -35,7 +35,8 @@ constexpr int TILE_B = TN * TK * 2;
 constexpr int STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
 constexpr long long WAIT_BUDGET = 200000000LL;
-constexpr int kApplySegment = 8;   // K chunks (of 64) per TMEM accumulation segment in the M^-1 GEMM  // SM cycles (~0.1 s); normal waits take microseconds
+constexpr int kApplySegment = 8;   // K chunks (of 64) per TMEM accumulation segment in the M^-1 GEMM
+constexpr int kGramSegment = 8;    // the same for each of the two Gram products  // SM cycles (~0.1 s); normal waits take microseconds
 
 struct MixScales {
     unsigned int maxabs_phi, maxrho_phi, maxabs_psi, maxrho_psi, maxabs_w;  // float bits
@@ -158,16 +159,22 @@ struct EpiParams {
     int *err;
 };
 
-// One persistent CTA per SM walks the output tiles (row-block
-// major, so concurrently running CTAs share A tiles in L2). Warp 0 lane 0
-// feeds the 3-stage shared-memory ring with TMA, warp 1 lane 0 issues the
-// MMAs, warps 2-5 run the epilogue. The TMEM accumulator is double-buffered
-// (tfull / tempty barriers), so the epilogue of one tile overlaps the MMAs of
-// the next.
-constexpr int EPI_WARPS = 4;
+// One persistent CTA per SM walks the output tiles (row-block major, so
+// concurrently running CTAs share A tiles in L2). Warp 0 lane 0 feeds the
+// 3-stage shared-memory ring with TMA, warp 1 lane 0 issues the MMAs, warps
+// 2-9 run the epilogue (warp w reads TMEM lane quarter w % 4 and one half of
+// the tile's columns). The K loop runs in segments of `seg` chunks; every
+// segment accumulates into a fresh TMEM buffer (the tensor cores' internal
+// FP32 accumulation never spans more than one segment) and the epilogue sums
+// the segments in registers with IEEE FP32 adds. The TMEM buffer is double
+// buffered (tfull / tempty barriers), so the epilogue of one segment overlaps
+// the MMAs of the next. DUAL (the Gram-Hadamard kernel) accumulates the
+// Phi and Psi products of a segment side by side and writes the split Y.
+constexpr int EPI_WARPS = 8;
+constexpr int GEMM_THREADS = 64 + 32 * EPI_WARPS;
 
 template <bool DUAL>
-__global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
+__global__ void __launch_bounds__(GEMM_THREADS, 1)
     tc_gemm_persist(const __grid_constant__ CUtensorMap a1h, const __grid_constant__ CUtensorMap a1l,
                     const __grid_constant__ CUtensorMap b1h, const __grid_constant__ CUtensorMap b1l,
                     const __grid_constant__ CUtensorMap a2h, const __grid_constant__ CUtensorMap a2l,
@@ -188,9 +195,10 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
     const uint32_t raw = tc::smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t *sbase = smem_raw + (base - raw);
-    constexpr uint32_t ACC = DUAL ? 2 * TN : TN;   // TMEM columns of one accumulator stage
+    constexpr int PARTS = DUAL ? 2 : 1;
+    constexpr uint32_t ACC = PARTS * TN;   // TMEM columns of one buffer
     constexpr uint32_t NCOLS = 2 * ACC;
-    const int total = (DUAL ? 2 : 1) * kchunks;
+    const int nseg = (kchunks + seg - 1) / seg;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -214,28 +222,28 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
     if (warp == 0) {
         if (lane == 0) {
             const CUtensorMap *maps[8] = {&a1h, &a1l, &b1h, &b1l, &a2h, &a2l, &b2h, &b2l};
-            for (int i = 0; i < (DUAL ? 8 : 4); ++i) tc::prefetch_map(maps[i]);
+            for (int i = 0; i < 4 * PARTS; ++i) tc::prefetch_map(maps[i]);
             int c = 0, issued = 0;
             for (int tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
                 const int m0 = (tile / n_tiles_n) * TM, n0 = (tile % n_tiles_n) * TN;
-                for (int q = 0; q < total; ++q, ++c) {
-                    const int s = c % STAGES, it = c / STAGES;
-                    if (!tc::mbar_wait(&empty_bar[s], (it & 1) ^ 1, WAIT_BUDGET)) {
-                        atomicExch(ep.err, 1);
-                        failed = 1;
-                        break;
-                    }
-                    const bool second = DUAL && q >= kchunks;
-                    const int kc = second ? q - kchunks : q;
-                    const CUtensorMap *const *mp = maps + (second ? 4 : 0);
-                    uint8_t *st = sbase + s * STAGE_BYTES;
-                    tc::mbar_expect_tx(&full_bar[s], STAGE_BYTES);
-                    tc::tma_load_2d(st, mp[0], &full_bar[s], kc * TK, a_row0 + m0);
-                    tc::tma_load_2d(st + TILE_A, mp[1], &full_bar[s], kc * TK, a_row0 + m0);
-                    tc::tma_load_2d(st + 2 * TILE_A, mp[2], &full_bar[s], kc * TK, n0);
-                    tc::tma_load_2d(st + 2 * TILE_A + TILE_B, mp[3], &full_bar[s], kc * TK, n0);
-                    issued = c + 1;
-                }
+                for (int sg = 0; sg < nseg && !failed; ++sg)
+                    for (int part = 0; part < PARTS && !failed; ++part)
+                        for (int kc = sg * seg; kc < min(kchunks, (sg + 1) * seg); ++kc, ++c) {
+                            const int s = c % STAGES, it = c / STAGES;
+                            if (!tc::mbar_wait(&empty_bar[s], (it & 1) ^ 1, WAIT_BUDGET)) {
+                                atomicExch(ep.err, 1);
+                                failed = 1;
+                                break;
+                            }
+                            const CUtensorMap *const *mp = maps + 4 * part;
+                            uint8_t *st = sbase + s * STAGE_BYTES;
+                            tc::mbar_expect_tx(&full_bar[s], STAGE_BYTES);
+                            tc::tma_load_2d(st, mp[0], &full_bar[s], kc * TK, a_row0 + m0);
+                            tc::tma_load_2d(st + TILE_A, mp[1], &full_bar[s], kc * TK, a_row0 + m0);
+                            tc::tma_load_2d(st + 2 * TILE_A, mp[2], &full_bar[s], kc * TK, n0);
+                            tc::tma_load_2d(st + 2 * TILE_A + TILE_B, mp[3], &full_bar[s], kc * TK, n0);
+                            issued = c + 1;
+                        }
             }
             for (int c2 = issued - STAGES > 0 ? issued - STAGES : 0; c2 < issued; ++c2)
                 tc::mbar_wait(&full_bar[c2 % STAGES], (c2 / STAGES) & 1, WAIT_BUDGET);
@@ -244,11 +252,6 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             constexpr uint32_t idesc = tc::idesc_f16(TM, TN);
-            // the K loop of a tile is cut into segments of `seg` chunks (DUAL: one segment per
-            // product); every segment starts a fresh TMEM accumulator, so the tensor cores'
-            // internal FP32 accumulation never runs over more than `seg` chunks
-            const int nseg = DUAL ? 1 : (total + seg - 1) / seg;
-            const int seg_len = DUAL ? total : seg;
             int c = 0, tl = 0;
             bool ok = true;
             for (int tile = blockIdx.x; tile < n_tiles && !failed && ok; tile += gridDim.x) {
@@ -261,33 +264,31 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
                         break;
                     }
                     tc::fence_after();
-                    const uint32_t dbase = tmem + (uint32_t)acc * ACC;
-                    const int q0 = sg * seg_len, q1 = min(total, q0 + seg_len);
-                    for (int q = q0; q < q1; ++q, ++c) {
-                        const int s = c % STAGES, it = c / STAGES;
-                        if (!tc::mbar_wait(&full_bar[s], it & 1, WAIT_BUDGET)) {
-                            atomicExch(ep.err, 1);
-                            failed = 1;
-                            ok = false;
-                            break;
-                        }
-                        tc::fence_after();
-                        const bool second = DUAL && q >= kchunks;
-                        const int kc = second ? q - kchunks : q;
-                        const bool first = DUAL ? (kc == 0) : (q == q0);
-                        const uint32_t d = dbase + (second ? (uint32_t)TN : 0u);
-                        const uint32_t sa = base + s * STAGE_BYTES;
-                        const uint64_t dah = tc::desc_sw128(sa), dal = tc::desc_sw128(sa + TILE_A);
-                        const uint64_t dbh = tc::desc_sw128(sa + 2 * TILE_A),
-                                       dbl = tc::desc_sw128(sa + 2 * TILE_A + TILE_B);
+                    for (int part = 0; part < PARTS && ok; ++part) {
+                        const uint32_t d = tmem + (uint32_t)acc * ACC + (uint32_t)part * TN;
+                        const int k0 = sg * seg, k1 = min(kchunks, (sg + 1) * seg);
+                        for (int kc = k0; kc < k1; ++kc, ++c) {
+                            const int s = c % STAGES, it = c / STAGES;
+                            if (!tc::mbar_wait(&full_bar[s], it & 1, WAIT_BUDGET)) {
+                                atomicExch(ep.err, 1);
+                                failed = 1;
+                                ok = false;
+                                break;
+                            }
+                            tc::fence_after();
+                            const uint32_t sa = base + s * STAGE_BYTES;
+                            const uint64_t dah = tc::desc_sw128(sa), dal = tc::desc_sw128(sa + TILE_A);
+                            const uint64_t dbh = tc::desc_sw128(sa + 2 * TILE_A),
+                                           dbl = tc::desc_sw128(sa + 2 * TILE_A + TILE_B);
 #pragma unroll
-                        for (int kk = 0; kk < TK / 16; ++kk) {
-                            const uint64_t o = (uint64_t)(2 * kk);
-                            tc::mma_f16(d, dah + o, dbh + o, idesc, (!first || kk > 0) ? 1u : 0u);
-                            tc::mma_f16(d, dah + o, dbl + o, idesc, 1u);
-                            tc::mma_f16(d, dal + o, dbh + o, idesc, 1u);
+                            for (int kk = 0; kk < TK / 16; ++kk) {
+                                const uint64_t o = (uint64_t)(2 * kk);
+                                tc::mma_f16(d, dah + o, dbh + o, idesc, (kc > k0 || kk > 0) ? 1u : 0u);
+                                tc::mma_f16(d, dah + o, dbl + o, idesc, 1u);
+                                tc::mma_f16(d, dal + o, dbh + o, idesc, 1u);
+                            }
+                            tc::mma_commit(&empty_bar[s]);
                         }
-                        tc::mma_commit(&empty_bar[s]);
                     }
                     if (!ok) break;
                     tc::mma_commit(&tfull[acc]);
@@ -299,90 +300,80 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
         }
         __syncwarp();
     } else {
-        const int quarter = warp & 3;
-        const int nseg = DUAL ? 1 : (total + seg - 1) / seg;
+        const int quarter = warp & 3;          // TMEM lane quarter this warp may access
+        const int half = (warp - 2) >> 2;      // which 64 of the tile's 128 columns
+        constexpr int HC = TN / 2;
         int tl = 0;
         for (int tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
             const int m0 = (tile / n_tiles_n) * TM, n0 = (tile % n_tiles_n) * TN;
             const int row = m0 + quarter * 32 + lane;
-            if (DUAL) {
+            float sa[HC], sb[DUAL ? HC : 1];
+#pragma unroll
+            for (int i = 0; i < HC; ++i) sa[i] = 0.f;
+#pragma unroll
+            for (int i = 0; i < (DUAL ? HC : 1); ++i) sb[i] = 0.f;
+            bool ok = true;
+            for (int sg = 0; sg < nseg; ++sg, ++tl) {
                 const int acc = tl & 1, use = tl >> 1;
-                ++tl;
                 if (!tc::mbar_wait(&tfull[acc], use & 1, WAIT_BUDGET)) {
                     atomicExch(ep.err, 1);
                     failed = 1;
+                    ok = false;
                     break;
                 }
                 tc::fence_after();
-                const uint32_t tl_addr = tmem + (uint32_t)acc * ACC + ((uint32_t)(quarter * 32) << 16);
-                const float fy = ep.sc->fy;
-#pragma unroll 1
-                for (int j = 0; j < TN / 32; ++j) {
-                    uint32_t r1[32], r2[32];
-                    tc::tmem_ld32(tl_addr + 32 * j, r1);
-                    tc::tmem_ld32(tl_addr + TN + 32 * j, r2);
-                    tc::tmem_wait_ld();
-                    if (j == TN / 32 - 1) {
-                        tc::fence_before();
-                        __syncwarp();
-                        if (lane == 0) tc::mbar_arrive(&tempty[acc]);
+                const uint32_t ta = tmem + (uint32_t)acc * ACC + ((uint32_t)(quarter * 32) << 16) + half * HC;
+#pragma unroll
+                for (int j = 0; j < HC / 16; ++j) {
+                    uint32_t r[16];
+                    tc::tmem_ld16(ta + 16 * j, r);
+                    if (DUAL) {
+                        uint32_t r2[16];
+                        tc::tmem_ld16(ta + TN + 16 * j, r2);
+                        tc::tmem_wait_ld();
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) sb[(16 * j + q) % (DUAL ? HC : 1)] += __uint_as_float(r2[q]);
+                    } else {
+                        tc::tmem_wait_ld();
                     }
-                    if (row < rows) {
-                        __half2 hv[16], lv[16];
 #pragma unroll
-                        for (int q = 0; q < 16; ++q) {
-                            const float ar = __uint_as_float(r1[2 * q]), ai = __uint_as_float(r1[2 * q + 1]);
-                            const float br = __uint_as_float(r2[2 * q]), bi = __uint_as_float(r2[2 * q + 1]);
-                            const float yr = (ar * br + ai * bi) * fy, yi = (ai * br - ar * bi) * fy;
-                            const __half2 h = __floats2half2_rn(yr, yi);
-                            const float2 hf = __half22float2(h);
-                            hv[q] = h;
-                            lv[q] = __floats2half2_rn(yr - hf.x, yi - hf.y);
-                        }
-                        uint4 *dh = reinterpret_cast<uint4 *>(ep.yh + row * ep.ldy + n0 + 32 * j);
-                        uint4 *dl = reinterpret_cast<uint4 *>(ep.yl + row * ep.ldy + n0 + 32 * j);
+                    for (int q = 0; q < 16; ++q) sa[16 * j + q] += __uint_as_float(r[q]);
+                }
+                tc::fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&tempty[acc]);
+            }
+            if (!ok) break;
+            if (row >= rows) continue;
+            if (DUAL) {
+                const float fy = ep.sc->fy;
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            dh[q] = reinterpret_cast<const uint4 *>(hv)[q];
-                            dl[q] = reinterpret_cast<const uint4 *>(lv)[q];
-                        }
+                for (int j = 0; j < HC / 32; ++j) {
+                    __half2 hv[16], lv[16];
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const float ar = sa[32 * j + 2 * q], ai = sa[32 * j + 2 * q + 1];
+                        const float br = sb[(32 * j + 2 * q) % (DUAL ? HC : 1)],
+                                    bi = sb[(32 * j + 2 * q + 1) % (DUAL ? HC : 1)];
+                        const float yr = (ar * br + ai * bi) * fy, yi = (ai * br - ar * bi) * fy;
+                        const __half2 h = __floats2half2_rn(yr, yi);
+                        const float2 hf = __half22float2(h);
+                        hv[q] = h;
+                        lv[q] = __floats2half2_rn(yr - hf.x, yi - hf.y);
+                    }
+                    uint4 *dh = reinterpret_cast<uint4 *>(ep.yh + row * ep.ldy + n0 + half * HC + 32 * j);
+                    uint4 *dl = reinterpret_cast<uint4 *>(ep.yl + row * ep.ldy + n0 + half * HC + 32 * j);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        dh[q] = reinterpret_cast<const uint4 *>(hv)[q];
+                        dl[q] = reinterpret_cast<const uint4 *>(lv)[q];
                     }
                 }
             } else {
-                // sum the segments of this tile in registers (IEEE FP32 adds), then store
-                float sum[TN];
+                const float ft = ep.sc->ftheta;
+                float2 *dst = ep.theta + row * ep.ld_theta + ((n0 + half * HC) >> 1);
 #pragma unroll
-                for (int i = 0; i < TN; ++i) sum[i] = 0.f;
-                bool ok = true;
-                for (int sg = 0; sg < nseg; ++sg, ++tl) {
-                    const int acc = tl & 1, use = tl >> 1;
-                    if (!tc::mbar_wait(&tfull[acc], use & 1, WAIT_BUDGET)) {
-                        atomicExch(ep.err, 1);
-                        failed = 1;
-                        ok = false;
-                        break;
-                    }
-                    tc::fence_after();
-                    const uint32_t tl_addr = tmem + (uint32_t)acc * ACC + ((uint32_t)(quarter * 32) << 16);
-#pragma unroll
-                    for (int j = 0; j < TN / 32; ++j) {
-                        uint32_t r[32];
-                        tc::tmem_ld32(tl_addr + 32 * j, r);
-                        tc::tmem_wait_ld();
-#pragma unroll
-                        for (int q = 0; q < 32; ++q) sum[32 * j + q] += __uint_as_float(r[q]);
-                    }
-                    tc::fence_before();
-                    __syncwarp();
-                    if (lane == 0) tc::mbar_arrive(&tempty[acc]);
-                }
-                if (!ok) break;
-                if (row < rows) {
-                    const float ft = ep.sc->ftheta;
-                    float2 *dst = ep.theta + row * ep.ld_theta + (n0 >> 1);
-#pragma unroll
-                    for (int q = 0; q < TN / 2; ++q) dst[q] = make_float2(sum[2 * q] * ft, sum[2 * q + 1] * ft);
-                }
+                for (int q = 0; q < HC / 2; ++q) dst[q] = make_float2(sa[2 * q] * ft, sa[2 * q + 1] * ft);
             }
         }
     }
@@ -550,12 +541,12 @@ isdf_status mixed_fit(isdf_plan *p, int64_t row_begin, int64_t row_count, void *
         const int n_tiles_n = (2 * nm) / TN, m_tiles = (rows + TM - 1) / TM;
         const int n_tiles = n_tiles_n * m_tiles;
         const unsigned grid = (unsigned)(n_tiles < num_sms() ? n_tiles : num_sms());
-        const unsigned threads = 64 + 32 * EPI_WARPS;
+        const unsigned threads = GEMM_THREADS;
         // a10: Y_b = (Phi_b Phi_mu^H) o conj(Psi_b Psi_mu^H), written split for the next GEMM
         timer_start(p, 0, st);
         tc_gemm_persist<true><<<grid, threads, SMEM_BYTES, st>>>(b->m_a1h, b->m_a1l, b->m_b1h, b->m_b1l, b->m_a2h,
                                                                  b->m_a2l, b->m_b2h, b->m_b2l, (2 * n) / TK, (int)r0,
-                                                                 rows, n_tiles_n, n_tiles, 0, ep); isdf_note_launch();
+                                                                 rows, n_tiles_n, n_tiles, kGramSegment, ep); isdf_note_launch();
         timer_stop(p, 0, st, rows);
         ISDF_LAUNCH_CHECK();
         // a11: Theta_b = Y_b M^-1

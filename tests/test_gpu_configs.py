@@ -4,7 +4,8 @@ waterbox (96^3 grid, 256 complex64 orbitals, 2048 points, T = 100): the whole
 K-means bit-exact against the oracle, mixed Theta on sampled rows <= 1e-5.
 adjoint (72^3, 192 orbitals, 1536 points fixed from a prior K-means): the
 FP64 adjoint of the exchange-like surrogate against the oracle gradient and
-central finite differences (h = 1e-6, 32 seeded directions, FP64 fits).
+central finite differences (h = 1e-6 relative to the orbital norms, 32 seeded
+directions, FP64 fits).
 silica (128^3, 1024 orbitals, 4096 points): K-means checked through
 properties that hold at any size (labels are nearest centroids, centroids are
 weighted means of their members, snapped points are nearest members), and
@@ -118,9 +119,11 @@ def test_adjoint_config_finite_differences(isdf):
     for _ in range(32):
         Dp = torch.randn(P.shape, dtype=torch.complex128, device=DEV, generator=gen)
         Dq = torch.randn(Q.shape, dtype=torch.complex128, device=DEV, generator=gen)
-        nrm = torch.sqrt(torch.linalg.vector_norm(Dp) ** 2 + torch.linalg.vector_norm(Dq) ** 2)
-        Dp /= nrm
-        Dq /= nrm
+        # scaled to the orbitals' norms, so that h is a relative step: with unit-norm directions the
+        # directional derivative is ~100x smaller than here and the FP64 rounding of the loss
+        # (eps |L| / h) alone exceeds 1e-6 of it on this problem size
+        Dp *= torch.linalg.vector_norm(P) / torch.linalg.vector_norm(Dp)
+        Dq *= torch.linalg.vector_norm(Q) / torch.linalg.vector_norm(Dq)
         fd = (loss_at(+1, Dp, Dq, h) - loss_at(-1, Dp, Dq, h)) / (2 * h)
         an = torch.real(torch.vdot(gphi.flatten(), Dp.flatten()) + torch.vdot(gpsi.flatten(), Dq.flatten())).item()
         worst = max(worst, abs(fd - an) / max(abs(an), 1e-30))
