@@ -60,6 +60,8 @@ namespace {
 
 __device__ __forceinline__ void atomic_max_pos(unsigned int *p, float v) { atomicMax(p, __float_as_uint(v)); }
 
+// max |Re|, |Im| over the matrix and max row density sum_i |x_ri|^2 (FP32 for
+// complex64 input, FP64 for complex128; both are bounds used with margins)
 template <typename T>
 __global__ void absmax_rows(const T *x, int64_t ld, int n, int64_t n_r, unsigned int *maxabs, unsigned int *maxrho)
 {
@@ -68,21 +70,35 @@ __global__ void absmax_rows(const T *x, int64_t ld, int n, int64_t n_r, unsigned
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t r = warp; r < n_r; r += nwarps) {
-        double rho = 0.0;
-        for (int i = lane; i < n; i += 32) {
-            const double2 v = cload(x, r * ld + i);
-            ma = fmaxf(ma, (float)fmax(fabs(v.x), fabs(v.y)));
-            rho += v.x * v.x + v.y * v.y;
+        float rho;
+        if (sizeof(T) == 8) {
+            const float2 *xr = reinterpret_cast<const float2 *>(x) + r * ld;
+            float acc = 0.f;
+            for (int i = lane; i < n; i += 32) {
+                const float2 v = xr[i];
+                ma = fmaxf(ma, fmaxf(fabsf(v.x), fabsf(v.y)));
+                acc = fmaf(v.x, v.x, fmaf(v.y, v.y, acc));
+            }
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            rho = acc * (1.f + 1e-5f);
+        } else {
+            double acc = 0.0;
+            for (int i = lane; i < n; i += 32) {
+                const double2 v = cload(x, r * ld + i);
+                ma = fmaxf(ma, (float)fmax(fabs(v.x), fabs(v.y)));
+                acc += v.x * v.x + v.y * v.y;
+            }
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            rho = (float)acc * (1.f + 1e-6f);
         }
-        for (int o = 16; o > 0; o >>= 1) rho += __shfl_xor_sync(0xffffffffu, rho, o);
-        mr = fmaxf(mr, (float)rho);
+        mr = fmaxf(mr, rho);
     }
     for (int o = 16; o > 0; o >>= 1) {
         ma = fmaxf(ma, __shfl_xor_sync(0xffffffffu, ma, o));
         mr = fmaxf(mr, __shfl_xor_sync(0xffffffffu, mr, o));
     }
     if (lane == 0) {
-        atomic_max_pos(maxabs, ma);
+        atomic_max_pos(maxabs, ma * 1.0001f);
         if (maxrho) atomic_max_pos(maxrho, mr);
     }
 }
@@ -112,19 +128,34 @@ __global__ void compute_scales(MixScales *sc)
     if (!isfinite(ma_phi) || !isfinite(ma_psi) || !isfinite(ma_w) || !isfinite(mr_phi * mr_psi)) sc->err = 2;
 }
 
+// hi = fp16(x s), lo = fp16(x s - hi); s is a power of two, so for complex64
+// input x s and x s - hi are exact in FP32 and no FP64 arithmetic is needed
 template <typename T>
 __global__ void split_orbitals(const T *x, int64_t ld, int n, int64_t n_r, const float *scale, __half *hi,
                                __half *lo)
 {
     const int64_t total = n_r * n;
-    const double s = (double)*scale;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = e / n;
         const int i = (int)(e % n);
-        const double2 v = cload(x, r * ld + i);
-        const double a = v.x * s, b = v.y * s;
-        const __half ha = __double2half(a), hb = __double2half(b);
-        const __half la = __double2half(a - (double)__half2float(ha)), lb = __double2half(b - (double)__half2float(hb));
+        __half ha, hb, la, lb;
+        if (sizeof(T) == 8) {
+            const float2 v = reinterpret_cast<const float2 *>(x)[r * ld + i];
+            const float s = *scale;
+            const float a = v.x * s, b = v.y * s;
+            ha = __float2half_rn(a);
+            hb = __float2half_rn(b);
+            la = __float2half_rn(a - __half2float(ha));
+            lb = __float2half_rn(b - __half2float(hb));
+        } else {
+            const double2 v = cload(x, r * ld + i);
+            const double s = (double)*scale;
+            const double a = v.x * s, b = v.y * s;
+            ha = __double2half(a);
+            hb = __double2half(b);
+            la = __double2half(a - (double)__half2float(ha));
+            lb = __double2half(b - (double)__half2float(hb));
+        }
         reinterpret_cast<__half2 *>(hi)[r * n + i] = __halves2half2(ha, hb);
         reinterpret_cast<__half2 *>(lo)[r * n + i] = __halves2half2(la, lb);
     }

@@ -4,11 +4,12 @@ waterbox (96^3 grid, 256 complex64 orbitals, 2048 points, T = 100): the whole
 K-means bit-exact against the oracle, mixed Theta on sampled rows <= 1e-5.
 adjoint (72^3, 192 orbitals, 1536 points fixed from a prior K-means): the
 FP64 adjoint of the exchange-like surrogate against the oracle gradient and
-central finite differences (h = 1e-6 relative to the orbital norms, 32 seeded
-directions, FP64 fits).
+central finite differences on 32 seeded directions scaled to the orbital
+norms (h = 1e-5 within 1e-6; h = 1e-6 within its FP64 noise floor, 1e-5).
 silica (128^3, 1024 orbitals, 4096 points): K-means checked through
-properties that hold at any size (labels are nearest centroids, centroids are
-weighted means of their members, snapped points are nearest members), and
+properties that hold at any size (sampled labels are the nearest centroids
+under the FP64 formula, every cluster is non-empty, snapped points are
+distinct members nearest to their centroids), and
 Theta fitted in blocks of 131,072 rows, never fully resident, <= 1e-5 against
 the oracle on a 16,384-row sample."""
 import numpy as np
@@ -113,21 +114,20 @@ def test_adjoint_config_finite_differences(isdf):
         fplan.fit_theta(out=theta)
         return w.dV * torch.real(torch.sum(theta.conj() * (theta @ Kd.T))).item()
 
-    h = 1e-6
+    # FP64 rounding of the loss (~1e-14 relative on 5.7e8 terms) divided by 2h is ~3e-6 of the
+    # directional derivative at h = 1e-6 on this size: the 1e-6 check uses h = 1e-5 (truncation
+    # ~1e-10), and h = 1e-6 is held to its noise floor
     gen = torch.Generator(device=DEV).manual_seed(4242)
-    worst = 0.0
     for _ in range(32):
         Dp = torch.randn(P.shape, dtype=torch.complex128, device=DEV, generator=gen)
         Dq = torch.randn(Q.shape, dtype=torch.complex128, device=DEV, generator=gen)
-        # scaled to the orbitals' norms, so that h is a relative step: with unit-norm directions the
-        # directional derivative is ~100x smaller than here and the FP64 rounding of the loss
-        # (eps |L| / h) alone exceeds 1e-6 of it on this problem size
+        # scaled to the orbitals' norms, so that h is a relative step
         Dp *= torch.linalg.vector_norm(P) / torch.linalg.vector_norm(Dp)
         Dq *= torch.linalg.vector_norm(Q) / torch.linalg.vector_norm(Dq)
-        fd = (loss_at(+1, Dp, Dq, h) - loss_at(-1, Dp, Dq, h)) / (2 * h)
         an = torch.real(torch.vdot(gphi.flatten(), Dp.flatten()) + torch.vdot(gpsi.flatten(), Dq.flatten())).item()
-        worst = max(worst, abs(fd - an) / max(abs(an), 1e-30))
-        assert abs(fd - an) <= 1e-6 * abs(an), (fd, an)
+        for h, tol in ((1e-5, 1e-6), (1e-6, 1e-5)):
+            fd = (loss_at(+1, Dp, Dq, h) - loss_at(-1, Dp, Dq, h)) / (2 * h)
+            assert abs(fd - an) <= tol * abs(an), (h, fd, an)
     fplan.check()
 
 
@@ -145,7 +145,6 @@ def test_silica_kmeans_properties_and_blocked_mixed_theta(isdf):
     cen = km["centroids"].cpu().numpy()
     assert len(set(idx.tolist())) == w.n_mu
     x = O.grid_coords(shape, cell)
-    wt_h = wt.cpu().numpy()
     # labels of sampled points are their nearest centroids under the FP64 formula (lowest index on ties)
     rs = W.subsample_rows(w.n_r, 4096, 99)
     d = ((x[rs][:, None, :] - cen[None, :, :]) ** 2).sum(-1)
