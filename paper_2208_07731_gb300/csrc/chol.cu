@@ -19,55 +19,65 @@ constexpr int DT = 128;   // threads of the diagonal-block kernel
 // Factor the nb x nb diagonal block at (k, k) of A (lower triangle used),
 // write L_kk back (upper part zeroed) and L_kk^-1 into Linv at (k, k).
 // A pivot not above 1e-13 of M's original diagonal entry (M0) is reported.
+//
+// Latency matters more than throughput here (one block per launch, on the
+// critical path of the factorisation), so each elimination step costs one
+// barrier: step j subtracts T[i][j] conj(T[c][j]) / d_j from the trailing
+// triangle with the unscaled column j, and the columns are scaled by
+// 1/sqrt(d_j) once at the end. The inverse is computed column by column; the
+// 4 threads of a column sit in one warp, so it needs no block barrier.
 __global__ void __launch_bounds__(DT) potrf_diag(double2 *A, int64_t lda, const double2 *M0, double2 *Linv,
                                                 int64_t ldi, int k, int nb, DeviceStatus *st)
 {
     __shared__ double2 T[NB][NB + 1];
     __shared__ double2 I[NB][NB + 1];
-    __shared__ double rdiag[NB];   // 1 / L_jj (FP64 division is slow on this part: one per pivot)
-    __shared__ int fail;
+    __shared__ double d0s[NB];     // original diagonal entries of M
+    __shared__ double rdiag[NB];   // 1 / L_jj
     if (st->code != 0) return;
     const int tid = threadIdx.x;
-    if (tid == 0) fail = 0;
     for (int e = tid; e < NB * NB; e += DT) {
         const int i = e / NB, j = e % NB;
         T[i][j] = (i < nb && j <= i) ? A[(int64_t)(k + i) * lda + (k + j)] : make_double2(0.0, 0.0);
     }
+    if (tid < nb) d0s[tid] = M0[(int64_t)(k + tid) * lda + (k + tid)].x;
     __syncthreads();
-    // right-looking factorisation; thread t owns rows i = t % NB and column slice t / NB
-    const int my_row = tid % NB, slice = tid / NB;   // 4 slices of the columns
+    // thread t updates row i = t % NB, columns c = j + 1 + slice, step 4
+    const int my_row = tid % NB, slice = tid / NB;
     for (int j = 0; j < nb; ++j) {
-        if (tid == 0) {
-            const double d = T[j][j].x;
-            const double d0 = M0[(int64_t)(k + j) * lda + (k + j)].x;
-            if (!(d > 1e-13 * d0) || isinf(d)) {
-                set_status(st, isnan(d) ? ISDF_ERR_NONFINITE : ISDF_ERR_NOT_HPD, k + j);
-                fail = 1;
-            } else {
-                const double l = sqrt(d);
-                T[j][j] = make_double2(l, 0.0);
-                rdiag[j] = 1.0 / l;
-            }
+        const double d = T[j][j].x;
+        if (!(d > 1e-13 * d0s[j]) || isinf(d)) {
+            if (tid == 0) set_status(st, isnan(d) ? ISDF_ERR_NONFINITE : ISDF_ERR_NOT_HPD, k + j);
+            return;   // uniform: every thread read the same pivot
         }
-        __syncthreads();
-        if (fail) return;
-        const double rj = rdiag[j];
-        if (slice == 0 && my_row > j && my_row < nb) T[my_row][j] = make_double2(T[my_row][j].x * rj, T[my_row][j].y * rj);
-        __syncthreads();
-        // T[i][c] -= T[i][j] conj(T[c][j]) for j < c <= i
         if (my_row > j && my_row < nb) {
+            const double r = 1.0 / d;
             const double2 a = T[my_row][j];
+            const double2 ar = make_double2(a.x * r, a.y * r);
             for (int c = j + 1 + slice; c <= my_row; c += DT / NB) {
                 const double2 b = T[c][j];
-                T[my_row][c].x -= a.x * b.x + a.y * b.y;
-                T[my_row][c].y -= a.y * b.x - a.x * b.y;
+                T[my_row][c].x -= ar.x * b.x + ar.y * b.y;
+                T[my_row][c].y -= ar.y * b.x - ar.x * b.y;
             }
         }
         __syncthreads();
     }
-    // inverse by forward substitution, row by row:
-    // I[i][c] = (delta_ic - sum_{c <= l < i} T[i][l] I[l][c]) / T[i][i];
-    // the columns of a row are independent and each sum is split over 4 threads
+    // L_jj = sqrt(d_j), L_ij = T_ij / sqrt(d_j)
+    if (tid < nb) {
+        const double l = sqrt(T[tid][tid].x);
+        rdiag[tid] = 1.0 / l;
+        T[tid][tid] = make_double2(l, 0.0);
+    }
+    __syncthreads();
+    for (int e = tid; e < NB * NB; e += DT) {
+        const int i = e / NB, j = e % NB;
+        if (i < nb && j < i) {
+            const double r = rdiag[j];
+            T[i][j] = make_double2(T[i][j].x * r, T[i][j].y * r);
+        }
+    }
+    __syncthreads();
+    // inverse by forward substitution down each column c:
+    // I[i][c] = (delta_ic - sum_{c <= l < i} T[i][l] I[l][c]) / T[i][i]
     {
         const int c = tid >> 2, part = tid & 3;
         for (int i = 0; i < NB; ++i) {
@@ -90,9 +100,10 @@ __global__ void __launch_bounds__(DT) potrf_diag(double2 *A, int64_t lda, const 
                 }
                 I[i][c] = v;
             }
-            __syncthreads();
+            __syncwarp();
         }
     }
+    __syncthreads();
     for (int e = tid; e < nb * nb; e += DT) {
         const int i = e / nb, j = e % nb;
         A[(int64_t)(k + i) * lda + (k + j)] = j <= i ? T[i][j] : make_double2(0.0, 0.0);

@@ -20,6 +20,8 @@
 //    winner, then per CTA in shared memory, then in global memory, with the
 //    carry of the low word detected by the adding thread; the update kernel
 //    rounds each sum to FP64 and divides once.
+#include <mutex>
+
 #include "common.cuh"
 
 namespace {
@@ -630,6 +632,25 @@ int bits_of(uint64_t v)
     return b;
 }
 
+// the dynamic shared-memory limit of the assign kernels, set once per device
+// (so that later calls issue only stream-ordered work and can be captured)
+isdf_status set_kernel_attributes()
+{
+    static std::mutex lock;
+    static bool done[64] = {};
+    int dev = 0;
+    ISDF_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return ISDF_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> guard(lock);
+    if (done[dev]) return ISDF_OK;
+    ISDF_CUDA_TRY(cudaFuncSetAttribute(km_assign<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(sizeof(float4) * kMaxMu)));
+    ISDF_CUDA_TRY(cudaFuncSetAttribute(km_assign<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(sizeof(float4) * kMaxMu)));
+    done[dev] = true;
+    return ISDF_OK;
+}
+
 }  // namespace
 
 extern "C" isdf_status isdf_kmeans_workspace(int32_t nx, int32_t ny, int32_t nz, int32_t n_mu, size_t *ws_bytes)
@@ -696,10 +717,7 @@ extern "C" isdf_status isdf_kmeans(const double *w, int32_t nx, int32_t ny, int3
 
     cudaStream_t st = as_stream(stream);
     const size_t smem = sizeof(float4) * (size_t)n_mu;
-    ISDF_CUDA_TRY(cudaFuncSetAttribute(km_assign<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(sizeof(float4) * kMaxMu)));
-    ISDF_CUDA_TRY(cudaFuncSetAttribute(km_assign<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(sizeof(float4) * kMaxMu)));
+    ISDF_TRY(set_kernel_attributes());
     const int64_t nmax = n_r > n_mu ? n_r : n_mu;
     const unsigned ginit = (unsigned)((nmax + 255) / 256 < 4096 ? (nmax + 255) / 256 : 4096);
     km_init<<<ginit, 256, 0, st>>>(a, init_idx, n_r); isdf_note_launch();

@@ -240,8 +240,13 @@ isdf_status zgemm_auto(const ZGemm &g_in, double2 *partial, size_t partial_elems
     const int nt = tiles(g.tile);
     g.splits = 1;
     if (!g.dual && partial) {
+        // tiles with a triangular K range carry up to twice the average work, so they get more
+        // splits; the target is ~8 CTAs per SM of balanced work
+        const int target = (g.kmode != ZG_K_ALL || g.k_to_m_end) ? 8 * sms : 4 * sms;
         int s = 1;
-        while (nt * s * 2 <= 4 * sms && g.K / (s * 2) >= 64 && (size_t)(s * 2) * g.M * g.N <= partial_elems) s *= 2;
+        while (s < 16 && nt * s * 2 <= target && g.K / (s * 2) >= 64 &&
+               (size_t)(s * 2) * g.M * g.N <= partial_elems)
+            s *= 2;
         if (s > 1) {
             g.splits = s;
             g.partial = partial;
