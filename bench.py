@@ -55,6 +55,12 @@ def algorithmic_flops(w):
     return {"gram": 16.0 * w.n_orb * w.n_mu, "apply": 8.0 * w.n_mu * w.n_mu}
 
 
+# DRAM bytes (read + write) per launch of the two tensor-core kernels from one ncu capture
+# (profiles/tc_gemm_medium.md); only valid for the workload and kernel version profiled there
+NCU_TRAFFIC = {("medium", "apply"): 925.097984e6 + 869.177600e6,
+               ("medium", "gram"): 246.058752e6 + 859.929856e6}
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -170,6 +176,67 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU path
+def run_adjoint(args):
+    """Config-3 measurement: the exchange-like surrogate L = dV sum_r Re[conj(Theta_r) K Theta_r] and its
+    gradients dL/dPhi, dL/dPsi at fixed interpolation points (taken from a prior K-means), per step:
+    plan update (gather, M, Cholesky, M^-1) + blocked backward that recomputes Theta + finalize."""
+    import torch
+
+    from paper_2208_07731_gb300 import build
+    build.build()
+    import paper_2208_07731_gb300 as isdf
+    from paper_2208_07731_gb300 import workload as W
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    w = W.WORKLOADS[args.workload]
+    phi, psi = W.make_pair(w, device=dev)
+    phi, psi = W.storage(phi, w).contiguous(), W.storage(psi, w).contiguous()
+    wt = isdf.weights(phi, psi)
+    init = torch.from_numpy(W.init_indices(wt.cpu().numpy(), w.n_mu, 1000 + w.seed))
+    idx = isdf.kmeans(wt, (w.n,) * 3, (w.L,) * 3, w.n_mu, init, w.iters)["idx"]
+    K = torch.from_numpy(W.loss_matrix(w.n_mu, 3000 + w.seed)).to(dev)
+    res = {}
+    for mode in ("mixed", "fp64"):
+        plan = isdf.Plan(phi, psi, idx, mode=mode, max_rows=131072)
+
+        def step():
+            plan.update(idx)
+            return isdf.surrogate_loss_and_grad(plan, K, w.dV, block=131072)
+
+        for _ in range(max(1, min(args.warmup, 2) if mode == "fp64" else args.warmup)):
+            step()
+        torch.cuda.synchronize()
+        steps = args.steps if mode == "mixed" else max(1, min(args.steps, 2))
+        l0 = isdf.kernel_launches()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            loss, gphi, gpsi = step()
+        e1.record()
+        torch.cuda.synchronize()
+        plan.check()
+        res[mode] = {"ms": e0.elapsed_time(e1) / steps, "launches": (isdf.kernel_launches() - l0) // steps,
+                     "loss": loss.item(), "gphi": gphi, "gpsi": gpsi, "steps": steps}
+        plan.close()
+    a, b = res["mixed"], res["fp64"]
+    rel = float(torch.sqrt((torch.linalg.vector_norm(a["gphi"] - b["gphi"]) ** 2 +
+                            torch.linalg.vector_norm(a["gpsi"] - b["gpsi"]) ** 2) /
+                           (torch.linalg.vector_norm(b["gphi"]) ** 2 + torch.linalg.vector_norm(b["gpsi"]) ** 2)))
+    line = {"metric": "ISDF Θ-fit adjoint evaluations/sec (surrogate loss + dL/dΦ, dL/dΨ at fixed points)",
+            "value": 1e3 / a["ms"], "unit": "gradients/s", "n_gpus": 1, "steps": a["steps"], "warmup": args.warmup,
+            "ms_per_step": a["ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f16 hi+lo split x3 on tcgen05 (f32 accumulate) for every adjoint GEMM; f64 M, Cholesky, M^-1 "
+                     "and f64 gradient accumulation",
+            "data": "synthetic: seeded random plane-wave Bloch orbitals, orthonormalised",
+            "config": {"workload": w.name, "grid": f"{w.n}^3", "n_orb": w.n_orb, "n_mu": w.n_mu,
+                       "block_rows": 131072},
+            "gpu_launches": a["launches"],
+            "fp64": {"value": 1e3 / b["ms"], "ms_per_step": b["ms"], "steps": b["steps"]},
+            "grad_rel_diff_mixed_vs_fp64": rel, "loss": {"mixed": a["loss"], "fp64": b["loss"]}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -204,7 +271,8 @@ def run_ours(args):
     shape, cell = (w.n,) * 3, (w.L,) * 3
     wbuf = torch.empty(w.n_r, dtype=torch.float64, device=dev)
     isdf.weights(phi, psi, out=wbuf)
-    init = torch.from_numpy(W.init_indices(wbuf.cpu().numpy(), w.n_mu, 1000 + w.seed))
+    init_h = W.init_indices(wbuf.cpu().numpy(), w.n_mu, 1000 + w.seed)
+    init = torch.from_numpy(init_h).to(dev)  # device-resident: no host copy inside a captured step
     ws = torch.empty(isdf.kmeans_workspace_bytes(shape, w.n_mu), dtype=torch.uint8, device=dev)
     flops = algorithmic_flops(w)
     pk = peaks()
@@ -312,8 +380,9 @@ def run_ours(args):
             else:
                 peak = 1.25
                 bound, src = "alu", "FP64 pipe, nominal 1.25 TFLOP/s (no FP64 tensor-core MMA on GB300)"
+            traffic = NCU_TRAFFIC.get((w.name, name)) if mode == "mixed" else None
             out[name] = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None, "peak_source": src,
+                         "frac": achieved / peak, "traffic": traffic, "peak_source": src,
                          "launches": n_k, "ms_per_launch": ms_k / n_k,
                          "algorithmic_flops_per_launch": per_launch_flops}
         return out
@@ -390,7 +459,7 @@ def run_ours(args):
         import oracle as O
         O.load()
         phi_h, psi_h = phi.cpu().numpy(), psi.cpu().numpy()
-        total, parts, sample = oracle_sample(w, phi_h, psi_h, init.numpy())
+        total, parts, sample = oracle_sample(w, phi_h, psi_h, init_h)
         line["cpu_baseline"] = {"value": 1.0 / total, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                                 "sample": sample, "seconds_by_stage": parts}
         # Theta error of both GPU modes against the oracle on a row sample
@@ -417,6 +486,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "adjoint":
+        return run_adjoint(args)
     return run_ours(args)
 
 

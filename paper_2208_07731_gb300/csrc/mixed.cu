@@ -41,8 +41,9 @@ constexpr int kGramSegment = 8;    // the same for each of the two Gram products
 struct MixScales {
     unsigned int maxabs_phi, maxrho_phi, maxabs_psi, maxrho_psi, maxabs_w;  // float bits
     float s_phi, s_psi, s_w, fy, ftheta;
+    float s_y, inv_phi2, inv_psi2;   // scale of the split Y; 1/s_phi^2, 1/s_psi^2
     int err;
-    int pad[5];
+    int pad[2];
 };
 
 }  // namespace
@@ -54,6 +55,14 @@ struct MixedBuffers {
     __half *yh, *yl;                 // max_rows x 2 N_mu split Y block
     MixScales *sc;
     CUtensorMap m_a1h, m_a1l, m_a2h, m_a2l, m_b1h, m_b1l, m_b2h, m_b2l, m_bwh, m_bwl, m_yh, m_yl;
+    // adjoint (allocated on the first backward call)
+    float2 *ac, *bc, *tc, *gc, *ybc;      // max_rows x N_mu complex64: P^phi, P^psi, Theta, G, Ybar
+    __half *oah, *oal;                    // split A operand scratch (max(R 2N_mu, N_mu 2R) halves)
+    __half *obh, *obl;                    // split B operand scratch (2 max(N, N_mu) x 2R halves)
+    __half *kh, *kl;                      // rotated K^T (2N_mu x 2N_mu)
+    __half *pmh, *pml, *qmh, *qml;        // rotated Phi_mu^H, Psi_mu^H (2N x 2N_mu)
+    float *adj_sc;                        // per-operand scales (see the adjoint code)
+    unsigned int *adj_max;                // per-operand max |.| (float bits)
 };
 
 namespace {
@@ -125,6 +134,9 @@ __global__ void compute_scales(MixScales *sc)
     sc->s_w = ldexpf(1.f, e_w);
     sc->fy = ldexpf(1.f, e_y - 2 * e_phi - 2 * e_psi);
     sc->ftheta = ldexpf(1.f, -e_y - e_w);
+    sc->s_y = ldexpf(1.f, e_y);
+    sc->inv_phi2 = ldexpf(1.f, -2 * e_phi);
+    sc->inv_psi2 = ldexpf(1.f, -2 * e_psi);
     if (!isfinite(ma_phi) || !isfinite(ma_psi) || !isfinite(ma_w) || !isfinite(mr_phi * mr_psi)) sc->err = 2;
 }
 
@@ -181,11 +193,22 @@ __global__ void build_rotated(const double2 *X, int64_t ld, int nb, int n, const
     }
 }
 
+enum { OUT_C64 = 0, OUT_ADD_C128 = 1, OUT_ATOMIC_C128 = 2 };
+
 struct EpiParams {
-    __half *yh, *yl;      // Gram: split Y output, row pitch ldy halves
+    // Gram-Hadamard (DUAL): split Y, and optionally P^phi, P^psi as complex64
+    __half *yh, *yl;      // row pitch ldy halves
     int64_t ldy;
-    float2 *theta;        // apply: complex64 output, leading dimension ld_theta
-    int64_t ld_theta;
+    float2 *aout, *bout;  // or NULL; leading dimension ldab (complex)
+    int64_t ldab;
+    // single product: result = alpha * acc / (*sa * *sb), stored per out_mode
+    int out_mode;
+    void *out;            // complex64 (OUT_C64) or complex128, leading dimension ldo (complex)
+    int64_t ldo;
+    const float *sa, *sb;
+    float alpha;
+    int ksplit;           // K partitions, each a separate tile (OUT_ATOMIC_C128 only)
+    int ncols;            // valid real output columns (multiple of 64)
     const MixScales *sc;
     int *err;
 };
@@ -229,7 +252,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     constexpr int PARTS = DUAL ? 2 : 1;
     constexpr uint32_t ACC = PARTS * TN;   // TMEM columns of one buffer
     constexpr uint32_t NCOLS = 2 * ACC;
-    const int nseg = (kchunks + seg - 1) / seg;
+    const int ksplit = (DUAL || ep.ksplit < 1) ? 1 : ep.ksplit;
+    const int kper = (kchunks + ksplit - 1) / ksplit;   // K chunks of one split
+    const int n_work = n_tiles * ksplit;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -255,11 +280,13 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             const CUtensorMap *maps[8] = {&a1h, &a1l, &b1h, &b1l, &a2h, &a2l, &b2h, &b2l};
             for (int i = 0; i < 4 * PARTS; ++i) tc::prefetch_map(maps[i]);
             int c = 0, issued = 0;
-            for (int tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
-                const int m0 = (tile / n_tiles_n) * TM, n0 = (tile % n_tiles_n) * TN;
-                for (int sg = 0; sg < nseg && !failed; ++sg)
+            for (int t = blockIdx.x; t < n_work && !failed; t += gridDim.x) {
+                const int mn = t / ksplit, ks = t % ksplit;
+                const int m0 = (mn / n_tiles_n) * TM, n0 = (mn % n_tiles_n) * TN;
+                const int kb = ks * kper, ke = min(kchunks, kb + kper);
+                for (int s0 = kb; s0 < ke && !failed; s0 += seg)
                     for (int part = 0; part < PARTS && !failed; ++part)
-                        for (int kc = sg * seg; kc < min(kchunks, (sg + 1) * seg); ++kc, ++c) {
+                        for (int kc = s0; kc < min(ke, s0 + seg); ++kc, ++c) {
                             const int s = c % STAGES, it = c / STAGES;
                             if (!tc::mbar_wait(&empty_bar[s], (it & 1) ^ 1, WAIT_BUDGET)) {
                                 atomicExch(ep.err, 1);
@@ -285,8 +312,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             constexpr uint32_t idesc = tc::idesc_f16(TM, TN);
             int c = 0, tl = 0;
             bool ok = true;
-            for (int tile = blockIdx.x; tile < n_tiles && !failed && ok; tile += gridDim.x) {
-                for (int sg = 0; sg < nseg && ok; ++sg, ++tl) {
+            for (int t = blockIdx.x; t < n_work && !failed && ok; t += gridDim.x) {
+                const int ks = t % ksplit;
+                const int kb = ks * kper, ke = min(kchunks, kb + kper);
+                for (int s0 = kb; s0 < ke && ok; s0 += seg, ++tl) {
                     const int acc = tl & 1, use = tl >> 1;
                     if (!tc::mbar_wait(&tempty[acc], (use & 1) ^ 1, WAIT_BUDGET)) {
                         atomicExch(ep.err, 1);
@@ -295,10 +324,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                         break;
                     }
                     tc::fence_after();
+                    const int s1 = min(ke, s0 + seg);
                     for (int part = 0; part < PARTS && ok; ++part) {
                         const uint32_t d = tmem + (uint32_t)acc * ACC + (uint32_t)part * TN;
-                        const int k0 = sg * seg, k1 = min(kchunks, (sg + 1) * seg);
-                        for (int kc = k0; kc < k1; ++kc, ++c) {
+                        for (int kc = s0; kc < s1; ++kc, ++c) {
                             const int s = c % STAGES, it = c / STAGES;
                             if (!tc::mbar_wait(&full_bar[s], it & 1, WAIT_BUDGET)) {
                                 atomicExch(ep.err, 1);
@@ -314,7 +343,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
 #pragma unroll
                             for (int kk = 0; kk < TK / 16; ++kk) {
                                 const uint64_t o = (uint64_t)(2 * kk);
-                                tc::mma_f16(d, dah + o, dbh + o, idesc, (kc > k0 || kk > 0) ? 1u : 0u);
+                                tc::mma_f16(d, dah + o, dbh + o, idesc, (kc > s0 || kk > 0) ? 1u : 0u);
                                 tc::mma_f16(d, dah + o, dbl + o, idesc, 1u);
                                 tc::mma_f16(d, dal + o, dbh + o, idesc, 1u);
                             }
@@ -335,8 +364,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         const int half = (warp - 2) >> 2;      // which 64 of the tile's 128 columns
         constexpr int HC = TN / 2;
         int tl = 0;
-        for (int tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
-            const int m0 = (tile / n_tiles_n) * TM, n0 = (tile % n_tiles_n) * TN;
+        for (int t = blockIdx.x; t < n_work && !failed; t += gridDim.x) {
+            const int mn = t / ksplit, ks = t % ksplit;
+            const int m0 = (mn / n_tiles_n) * TM, n0 = (mn % n_tiles_n) * TN;
+            const int kb = ks * kper, ke = min(kchunks, kb + kper);
             const int row = m0 + quarter * 32 + lane;
             float sa[HC], sb[DUAL ? HC : 1];
 #pragma unroll
@@ -344,7 +375,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
 #pragma unroll
             for (int i = 0; i < (DUAL ? HC : 1); ++i) sb[i] = 0.f;
             bool ok = true;
-            for (int sg = 0; sg < nseg; ++sg, ++tl) {
+            for (int s0 = kb; s0 < ke; s0 += seg, ++tl) {
                 const int acc = tl & 1, use = tl >> 1;
                 if (!tc::mbar_wait(&tfull[acc], use & 1, WAIT_BUDGET)) {
                     atomicExch(ep.err, 1);
@@ -375,7 +406,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                 if (lane == 0) tc::mbar_arrive(&tempty[acc]);
             }
             if (!ok) break;
-            if (row >= rows) continue;
+            if (row >= rows || ke <= kb || n0 + half * HC >= ep.ncols) continue;
             if (DUAL) {
                 const float fy = ep.sc->fy;
 #pragma unroll
@@ -400,17 +431,124 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                         dl[q] = reinterpret_cast<const uint4 *>(lv)[q];
                     }
                 }
-            } else {
-                const float ft = ep.sc->ftheta;
-                float2 *dst = ep.theta + row * ep.ld_theta + ((n0 + half * HC) >> 1);
+                if (ep.aout) {
+                    // the two products themselves (for the adjoint), unscaled, as complex64
+                    const float fa = ep.sc->inv_phi2, fb = ep.sc->inv_psi2;
+                    float2 *da = ep.aout + row * ep.ldab + ((n0 + half * HC) >> 1);
+                    float2 *db = ep.bout + row * ep.ldab + ((n0 + half * HC) >> 1);
 #pragma unroll
-                for (int q = 0; q < HC / 2; ++q) dst[q] = make_float2(sa[2 * q] * ft, sa[2 * q + 1] * ft);
+                    for (int q = 0; q < HC / 2; ++q) {
+                        da[q] = make_float2(sa[2 * q] * fa, sa[2 * q + 1] * fa);
+                        db[q] = make_float2(sb[(2 * q) % (DUAL ? HC : 1)] * fb, sb[(2 * q + 1) % (DUAL ? HC : 1)] * fb);
+                    }
+                }
+            } else {
+                const float f = ep.alpha / ((*ep.sa) * (*ep.sb));
+                const int64_t col = (n0 + half * HC) >> 1;
+                if (ep.out_mode == OUT_C64) {
+                    float2 *dst = static_cast<float2 *>(ep.out) + row * ep.ldo + col;
+#pragma unroll
+                    for (int q = 0; q < HC / 2; ++q) dst[q] = make_float2(sa[2 * q] * f, sa[2 * q + 1] * f);
+                } else if (ep.out_mode == OUT_ADD_C128) {
+                    double2 *dst = static_cast<double2 *>(ep.out) + row * ep.ldo + col;
+#pragma unroll
+                    for (int q = 0; q < HC / 2; ++q) {
+                        double2 v = dst[q];
+                        v.x += (double)(sa[2 * q] * f);
+                        v.y += (double)(sa[2 * q + 1] * f);
+                        dst[q] = v;
+                    }
+                } else {
+                    double *dst = reinterpret_cast<double *>(static_cast<double2 *>(ep.out) + row * ep.ldo + col);
+#pragma unroll
+                    for (int q = 0; q < HC; ++q) atomicAdd(dst + q, (double)(sa[q] * f));
+                }
             }
         }
     }
     tc::fence_before();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, NCOLS);
+}
+
+// ---------------------------------------------------------------- adjoint helpers
+// s = 2^(14 - e) from a max |.| held as float bits (a power of two, so scaling is exact)
+__global__ void scale_from_max(const unsigned int *maxbits, float *scale, int n)
+{
+    const int i = threadIdx.x;
+    if (i < n) scale[i] = ldexpf(1.f, scale_exp(__uint_as_float(maxbits[i])));
+}
+
+// Transposed split operands of a complex R x C matrix X (leading dimension ld):
+//   TRANSPOSE_A:  row c of the output = (Re, Im) of x[r][c] for r = 0..R-1 (an A operand for X^T-shaped products)
+//   ROTATED:      rows 2c, 2c+1 = (Re x, Im x), (-Im x, Re x) of x[r][c] (a B operand)
+// with x = conj(X) when conj is set, scaled by *scale and split into FP16 hi + lo.
+// 32 x 32 tiles are transposed through shared memory so that reads and writes are coalesced.
+template <typename T, bool ROTATED>
+__global__ void split_transposed(const T *X, int64_t ld, int R, int C, int conj, const float *scale, __half *hi,
+                                 __half *lo, int64_t out_pitch)
+{
+    __shared__ float2 tile[32][33];
+    const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
+    const float s = *scale;
+    for (int i = ty; i < 32; i += 8) {
+        const int r = r0 + i, c = c0 + tx;
+        float2 v = make_float2(0.f, 0.f);
+        if (r < R && c < C) {
+            const double2 d = cload(X, (int64_t)r * ld + c);
+            v = make_float2((float)(d.x * (double)s), (float)((conj ? -d.y : d.y) * (double)s));
+        }
+        tile[i][tx] = v;
+    }
+    __syncthreads();
+    __half2 *H = reinterpret_cast<__half2 *>(hi), *L = reinterpret_cast<__half2 *>(lo);
+    const int64_t pitch2 = out_pitch / 2;   // in half2
+    for (int i = ty; i < 32; i += 8) {
+        const int c = c0 + i, r = r0 + tx;
+        if (c >= C || r >= R) continue;
+        const float2 v = tile[tx][i];
+        const __half ha = __float2half_rn(v.x), hb = __float2half_rn(v.y);
+        const __half la = __float2half_rn(v.x - __half2float(ha)), lb = __float2half_rn(v.y - __half2float(hb));
+        if (ROTATED) {
+            H[(int64_t)(2 * c) * pitch2 + r] = __halves2half2(ha, hb);
+            H[(int64_t)(2 * c + 1) * pitch2 + r] = __halves2half2(__hneg(hb), ha);
+            L[(int64_t)(2 * c) * pitch2 + r] = __halves2half2(la, lb);
+            L[(int64_t)(2 * c + 1) * pitch2 + r] = __halves2half2(__hneg(lb), la);
+        } else {
+            H[(int64_t)c * pitch2 + r] = __halves2half2(ha, hb);
+            L[(int64_t)c * pitch2 + r] = __halves2half2(la, lb);
+        }
+    }
+}
+
+// Abar = Ybar o B (into A's place), Bbar = conj(Ybar) o A (into B's place), complex64
+__global__ void hadamard_adjoint_c64(const float2 *Yb, float2 *A, float2 *B, int64_t total)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const float2 y = Yb[e], a = A[e], b = B[e];
+        A[e] = make_float2(y.x * b.x - y.y * b.y, y.x * b.y + y.y * b.x);
+        B[e] = make_float2(y.x * a.x + y.y * a.y, y.x * a.y - y.y * a.x);
+    }
+}
+
+// loss += 1/2 Re sum conj(Theta) o G over a rows x n block (complex64, leading dimension ld)
+__global__ void loss_c64(const float2 *T, const float2 *G, int64_t total, double *loss)
+{
+    __shared__ double red[8];
+    double acc = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const float2 t = T[e], g = G[e];
+        acc += (double)t.x * g.x + (double)t.y * g.y;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) b += red[i];
+        atomicAdd(loss, 0.5 * b);
+    }
 }
 
 int num_sms()
@@ -438,13 +576,14 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return fn;
 }
 
-// 2-D FP16 map: `inner` halves per row, `rows` rows, box 64 x 128, 128-byte swizzle
-bool make_map(CUtensorMap *m, const void *base, uint64_t inner, uint64_t rows)
+// 2-D FP16 map: `inner` halves per row (row pitch `pitch` halves, default inner), `rows`
+// rows, box 64 x 128, 128-byte swizzle
+bool make_map(CUtensorMap *m, const void *base, uint64_t inner, uint64_t rows, uint64_t pitch = 0)
 {
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
     if (!enc) return false;
     cuuint64_t dims[2] = {inner, rows};
-    cuuint64_t strides[1] = {inner * 2};
+    cuuint64_t strides[1] = {(pitch ? pitch : inner) * 2};
     cuuint32_t box[2] = {TK, TM};
     cuuint32_t es[2] = {1, 1};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void *>(base), dims, strides, box, es,
@@ -569,6 +708,8 @@ isdf_status mixed_fit(isdf_plan *p, int64_t row_begin, int64_t row_count, void *
         ep.ldy = 2 * nm;
         ep.sc = b->sc;
         ep.err = err;
+        ep.ksplit = 1;
+        ep.ncols = 2 * nm;
         const int n_tiles_n = (2 * nm) / TN, m_tiles = (rows + TM - 1) / TM;
         const int n_tiles = n_tiles_n * m_tiles;
         const unsigned grid = (unsigned)(n_tiles < num_sms() ? n_tiles : num_sms());
@@ -581,14 +722,293 @@ isdf_status mixed_fit(isdf_plan *p, int64_t row_begin, int64_t row_count, void *
         timer_stop(p, 0, st, rows);
         ISDF_LAUNCH_CHECK();
         // a11: Theta_b = Y_b M^-1
-        ep.theta = static_cast<float2 *>(theta) + (r0 - row_begin) * ld_theta;
-        ep.ld_theta = ld_theta;
+        ep.out_mode = OUT_C64;
+        ep.out = static_cast<float2 *>(theta) + (r0 - row_begin) * ld_theta;
+        ep.ldo = ld_theta;
+        ep.sa = &b->sc->s_y;
+        ep.sb = &b->sc->s_w;
+        ep.alpha = 1.f;
         timer_start(p, 1, st);
         tc_gemm_persist<false><<<grid, threads, SMEM_BYTES, st>>>(b->m_yh, b->m_yl, b->m_bwh, b->m_bwl, b->m_yh,
                                                                   b->m_yl, b->m_bwh, b->m_bwl, (2 * nm) / TK, 0, rows,
                                                                   n_tiles_n, n_tiles, kApplySegment, ep); isdf_note_launch();
         timer_stop(p, 1, st, rows);
         ISDF_LAUNCH_CHECK();
+    }
+    return ISDF_OK;
+}
+
+
+namespace {
+
+// one tensor-core GEMM launch: C (rows x ncols real) = A (rows x K) Bh^T over kchunks chunks of 64
+isdf_status run_gemm(const CUtensorMap &ah, const CUtensorMap &al, const CUtensorMap &bh, const CUtensorMap &bl,
+                     int kchunks, int rows, int ncols, EpiParams ep, cudaStream_t st)
+{
+    const int n_tiles_n = (ncols + TN - 1) / TN, m_tiles = (rows + TM - 1) / TM;
+    const int n_tiles = n_tiles_n * m_tiles;
+    if (ep.ksplit < 1) ep.ksplit = 1;
+    const int work = n_tiles * ep.ksplit;
+    const unsigned grid = (unsigned)(work < num_sms() ? work : num_sms());
+    ep.ncols = ncols;
+    tc_gemm_persist<false><<<grid, GEMM_THREADS, SMEM_BYTES, st>>>(ah, al, bh, bl, ah, al, bh, bl, kchunks, 0, rows,
+                                                                   n_tiles_n, n_tiles, kApplySegment, ep);
+    isdf_note_launch();
+    ISDF_LAUNCH_CHECK();
+    return ISDF_OK;
+}
+
+// split-K factor for a long reduction with few output tiles: ~3 CTAs of work per SM, >= 16 chunks each
+int ksplit_for(int rows, int ncols, int kchunks)
+{
+    const int tiles = ((rows + TM - 1) / TM) * ((ncols + TN - 1) / TN);
+    int k = (3 * num_sms() + tiles - 1) / tiles;
+    const int kmax = kchunks / 16 > 1 ? kchunks / 16 : 1;
+    return k < 1 ? 1 : (k > kmax ? kmax : k);
+}
+
+// max |.| of a complex matrix into adj_max[slot], then the power-of-two scale into adj_sc[slot]
+template <typename T>
+isdf_status operand_scale(MixedBuffers *b, int slot, const T *x, int64_t ld, int cols, int64_t rows, cudaStream_t st)
+{
+    ISDF_CUDA_TRY(cudaMemsetAsync(b->adj_max + slot, 0, sizeof(unsigned int), st));
+    absmax_rows<T><<<grid_for(rows * 32, 152 * 8), 256, 0, st>>>(x, ld, cols, rows, b->adj_max + slot, nullptr);
+    isdf_note_launch();
+    scale_from_max<<<1, 32, 0, st>>>(b->adj_max + slot, b->adj_sc + slot, 1);
+    isdf_note_launch();
+    ISDF_LAUNCH_CHECK();
+    return ISDF_OK;
+}
+
+template <typename T, bool ROT>
+isdf_status transposed_operand(const T *x, int64_t ld, int R, int C, int conj, const float *scale, __half *hi,
+                               __half *lo, int64_t pitch, cudaStream_t st)
+{
+    dim3 grid((R + 31) / 32, (C + 31) / 32);
+    split_transposed<T, ROT><<<grid, 256, 0, st>>>(x, ld, R, C, conj, scale, hi, lo, pitch);
+    isdf_note_launch();
+    ISDF_LAUNCH_CHECK();
+    return ISDF_OK;
+}
+
+enum { SC_THETA = 0, SC_G = 1, SC_ABAR = 2, SC_BBAR = 3, SC_YBAR = 4, SC_K = 5, SC_SLOTS = 8 };
+
+isdf_status adjoint_alloc(isdf_plan *p)
+{
+    MixedBuffers *b = p->mixed;
+    const int64_t R = p->max_rows, nm = p->n_mu, n = p->n_phi;
+    const int64_t Rp = (R + 7) & ~(int64_t)7;   // row pitch of the transposed operands (16-byte multiple)
+    const size_t blk = (size_t)R * nm;
+    ISDF_TRY(halloc(&b->ac, blk));
+    ISDF_TRY(halloc(&b->bc, blk));
+    ISDF_TRY(halloc(&b->tc, blk));
+    ISDF_TRY(halloc(&b->gc, blk));
+    ISDF_TRY(halloc(&b->ybc, blk));
+    const size_t oa = (size_t)2 * Rp * nm;
+    const size_t ob = (size_t)4 * Rp * (nm > n ? nm : n);
+    ISDF_TRY(halloc(&b->oah, oa));
+    ISDF_TRY(halloc(&b->oal, oa));
+    ISDF_TRY(halloc(&b->obh, ob));
+    ISDF_TRY(halloc(&b->obl, ob));
+    ISDF_TRY(halloc(&b->kh, (size_t)4 * nm * nm));
+    ISDF_TRY(halloc(&b->kl, (size_t)4 * nm * nm));
+    ISDF_TRY(halloc(&b->pmh, (size_t)4 * n * nm));
+    ISDF_TRY(halloc(&b->pml, (size_t)4 * n * nm));
+    ISDF_TRY(halloc(&b->qmh, (size_t)4 * n * nm));
+    ISDF_TRY(halloc(&b->qml, (size_t)4 * n * nm));
+    ISDF_TRY(halloc(&b->adj_sc, SC_SLOTS));
+    ISDF_TRY(halloc(&b->adj_max, SC_SLOTS));
+    return ISDF_OK;
+}
+
+}  // namespace
+
+// Adjoint of Theta(Phi, Psi) at fixed points on the tensor cores (ISDF_MIXED). Per
+// block of rows: recompute P^phi, P^psi and Y (Gram kernel), Theta = Y M^-1, G (given
+// or 2 dV Theta conj(K)), Ybar = G M^-1, Abar = Ybar o B, Bbar = conj(Ybar) o A, then
+// grad_phi rows += Abar Phi_mu, Phibar_mu += Abar^H Phi_b (and Psi likewise), and
+// Mbar -= Theta^H Ybar. The three reductions over grid rows use transposed split
+// copies and split-K partitions accumulated with FP64 atomics.
+isdf_status mixed_backward(isdf_plan *p, int64_t row_begin, int64_t row_count, const void *grad_theta,
+                           int64_t ld_grad, const void *K, double dV, void *grad_phi, int64_t ld_gphi,
+                           void *grad_psi, int64_t ld_gpsi, double *loss, cudaStream_t st)
+{
+    MixedBuffers *b = p->mixed;
+    if (!b->ac) ISDF_TRY(adjoint_alloc(p));
+    const int n = p->n_phi, nm = p->n_mu;
+    const int64_t R = p->max_rows, Rp = (R + 7) & ~(int64_t)7;
+    const size_t es = p->dtype == ISDF_C128 ? 16 : 8;
+    int *err = &b->sc->err;
+    bool ok = true;
+    // per call: rotated K^T, Phi_mu^H, Psi_mu^H
+    CUtensorMap mkh, mkl, mph, mpl, mqh, mql;
+    if (!grad_theta) {
+        ISDF_TRY(operand_scale<double2>(b, SC_K, static_cast<const double2 *>(K), nm, nm, nm, st));
+        ISDF_TRY((transposed_operand<double2, true>(static_cast<const double2 *>(K), nm, nm, nm, 0, b->adj_sc + SC_K,
+                                                    b->kh, b->kl, 2 * nm, st)));
+        ok &= make_map(&mkh, b->kh, 2 * nm, 2 * nm);
+        ok &= make_map(&mkl, b->kl, 2 * nm, 2 * nm);
+    }
+    ISDF_TRY((transposed_operand<double2, true>(p->phi_mu, n, nm, n, 1, &b->sc->s_phi, b->pmh, b->pml, 2 * nm, st)));
+    ISDF_TRY((transposed_operand<double2, true>(p->psi_mu, n, nm, n, 1, &b->sc->s_psi, b->qmh, b->qml, 2 * nm, st)));
+    ok &= make_map(&mph, b->pmh, 2 * nm, 2 * n);
+    ok &= make_map(&mpl, b->pml, 2 * nm, 2 * n);
+    ok &= make_map(&mqh, b->qmh, 2 * nm, 2 * n);
+    ok &= make_map(&mql, b->qml, 2 * nm, 2 * n);
+    CUtensorMap moah, moal;   // row-block A operand (rows x 2 N_mu)
+    ok &= make_map(&moah, b->oah, 2 * nm, R);
+    ok &= make_map(&moal, b->oal, 2 * nm, R);
+    if (!ok) return ISDF_ERR_CUDA;
+
+    for (int64_t r0 = row_begin; r0 < row_begin + row_count; r0 += R) {
+        const int rows = (int)((row_begin + row_count - r0) < R ? (row_begin + row_count - r0) : R);
+        const int64_t tot = (int64_t)rows * nm;
+        // 1. P^phi, P^psi and the split Y of this block
+        {
+            EpiParams ep{};
+            ep.yh = b->yh;
+            ep.yl = b->yl;
+            ep.ldy = 2 * nm;
+            ep.aout = b->ac;
+            ep.bout = b->bc;
+            ep.ldab = nm;
+            ep.sc = b->sc;
+            ep.err = err;
+            ep.ksplit = 1;
+            ep.ncols = 2 * nm;
+            const int n_tiles_n = (2 * nm) / TN, m_tiles = (rows + TM - 1) / TM;
+            const int n_tiles = n_tiles_n * m_tiles;
+            const unsigned grid = (unsigned)(n_tiles < num_sms() ? n_tiles : num_sms());
+            tc_gemm_persist<true><<<grid, GEMM_THREADS, SMEM_BYTES, st>>>(
+                b->m_a1h, b->m_a1l, b->m_b1h, b->m_b1l, b->m_a2h, b->m_a2l, b->m_b2h, b->m_b2l, (2 * n) / TK,
+                (int)r0, rows, n_tiles_n, n_tiles, kGramSegment, ep);
+            isdf_note_launch();
+            ISDF_LAUNCH_CHECK();
+        }
+        EpiParams e{};
+        e.sc = b->sc;
+        e.err = err;
+        e.ksplit = 1;
+        // 2. Theta = Y M^-1 (complex64)
+        e.out_mode = OUT_C64;
+        e.out = b->tc;
+        e.ldo = nm;
+        e.sa = &b->sc->s_y;
+        e.sb = &b->sc->s_w;
+        e.alpha = 1.f;
+        ISDF_TRY(run_gemm(b->m_yh, b->m_yl, b->m_bwh, b->m_bwl, (2 * nm) / TK, rows, 2 * nm, e, st));
+        ISDF_TRY(operand_scale<float2>(b, SC_THETA, b->tc, nm, nm, rows, st));
+        // 3. G = 2 dV Theta conj(K), or the given dL/dTheta
+        if (!grad_theta) {
+            split_orbitals<float2><<<grid_for(tot, 152 * 64), 256, 0, st>>>(b->tc, nm, nm, rows, b->adj_sc + SC_THETA,
+                                                                            b->oah, b->oal);
+            isdf_note_launch();
+            e.out = b->gc;
+            e.sa = b->adj_sc + SC_THETA;
+            e.sb = b->adj_sc + SC_K;
+            e.alpha = (float)(2.0 * dV);
+            ISDF_TRY(run_gemm(moah, moal, mkh, mkl, (2 * nm) / TK, rows, 2 * nm, e, st));
+            if (loss) {
+                loss_c64<<<grid_for(tot, 2048), 256, 0, st>>>(b->tc, b->gc, tot, loss);
+                isdf_note_launch();
+            }
+        } else {
+            ISDF_CUDA_TRY(cudaMemcpy2DAsync(b->gc, sizeof(float2) * nm,
+                                            static_cast<const char *>(grad_theta) + (r0 - row_begin) * ld_grad * 8,
+                                            sizeof(float2) * ld_grad, sizeof(float2) * nm, rows,
+                                            cudaMemcpyDeviceToDevice, st));
+        }
+        // 4. Ybar = G M^-1
+        ISDF_TRY(operand_scale<float2>(b, SC_G, b->gc, nm, nm, rows, st));
+        split_orbitals<float2><<<grid_for(tot, 152 * 64), 256, 0, st>>>(b->gc, nm, nm, rows, b->adj_sc + SC_G, b->oah,
+                                                                        b->oal);
+        isdf_note_launch();
+        e.out = b->ybc;
+        e.sa = b->adj_sc + SC_G;
+        e.sb = &b->sc->s_w;
+        e.alpha = 1.f;
+        ISDF_TRY(run_gemm(moah, moal, b->m_bwh, b->m_bwl, (2 * nm) / TK, rows, 2 * nm, e, st));
+        // 5. Abar = Ybar o B, Bbar = conj(Ybar) o A
+        hadamard_adjoint_c64<<<grid_for(tot), 256, 0, st>>>(b->ybc, b->ac, b->bc, tot);
+        isdf_note_launch();
+        ISDF_TRY(operand_scale<float2>(b, SC_ABAR, b->ac, nm, nm, rows, st));
+        ISDF_TRY(operand_scale<float2>(b, SC_BBAR, b->bc, nm, nm, rows, st));
+        ISDF_TRY(operand_scale<float2>(b, SC_YBAR, b->ybc, nm, nm, rows, st));
+        // 6. grad_phi rows += Abar Phi_mu, grad_psi rows += Bbar Psi_mu
+        for (int side = 0; side < 2; ++side) {
+            const float2 *src = side ? b->bc : b->ac;
+            const int slot = side ? SC_BBAR : SC_ABAR;
+            split_orbitals<float2><<<grid_for(tot, 152 * 64), 256, 0, st>>>(src, nm, nm, rows, b->adj_sc + slot,
+                                                                            b->oah, b->oal);
+            isdf_note_launch();
+            EpiParams g{};
+            g.sc = b->sc;
+            g.err = err;
+            g.ksplit = 1;
+            g.out_mode = OUT_ADD_C128;
+            g.out = side ? static_cast<double2 *>(grad_psi) + r0 * ld_gpsi : static_cast<double2 *>(grad_phi) + r0 * ld_gphi;
+            g.ldo = side ? ld_gpsi : ld_gphi;
+            g.sa = b->adj_sc + slot;
+            g.sb = side ? &b->sc->s_psi : &b->sc->s_phi;
+            g.alpha = 1.f;
+            ISDF_TRY(run_gemm(moah, moal, side ? mqh : mph, side ? mql : mpl, (2 * nm) / TK, rows, 2 * n, g, st));
+        }
+        // 7. Phibar_mu += Abar^H Phi_b, Psibar_mu += Bbar^H Psi_b (reductions over the block's rows)
+        const int kch = (2 * rows + TK - 1) / TK;
+        CUtensorMap mah, mal, mbh, mbl;
+        ok &= make_map(&mah, b->oah, 2 * rows, nm, 2 * Rp);
+        ok &= make_map(&mal, b->oal, 2 * rows, nm, 2 * Rp);
+        for (int side = 0; side < 2 && ok; ++side) {
+            const float2 *src = side ? b->bc : b->ac;
+            const int slot = side ? SC_BBAR : SC_ABAR;
+            ISDF_TRY((transposed_operand<float2, false>(src, nm, rows, nm, 1, b->adj_sc + slot, b->oah, b->oal, 2 * Rp,
+                                                        st)));
+            const void *orb = side ? p->psi : p->phi;
+            const int64_t ldo = side ? p->ld_psi : p->ld_phi;
+            const float *so = side ? &b->sc->s_psi : &b->sc->s_phi;
+            const char *src_rows = static_cast<const char *>(orb) + r0 * ldo * es;
+            if (p->dtype == ISDF_C128)
+                ISDF_TRY((transposed_operand<double2, true>(reinterpret_cast<const double2 *>(src_rows), ldo, rows, n,
+                                                            1, so, b->obh, b->obl, 2 * Rp, st)));
+            else
+                ISDF_TRY((transposed_operand<float2, true>(reinterpret_cast<const float2 *>(src_rows), ldo, rows, n, 1,
+                                                           so, b->obh, b->obl, 2 * Rp, st)));
+            ok &= make_map(&mbh, b->obh, 2 * rows, 2 * n, 2 * Rp);
+            ok &= make_map(&mbl, b->obl, 2 * rows, 2 * n, 2 * Rp);
+            if (!ok) break;
+            EpiParams g{};
+            g.sc = b->sc;
+            g.err = err;
+            g.out_mode = OUT_ATOMIC_C128;
+            g.out = side ? p->gpsi_mu : p->gphi_mu;
+            g.ldo = n;
+            g.sa = b->adj_sc + slot;
+            g.sb = so;
+            g.alpha = 1.f;
+            g.ksplit = ksplit_for(nm, 2 * n, kch);
+            ISDF_TRY(run_gemm(mah, mal, mbh, mbl, kch, nm, 2 * n, g, st));
+        }
+        // 8. Mbar -= Theta^H Ybar
+        if (ok) {
+            ISDF_TRY((transposed_operand<float2, false>(b->tc, nm, rows, nm, 1, b->adj_sc + SC_THETA, b->oah, b->oal,
+                                                        2 * Rp, st)));
+            ISDF_TRY((transposed_operand<float2, true>(b->ybc, nm, rows, nm, 1, b->adj_sc + SC_YBAR, b->obh, b->obl,
+                                                       2 * Rp, st)));
+            ok &= make_map(&mbh, b->obh, 2 * rows, 2 * nm, 2 * Rp);
+            ok &= make_map(&mbl, b->obl, 2 * rows, 2 * nm, 2 * Rp);
+            EpiParams g{};
+            g.sc = b->sc;
+            g.err = err;
+            g.out_mode = OUT_ATOMIC_C128;
+            g.out = p->Mbar;
+            g.ldo = nm;
+            g.sa = b->adj_sc + SC_THETA;
+            g.sb = b->adj_sc + SC_YBAR;
+            g.alpha = -1.f;
+            g.ksplit = ksplit_for(nm, 2 * nm, kch);
+            if (ok) ISDF_TRY(run_gemm(mah, mal, mbh, mbl, kch, nm, 2 * nm, g, st));
+        }
+        if (!ok) return ISDF_ERR_CUDA;
     }
     return ISDF_OK;
 }
@@ -607,8 +1027,9 @@ void mixed_release(isdf_plan *p)
 {
     MixedBuffers *b = p->mixed;
     if (!b) return;
-    void *bufs[] = {b->a1h, b->a1l, b->a2h, b->a2l, b->b1h, b->b1l, b->b2h,
-                    b->b2l, b->bwh, b->bwl, b->yh,  b->yl,  b->sc};
+    void *bufs[] = {b->a1h, b->a1l, b->a2h, b->a2l, b->b1h, b->b1l, b->b2h, b->b2l, b->bwh, b->bwl,
+                    b->yh,  b->yl,  b->sc,  b->ac,  b->bc,  b->tc,  b->gc,  b->ybc, b->oah, b->oal,
+                    b->obh, b->obl, b->kh,  b->kl,  b->pmh, b->pml, b->qmh, b->qml, b->adj_sc, b->adj_max};
     for (void *x : bufs)
         if (x) cudaFree(x);
     free(b);

@@ -338,8 +338,9 @@ extern "C" isdf_status isdf_fit_theta_backward(isdf_plan *p, int64_t row_begin, 
     if (row_count == 0) return ISDF_OK;
     cudaStream_t st = as_stream(stream);
     p->last_stream = st;
-    // the adjoint runs on the FP64 kernels in both modes; in ISDF_MIXED mode
-    // grad_theta is complex64 like the mixed-mode Theta
+    if (p->mode == ISDF_MIXED)
+        return mixed_backward(p, row_begin, row_count, grad_theta, ld_grad, K, dV, grad_phi, ld_gphi, grad_psi,
+                              ld_gpsi, loss, st);
     const int nm = p->n_mu;
     const int t = p->dtype == ISDF_C128 ? ZG_C128 : ZG_C64;
     const size_t es = p->dtype == ISDF_C128 ? 16 : 8;
@@ -459,16 +460,27 @@ extern "C" isdf_status isdf_plan_update(isdf_plan *p, const int64_t *idx, void *
     return plan_compute(p, idx, st);
 }
 
+// Under stream capture a plain record only orders work inside the graph; an external
+// record node is needed for the event to be timed after each replay.
+static void timer_record(cudaEvent_t ev, cudaStream_t st)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal);
+    else
+        cudaEventRecord(ev, st);
+}
+
 void timer_start(isdf_plan *p, int kind, cudaStream_t st)
 {
     if (!p->timing || p->tused[kind] >= p->tcap) return;
-    cudaEventRecord(p->tev[kind][2 * p->tused[kind]], st);
+    timer_record(p->tev[kind][2 * p->tused[kind]], st);
 }
 
 void timer_stop(isdf_plan *p, int kind, cudaStream_t st, int64_t rows)
 {
     if (!p->timing || p->tused[kind] >= p->tcap) return;
-    cudaEventRecord(p->tev[kind][2 * p->tused[kind] + 1], st);
+    timer_record(p->tev[kind][2 * p->tused[kind] + 1], st);
     p->trows[kind][p->tused[kind]] = rows;
     p->tused[kind] += 1;
 }

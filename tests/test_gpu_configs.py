@@ -3,9 +3,9 @@
 waterbox (96^3 grid, 256 complex64 orbitals, 2048 points, T = 100): the whole
 K-means bit-exact against the oracle, mixed Theta on sampled rows <= 1e-5.
 adjoint (72^3, 192 orbitals, 1536 points fixed from a prior K-means): the
-FP64 adjoint of the exchange-like surrogate against the oracle gradient and
-central finite differences on 32 seeded directions scaled to the orbital
-norms (h = 1e-5 within 1e-6; h = 1e-6 within its FP64 noise floor, 1e-5).
+FP64 and tensor-core adjoints of the exchange-like surrogate against the
+oracle gradient, and the FP64 adjoint against central finite differences on
+32 seeded directions scaled to the orbital norms (h = 1e-5 within 1e-6).
 silica (128^3, 1024 orbitals, 4096 points): K-means checked through
 properties that hold at any size (sampled labels are the nearest centroids
 under the FP64 formula, every cluster is non-empty, snapped points are
@@ -87,17 +87,27 @@ def test_adjoint_config_against_oracle_gradient(isdf):
     for got, exp in ((gphi, ref["grad_phi"]), (gpsi, ref["grad_psi"])):
         g = got.cpu().numpy()
         assert np.linalg.norm(g - exp) < 1e-9 * np.linalg.norm(exp)
-    # the mixed-precision adjoint (tensor-core Theta, FP64 adjoint kernels) against the same oracle gradient
+    # the tensor-core adjoint against the same FP64 oracle gradient
     mplan = isdf.Plan(phi, psi, idx, mode="mixed", max_rows=65536)
     _, mphi, mpsi = isdf.surrogate_loss_and_grad(mplan, torch.from_numpy(K).to(DEV), w.dV, block=65536)
     mplan.check()
     for got, exp in ((mphi, ref["grad_phi"]), (mpsi, ref["grad_psi"])):
-        assert np.linalg.norm(got.cpu().numpy() - exp) < 1e-9 * np.linalg.norm(exp)
+        assert np.linalg.norm(got.cpu().numpy() - exp) < 1e-4 * np.linalg.norm(exp)
 
 
 def test_adjoint_config_finite_differences(isdf):
-    w, phi, psi, idx, K = _adjoint_setup(isdf)
+    w, phi, psi, idx, _ = _adjoint_setup(isdf)
+    # a Hermitian positive-definite K = c I + U U^H with U of rank 32 (passed to the adjoint as a
+    # dense matrix), so that each FD loss costs one Theta fit: with P = Theta conj(U),
+    # sum conj(Theta) o (Theta K^T) = c ||Theta||^2 + ||P||^2
+    rng = np.random.default_rng(3000 + w.seed)
+    Qk, _ = np.linalg.qr(rng.standard_normal((w.n_mu, 32)) + 1j * rng.standard_normal((w.n_mu, 32)))
+    U = Qk * np.sqrt(rng.uniform(1.0, 9.0, size=32))[None, :]
+    c = 1.0
+    K = c * np.eye(w.n_mu) + U @ U.conj().T
+    K = 0.5 * (K + K.conj().T)
     Kd = torch.from_numpy(K).to(DEV)
+    Ucd = torch.from_numpy(U.conj()).to(DEV)
     P = phi.to(torch.complex128)
     Q = psi.to(torch.complex128)
     plan = isdf.Plan(P, Q, idx, mode="fp64", max_rows=131072)
@@ -112,22 +122,24 @@ def test_adjoint_config_finite_differences(isdf):
         Qp.copy_(Q).add_(Dq, alpha=sign * h)
         fplan.update(idx)
         fplan.fit_theta(out=theta)
-        return w.dV * torch.real(torch.sum(theta.conj() * (theta @ Kd.T))).item()
+        return w.dV * (c * torch.linalg.vector_norm(theta) ** 2 +
+                       torch.linalg.vector_norm(theta @ Ucd) ** 2).item()
 
-    # FP64 rounding of the loss (~1e-14 relative on 5.7e8 terms) divided by 2h is ~3e-6 of the
-    # directional derivative at h = 1e-6 on this size: the 1e-6 check uses h = 1e-5 (truncation
-    # ~1e-10), and h = 1e-6 is held to its noise floor
+    assert abs(loss_at(0, P, Q, 0.0) - loss.item()) < 1e-10 * abs(loss.item())
+    # FP64 rounding of the loss divided by 2h is ~3e-6 of the directional derivative at
+    # h = 1e-6 on this size (5.7e8 terms): the 1e-6 check uses h = 1e-5, whose
+    # truncation error is ~1e-10 (h = 1e-6 is checked on the small workload)
     gen = torch.Generator(device=DEV).manual_seed(4242)
-    for _ in range(32):
+    h = 1e-5
+    for d in range(32):
         Dp = torch.randn(P.shape, dtype=torch.complex128, device=DEV, generator=gen)
         Dq = torch.randn(Q.shape, dtype=torch.complex128, device=DEV, generator=gen)
         # scaled to the orbitals' norms, so that h is a relative step
         Dp *= torch.linalg.vector_norm(P) / torch.linalg.vector_norm(Dp)
         Dq *= torch.linalg.vector_norm(Q) / torch.linalg.vector_norm(Dq)
         an = torch.real(torch.vdot(gphi.flatten(), Dp.flatten()) + torch.vdot(gpsi.flatten(), Dq.flatten())).item()
-        for h, tol in ((1e-5, 1e-6), (1e-6, 1e-5)):
-            fd = (loss_at(+1, Dp, Dq, h) - loss_at(-1, Dp, Dq, h)) / (2 * h)
-            assert abs(fd - an) <= tol * abs(an), (h, fd, an)
+        fd = (loss_at(+1, Dp, Dq, h) - loss_at(-1, Dp, Dq, h)) / (2 * h)
+        assert abs(fd - an) <= 1e-6 * abs(an), (d, fd, an)
     fplan.check()
 
 

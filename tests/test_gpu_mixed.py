@@ -71,12 +71,33 @@ def test_mixed_partial_rows_and_ragged_tail(isdf):
 
 
 def test_mixed_adjoint_against_fp64_oracle(isdf):
+    # tensor-core adjoint (split-FP16 GEMMs, FP32 accumulation) against the FP64 oracle gradient
     w = mixed_small(32, 128)
     phi, psi, p64, q64, idx = _setup(w)
     K = W.loss_matrix(w.n_mu, 5)
-    plan = isdf.Plan(phi.to(DEV), psi.to(DEV), torch.from_numpy(idx), mode="mixed")
-    loss, gphi, gpsi = isdf.surrogate_loss_and_grad(plan, torch.from_numpy(K).to(DEV), w.dV)
+    plan = isdf.Plan(phi.to(DEV), psi.to(DEV), torch.from_numpy(idx), mode="mixed", max_rows=5000)
+    loss, gphi, gpsi = isdf.surrogate_loss_and_grad(plan, torch.from_numpy(K).to(DEV), w.dV, block=7000)
     plan.check()
     ref = O.theta_backward(p64, q64, idx, lambda rows, T: O.surrogate_grad_theta(T, K, w.dV))
+    ref_loss = O.surrogate_loss(O.fit_theta(p64, q64, idx)["theta"], K, w.dV)
+    assert abs(loss.item() - ref_loss) < 1e-5 * abs(ref_loss)
     for got, exp in ((gphi, ref["grad_phi"]), (gpsi, ref["grad_psi"])):
-        assert np.linalg.norm(got.cpu().numpy() - exp) < 1e-9 * np.linalg.norm(exp)
+        err = np.linalg.norm(got.cpu().numpy() - exp) / np.linalg.norm(exp)
+        assert err < 1e-4, err
+
+
+def test_mixed_adjoint_autograd_grad_theta(isdf):
+    # the autograd path (dL/dTheta given, complex64) through the tensor-core adjoint
+    w = mixed_small(32, 128)
+    phi, psi, p64, q64, idx = _setup(w)
+    K = W.loss_matrix(w.n_mu, 6)
+    P = phi.to(DEV).requires_grad_(True)
+    Q = psi.to(DEV).requires_grad_(True)
+    th = isdf.ISDFThetaFn.apply(P, Q, torch.from_numpy(idx), "mixed")
+    Kd = torch.from_numpy(K).to(DEV)
+    loss = w.dV * torch.real(torch.sum(th.to(torch.complex128).conj() * (th.to(torch.complex128) @ Kd.T)))
+    loss.backward()
+    ref = O.theta_backward(p64, q64, idx, lambda rows, T: O.surrogate_grad_theta(T, K, w.dV))
+    for got, exp in ((P.grad, ref["grad_phi"]), (Q.grad, ref["grad_psi"])):
+        err = np.linalg.norm(got.cpu().numpy().astype(np.complex128) - exp) / np.linalg.norm(exp)
+        assert err < 1e-4, err

@@ -268,12 +268,16 @@ def test_adjoint_fp64_finite_differences(isdf):
         th = pl.fit_theta()
         return w.dV * torch.real(torch.sum(th.conj() * (th @ Kd.T))).item()
 
-    h = 1e-6
+    # the FD's FP64 rounding noise is absolute, ~4e-6 at h = 1e-6 on this loss (3.5e3) for the
+    # oracle too, i.e. above 1e-6 relative where a direction is nearly orthogonal to the
+    # gradient: the 1e-6 check uses h = 1e-5, and h = 1e-6 is held to its noise floor
+    floor = 1e-3 * gphi.abs().max().item()
     for D in W.directions((2,) + tuple(phi.shape), 32, 99):
         Dp, Dq = torch.from_numpy(D[0]).to(DEV), torch.from_numpy(D[1]).to(DEV)
-        fd = (loss_at(P + h * Dp, Q + h * Dq) - loss_at(P - h * Dp, Q - h * Dq)) / (2 * h)
         an = torch.real(torch.vdot(gphi.flatten(), Dp.flatten()) + torch.vdot(gpsi.flatten(), Dq.flatten())).item()
-        assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3 * gphi.abs().max().item())
+        for h, tol in ((1e-5, 1e-6), (1e-6, 1e-5)):
+            fd = (loss_at(P + h * Dp, Q + h * Dq) - loss_at(P - h * Dp, Q - h * Dq)) / (2 * h)
+            assert abs(fd - an) <= tol * max(abs(an), floor), (h, fd, an)
 
 
 def test_autograd_function_matches_oracle(isdf):
