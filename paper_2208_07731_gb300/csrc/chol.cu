@@ -4,9 +4,10 @@
 //
 // Right-looking Cholesky with 32-wide panels: one CTA factors the diagonal
 // block in shared memory and also inverts it; the panel below is L21 =
-// A21 L11^-H (a GEMM with the inverted diagonal block); the trailing lower
-// triangle is updated by A22 -= L21 L21^H. L^-1 is built recursively from the
-// inverted diagonal blocks: inv([[A, 0], [B, C]]) = [[A^-1, 0], [-C^-1 B A^-1, C^-1]].
+// A21 L11^-H (a split-K GEMM with the inverted diagonal block); the trailing
+// lower triangle is updated by A22 -= L21 L21^H. L^-1 is then assembled
+// bottom-up from the inverted diagonal blocks, one batched launch per level:
+// inv([[A, 0], [B, C]]) = [[A^-1, 0], [-C^-1 B A^-1, C^-1]].
 #include "chol.cuh"
 #include "plan.cuh"
 #include "zgemm.cuh"
@@ -20,94 +21,95 @@ constexpr int DT = 128;   // threads of the diagonal-block kernel
 // write L_kk back (upper part zeroed) and L_kk^-1 into Linv at (k, k).
 // A pivot not above 1e-13 of M's original diagonal entry (M0) is reported.
 //
-// Latency matters more than throughput here (one block per launch, on the
-// critical path of the factorisation), so each elimination step costs one
-// barrier: step j subtracts T[i][j] conj(T[c][j]) / d_j from the trailing
-// triangle with the unscaled column j, and the columns are scaled by
-// 1/sqrt(d_j) once at the end. The inverse is computed column by column; the
-// 4 threads of a column sit in one warp, so it needs no block barrier.
+// GB300 issues FP64 at a low rate per SM, so what matters on this one-CTA
+// critical path is the number of FP64 warp instructions. The block is
+// factored as L^ D L^H by elimination on [A | I] (one barrier per pivot):
+// step j subtracts m_i conj(A_cj) from A_ic (j < c <= i) and m_i X_jc from
+// X_ic (c <= j < i), m_i = A_ij / d_j. The active elements of a step are
+// numbered contiguously and dealt round-robin to the threads, so warps run
+// full. The thread that updates the next pivot also forms its reciprocal.
+// Afterwards L = (A's eliminated columns) D^-1/2 and L^-1 = D^-1/2 X.
 __global__ void __launch_bounds__(DT) potrf_diag(double2 *A, int64_t lda, const double2 *M0, double2 *Linv,
                                                 int64_t ldi, int k, int nb, DeviceStatus *st)
 {
     __shared__ double2 T[NB][NB + 1];
-    __shared__ double2 I[NB][NB + 1];
+    __shared__ double2 X[NB][NB + 1];
     __shared__ double d0s[NB];     // original diagonal entries of M
-    __shared__ double rdiag[NB];   // 1 / L_jj
+    __shared__ double rpiv[NB];    // 1 / d_j
+    __shared__ double rs[NB];      // 1 / sqrt(d_j)
+    __shared__ int bad[2];         // failing pivot + 1, or 0: written in step j - 1 into slot j & 1,
+                                   // read at the top of step j (two slots keep the read race-free)
     if (st->code != 0) return;
     const int tid = threadIdx.x;
     for (int e = tid; e < NB * NB; e += DT) {
         const int i = e / NB, j = e % NB;
         T[i][j] = (i < nb && j <= i) ? A[(int64_t)(k + i) * lda + (k + j)] : make_double2(0.0, 0.0);
+        X[i][j] = make_double2(i == j && i < nb ? 1.0 : 0.0, 0.0);
     }
     if (tid < nb) d0s[tid] = M0[(int64_t)(k + tid) * lda + (k + tid)].x;
     __syncthreads();
-    // thread t updates row i = t % NB, columns c = j + 1 + slice, step 4
-    const int my_row = tid % NB, slice = tid / NB;
+    if (tid == 0) {
+        const double d = T[0][0].x;
+        bad[0] = (!(d > 1e-13 * d0s[0]) || isinf(d)) ? 1 : 0;
+        rpiv[0] = 1.0 / d;
+    }
+    __syncthreads();
     for (int j = 0; j < nb; ++j) {
-        const double d = T[j][j].x;
-        if (!(d > 1e-13 * d0s[j]) || isinf(d)) {
-            if (tid == 0) set_status(st, isnan(d) ? ISDF_ERR_NONFINITE : ISDF_ERR_NOT_HPD, k + j);
-            return;   // uniform: every thread read the same pivot
+        const int b = bad[j & 1];   // uniform: written before the last barrier, not rewritten until the next
+        if (b) {
+            if (tid == 0) set_status(st, isnan(T[b - 1][b - 1].x) ? ISDF_ERR_NONFINITE : ISDF_ERR_NOT_HPD, k + b - 1);
+            return;
         }
-        if (my_row > j && my_row < nb) {
-            const double r = 1.0 / d;
-            const double2 a = T[my_row][j];
-            const double2 ar = make_double2(a.x * r, a.y * r);
-            for (int c = j + 1 + slice; c <= my_row; c += DT / NB) {
-                const double2 b = T[c][j];
-                T[my_row][c].x -= ar.x * b.x + ar.y * b.y;
-                T[my_row][c].y -= ar.y * b.x - ar.x * b.y;
+        const double r = rpiv[j];
+        const int rows = nb - 1 - j;               // i = j+1 .. nb-1
+        const int nT = rows * (rows + 1) / 2;      // j < c <= i
+        const int nX = rows * (j + 1);             // c <= j < i
+        for (int e = tid; e < nT + nX; e += DT) {
+            if (e < nT) {
+                // counted from the last column backwards: column nb-1-p holds p+1 entries
+                const int q = nT - 1 - e;
+                int p = (int)((sqrtf(8.f * (float)q + 1.f) - 1.f) * 0.5f);
+                if ((p + 1) * (p + 2) / 2 <= q) ++p;
+                if (p * (p + 1) / 2 > q) --p;
+                const int c = nb - 1 - p, i = nb - 1 - (q - p * (p + 1) / 2);
+                const double2 a = T[i][j], b = T[c][j];
+                const double2 m = make_double2(a.x * r, a.y * r);
+                double2 t = T[i][c];
+                t.x -= m.x * b.x + m.y * b.y;
+                t.y -= m.y * b.x - m.x * b.y;
+                T[i][c] = t;
+                if (e == 0) {   // (j+1, j+1): the next pivot
+                    const double d = t.x;
+                    bad[(j + 1) & 1] = (!(d > 1e-13 * d0s[j + 1]) || isinf(d)) ? j + 2 : 0;
+                    rpiv[j + 1] = 1.0 / d;
+                }
+            } else {
+                const int e2 = e - nT;
+                const int i = j + 1 + e2 / (j + 1), c = e2 % (j + 1);
+                const double2 a = T[i][j], b = X[j][c];
+                const double2 m = make_double2(a.x * r, a.y * r);
+                double2 x = X[i][c];
+                x.x -= m.x * b.x - m.y * b.y;
+                x.y -= m.x * b.y + m.y * b.x;
+                X[i][c] = x;
             }
         }
         __syncthreads();
     }
-    // L_jj = sqrt(d_j), L_ij = T_ij / sqrt(d_j)
-    if (tid < nb) {
-        const double l = sqrt(T[tid][tid].x);
-        rdiag[tid] = 1.0 / l;
-        T[tid][tid] = make_double2(l, 0.0);
-    }
-    __syncthreads();
-    for (int e = tid; e < NB * NB; e += DT) {
-        const int i = e / NB, j = e % NB;
-        if (i < nb && j < i) {
-            const double r = rdiag[j];
-            T[i][j] = make_double2(T[i][j].x * r, T[i][j].y * r);
-        }
-    }
-    __syncthreads();
-    // inverse by forward substitution down each column c:
-    // I[i][c] = (delta_ic - sum_{c <= l < i} T[i][l] I[l][c]) / T[i][i]
-    {
-        const int c = tid >> 2, part = tid & 3;
-        for (int i = 0; i < NB; ++i) {
-            double2 s = make_double2(0.0, 0.0);
-            if (i < nb && c < i)
-                for (int l = c + part; l < i; l += 4) {
-                    const double2 a = T[i][l], b = I[l][c];
-                    s.x += a.x * b.x - a.y * b.y;
-                    s.y += a.x * b.y + a.y * b.x;
-                }
-            s.x += __shfl_xor_sync(0xffffffffu, s.x, 1);
-            s.y += __shfl_xor_sync(0xffffffffu, s.y, 1);
-            s.x += __shfl_xor_sync(0xffffffffu, s.x, 2);
-            s.y += __shfl_xor_sync(0xffffffffu, s.y, 2);
-            if (part == 0) {
-                double2 v = make_double2(0.0, 0.0);
-                if (i < nb && c <= i) {
-                    const double r = rdiag[i];
-                    v = make_double2(((i == c ? 1.0 : 0.0) - s.x) * r, -s.y * r);
-                }
-                I[i][c] = v;
-            }
-            __syncwarp();
-        }
-    }
+    if (tid < nb) rs[tid] = 1.0 / sqrt(T[tid][tid].x);
     __syncthreads();
     for (int e = tid; e < nb * nb; e += DT) {
         const int i = e / nb, j = e % nb;
-        A[(int64_t)(k + i) * lda + (k + j)] = j <= i ? T[i][j] : make_double2(0.0, 0.0);
-        Linv[(int64_t)(k + i) * ldi + (k + j)] = j <= i ? I[i][j] : make_double2(0.0, 0.0);
+        double2 l = make_double2(0.0, 0.0), li = make_double2(0.0, 0.0);
+        if (j < i) {
+            l = make_double2(T[i][j].x * rs[j], T[i][j].y * rs[j]);
+            li = make_double2(X[i][j].x * rs[i], X[i][j].y * rs[i]);
+        } else if (j == i) {
+            l = make_double2(T[i][i].x * rs[i], 0.0);   // sqrt(d_i)
+            li = make_double2(rs[i], 0.0);
+        }
+        A[(int64_t)(k + i) * lda + (k + j)] = l;
+        Linv[(int64_t)(k + i) * ldi + (k + j)] = li;
     }
 }
 
@@ -149,25 +151,49 @@ ZGemm single(int M, int N, int K, ZOperand A, ZOperand B, double2 *C, int64_t ld
     return g;
 }
 
-// Linv[o:o+n, o:o+n] = inverse of the lower-triangular L block (its 64-wide
-// diagonal blocks are already inverted in Linv).
-isdf_status tri_inv(const double2 *L, double2 *Linv, double2 *tmp, int64_t ld, int o, int n, double2 *part,
+// L^-1 from the inverted 32-wide diagonal blocks already in Linv, merging
+// aligned groups of blocks bottom-up: at each level, every pair (left group
+// of h rows at o, right group of r <= h rows at o + h) gets
+//   tmp = L[o+h:, o:o+h] Linv[o:o+h, o:o+h],  Linv[o+h:, o:o+h] = -Linv[o+h:, o+h:] tmp,
+// all full pairs of a level in one batched launch, a ragged last pair apart.
+isdf_status tri_inv(const double2 *L, double2 *Linv, double2 *tmp, int64_t ld, int n, double2 *part,
                     size_t part_n, cudaStream_t st)
 {
-    if (n <= NB) return ISDF_OK;
-    const int h = ((n / 2 + NB - 1) / NB) * NB;
-    ISDF_TRY(tri_inv(L, Linv, tmp, ld, o, h, part, part_n, st));
-    ISDF_TRY(tri_inv(L, Linv, tmp, ld, o + h, n - h, part, part_n, st));
-    // tmp = L[o+h:o+n, o:o+h] * Linv[o:o+h, o:o+h]   (Linv lower: k >= n)
-    ZGemm g1 = single(n - h, h, h, op(L + (int64_t)(o + h) * ld + o, ld, 1, 0),
-                      op(Linv + (int64_t)o * ld + o, ld, 1, 0), tmp, h, 1.0, 0);
-    g1.kmode = ZG_K_FROM_N0;
-    ISDF_TRY(zgemm_auto(g1, part, part_n, st));
-    // Linv[o+h:o+n, o:o+h] = -Linv[o+h:o+n, o+h:o+n] * tmp   (A lower: k <= m)
-    ZGemm g2 = single(n - h, h, n - h, op(Linv + (int64_t)(o + h) * ld + (o + h), ld, 1, 0),
-                      op(tmp, h, 1, 0), Linv + (int64_t)(o + h) * ld + o, ld, -1.0, 0);
-    g2.k_to_m_end = 1;
-    return zgemm_auto(g2, part, part_n, st);
+    const int nblk = (n + NB - 1) / NB;
+    for (int g = 1; g < nblk; g *= 2) {
+        const int h = g * NB;
+        const int full = n / (2 * h);
+        const int64_t step = (int64_t)2 * h * (ld + 1);   // from one pair's diagonal block to the next
+        if (full > 0) {
+            ZGemm g1 = single(h, h, h, op(L + (int64_t)h * ld, ld, 1, 0), op(Linv, ld, 1, 0), tmp, h, 1.0, 0);
+            g1.kmode = ZG_K_FROM_N0;   // Linv lower: k >= n
+            g1.batch = full;
+            g1.bsa = step;
+            g1.bsb = step;
+            g1.bsc = (int64_t)h * h;
+            ISDF_TRY(zgemm_auto(g1, part, part_n, st));
+            ZGemm g2 = single(h, h, h, op(Linv + (int64_t)h * (ld + 1), ld, 1, 0), op(tmp, h, 1, 0),
+                              Linv + (int64_t)h * ld, ld, -1.0, 0);
+            g2.k_to_m_end = 1;         // Linv lower: k <= m
+            g2.batch = full;
+            g2.bsa = step;
+            g2.bsb = (int64_t)h * h;
+            g2.bsc = step;
+            ISDF_TRY(zgemm_auto(g2, part, part_n, st));
+        }
+        const int o = full * 2 * h, r = n - o - h;
+        if (r > 0) {
+            ZGemm g1 = single(r, h, h, op(L + (int64_t)(o + h) * ld + o, ld, 1, 0),
+                              op(Linv + (int64_t)o * ld + o, ld, 1, 0), tmp, h, 1.0, 0);
+            g1.kmode = ZG_K_FROM_N0;
+            ISDF_TRY(zgemm_auto(g1, part, part_n, st));
+            ZGemm g2 = single(r, h, r, op(Linv + (int64_t)(o + h) * ld + (o + h), ld, 1, 0), op(tmp, h, 1, 0),
+                              Linv + (int64_t)(o + h) * ld + o, ld, -1.0, 0);
+            g2.k_to_m_end = 1;
+            ISDF_TRY(zgemm_auto(g2, part, part_n, st));
+        }
+    }
+    return ISDF_OK;
 }
 
 }  // namespace
@@ -185,10 +211,15 @@ isdf_status cholesky_inverse(const double2 *M0, double2 *L, double2 *Linv, doubl
         ISDF_LAUNCH_CHECK();
         const int rest = n - k - nb;
         if (rest <= 0) break;
-        // L21 = A21 * Lkk^-H  (in place: one 64-wide CTA column per row block, no split-K)
+        // L21 = A21 * Lkk^-H, in place: the K partitions go to `part` and the reduction
+        // writes L21, so no CTA reads what another writes (N = nb is one tile column)
         ZGemm p = single(rest, nb, nb, op(L + (int64_t)(k + nb) * ld + k, ld, 1, 0),
                          op(Linv + (int64_t)k * ld + k, 1, ld, 1), L + (int64_t)(k + nb) * ld + k, ld, 1.0, 0);
-        p.tile = 32;  // N = nb fits one tile column, so the in-place update is race-free
+        p.tile = 32;
+        if ((size_t)4 * rest * nb <= part_n && nb >= 32) {
+            p.splits = 4;
+            p.partial = part;
+        }
         ISDF_TRY(zgemm(p, stream));
         // A22 -= L21 L21^H (lower tiles)
         ZGemm u = single(rest, rest, nb, op(L + (int64_t)(k + nb) * ld + k, ld, 1, 0),
@@ -207,7 +238,7 @@ isdf_status cholesky_inverse(const double2 *M0, double2 *L, double2 *Linv, doubl
         timer_stop(tp, 3, stream, n);
         timer_start(tp, 4, stream);
     }
-    ISDF_TRY(tri_inv(L, Linv, tmp, ld, 0, n, part, part_n, stream));
+    ISDF_TRY(tri_inv(L, Linv, tmp, ld, n, part, part_n, stream));
     if (tp) {
         timer_stop(tp, 4, stream, n);
         timer_start(tp, 5, stream);

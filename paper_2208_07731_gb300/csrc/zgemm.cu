@@ -18,8 +18,8 @@ __device__ __forceinline__ double2 ld_c(const void *p, int64_t i)
 }
 
 template <typename TA, typename TB, bool DUAL, int BM, int BN>
-__device__ __forceinline__ void load_tiles(const ZGemm &g, int m0, int n0, int k0, int kend,
-                                           double2 (*As)[BK][BM + 1], double2 (*Bs)[BK][BN + 1])
+__device__ __forceinline__ void load_tiles(const ZGemm &g, int64_t oa, int64_t ob, int m0, int n0, int k0,
+                                           int kend, double2 (*As)[BK][BM + 1], double2 (*Bs)[BK][BN + 1])
 {
     const int tid = threadIdx.x;
 #pragma unroll
@@ -37,7 +37,7 @@ __device__ __forceinline__ void load_tiles(const ZGemm &g, int m0, int n0, int k
             const int m = m0 + mi, k = k0 + ki;
             double2 v = make_double2(0.0, 0.0);
             if (m < g.M && k < kend) {
-                v = ld_c<TA>(A.p, (int64_t)m * A.s0 + (int64_t)k * A.s1);
+                v = ld_c<TA>(A.p, oa + (int64_t)m * A.s0 + (int64_t)k * A.s1);
                 if (A.conj) v.y = -v.y;
             }
             As[pr][ki][mi] = v;
@@ -51,7 +51,7 @@ __device__ __forceinline__ void load_tiles(const ZGemm &g, int m0, int n0, int k
             const int n = n0 + ni, k = k0 + ki;
             double2 v = make_double2(0.0, 0.0);
             if (n < g.N && k < kend) {
-                v = ld_c<TB>(B.p, (int64_t)k * B.s0 + (int64_t)n * B.s1);
+                v = ld_c<TB>(B.p, ob + (int64_t)k * B.s0 + (int64_t)n * B.s1);
                 if (B.conj) v.y = -v.y;
             }
             Bs[pr][ki][ni] = v;
@@ -68,6 +68,11 @@ __global__ void __launch_bounds__(256) zgemm_kernel(ZGemm g)
     __shared__ double2 Bs[DUAL ? 2 : 1][BK][BN + 1];
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     if (g.lower_only && m0 + BM <= n0) return;
+    // blockIdx.z = batch index * splits + K partition
+    const int nsplit = g.splits > 1 ? g.splits : 1;
+    const int bz = blockIdx.z / nsplit, zs = blockIdx.z % nsplit;
+    const int64_t oa = DUAL ? 0 : (int64_t)bz * g.bsa, ob = DUAL ? 0 : (int64_t)bz * g.bsb;
+    const int64_t oc = DUAL ? 0 : (int64_t)bz * g.bsc;
     int kb = 0, ke = g.K;
     if (g.kmode == ZG_K_FROM_MAX_MN) kb = (max(m0, n0) / BK) * BK;
     else if (g.kmode == ZG_K_FROM_N0) kb = (n0 / BK) * BK;
@@ -75,7 +80,7 @@ __global__ void __launch_bounds__(256) zgemm_kernel(ZGemm g)
     if (g.splits > 1) {
         const int span = ke - kb;
         const int chunk = ((span + g.splits - 1) / g.splits + BK - 1) / BK * BK;
-        kb = kb + blockIdx.z * chunk;
+        kb = kb + zs * chunk;
         ke = min(ke, kb + chunk);
     }
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
@@ -91,7 +96,7 @@ __global__ void __launch_bounds__(256) zgemm_kernel(ZGemm g)
             for (int j = 0; j < (DUAL ? R : 1); ++j) acc2[i][j] = make_double2(0.0, 0.0);
     }
     for (int k0 = kb; k0 < ke; k0 += BK) {
-        load_tiles<TA, TB, DUAL, BM, BN>(g, m0, n0, k0, ke, As, Bs);
+        load_tiles<TA, TB, DUAL, BM, BN>(g, oa, ob, m0, n0, k0, ke, As, Bs);
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
@@ -129,7 +134,7 @@ __global__ void __launch_bounds__(256) zgemm_kernel(ZGemm g)
                 g.partial[((int64_t)blockIdx.z * g.M + m) * g.N + n] = acc1[i][j];
                 continue;
             }
-            const int64_t ci = (int64_t)m * g.scm + (int64_t)n * g.scn;
+            const int64_t ci = oc + (int64_t)m * g.scm + (int64_t)n * g.scn;
             double2 v;
             if (DUAL) {
                 const double2 p1 = acc1[i][j], p2 = acc2[DUAL ? i : 0][DUAL ? j : 0];
@@ -152,17 +157,20 @@ __global__ void __launch_bounds__(256) zgemm_kernel(ZGemm g)
 template <typename TC>
 __global__ void splitk_reduce(ZGemm g)
 {
-    const int64_t total = (int64_t)g.M * g.N;
+    const int64_t mn = (int64_t)g.M * g.N;
+    const int nbatch = g.batch > 1 ? g.batch : 1;
+    const int64_t total = mn * nbatch;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int m = (int)(e / g.N), n = (int)(e % g.N);
+        const int64_t bz = e / mn, r = e % mn;
+        const int m = (int)(r / g.N), n = (int)(r % g.N);
         if (g.lower_only && (m / g.tile) < (n / g.tile)) continue;
         double2 s = make_double2(0.0, 0.0);
         for (int z = 0; z < g.splits; ++z) {
-            const double2 v = g.partial[(int64_t)z * total + e];
+            const double2 v = g.partial[(bz * g.splits + z) * mn + r];
             s.x += v.x;
             s.y += v.y;
         }
-        const int64_t ci = (int64_t)m * g.scm + (int64_t)n * g.scn;
+        const int64_t ci = bz * g.bsc + (int64_t)m * g.scm + (int64_t)n * g.scn;
         double2 v = make_double2(g.alpha * s.x, g.alpha * s.y);
         if (g.beta) {
             const double2 o = cload(static_cast<const TC *>(g.C), ci);
@@ -177,9 +185,10 @@ template <typename TA, typename TB, typename TC, bool DUAL>
 isdf_status launch(const ZGemm &g, cudaStream_t st)
 {
     const int splits = g.splits > 1 ? g.splits : 1;
+    const int nbatch = g.batch > 1 ? g.batch : 1;
     const int T = g.tile == 32 ? 32 : 64;
-    dim3 grid((g.N + T - 1) / T, (g.M + T - 1) / T, splits);
-    if (grid.y > 65535u) return ISDF_ERR_UNSUPPORTED;
+    dim3 grid((g.N + T - 1) / T, (g.M + T - 1) / T, splits * nbatch);
+    if (grid.y > 65535u || (int64_t)splits * nbatch > 65535) return ISDF_ERR_UNSUPPORTED;
     if (T == 32)
         zgemm_kernel<TA, TB, TC, DUAL, 32><<<grid, 256, 0, st>>>(g);
     else
@@ -187,7 +196,7 @@ isdf_status launch(const ZGemm &g, cudaStream_t st)
     isdf_note_launch();
     ISDF_LAUNCH_CHECK();
     if (splits > 1) {
-        const int64_t total = (int64_t)g.M * g.N;
+        const int64_t total = (int64_t)g.M * g.N * nbatch;
         const unsigned gr = (unsigned)((total + 255) / 256 < 8192 ? (total + 255) / 256 : 8192);
         splitk_reduce<TC><<<gr, 256, 0, st>>>(g); isdf_note_launch();
         ISDF_LAUNCH_CHECK();
@@ -215,6 +224,7 @@ isdf_status zgemm(const ZGemm &g_in, cudaStream_t st)
     if (g.M <= 0 || g.N <= 0) return ISDF_OK;
     if (g.tile != 32) g.tile = 64;
     if (g.splits > 1 && (g.dual || !g.partial)) return ISDF_ERR_INVALID_ARG;
+    if (g.batch > 1 && g.dual) return ISDF_ERR_INVALID_ARG;
     const int a = g.A1.type, b = g.B1.type, c = g.ctype;
     if (g.dual) {
         if (g.A2.type != a || g.B2.type != b || c != ZG_C128 || b != ZG_C128) return ISDF_ERR_UNSUPPORTED;
@@ -234,7 +244,7 @@ isdf_status zgemm_auto(const ZGemm &g_in, double2 *partial, size_t partial_elems
     const int sms = 152;
     auto tiles = [&](int t) {
         const int tm = (g.M + t - 1) / t, tn = (g.N + t - 1) / t;
-        return g.lower_only ? (tm * (tn + 1)) / 2 : tm * tn;
+        return (g.lower_only ? (tm * (tn + 1)) / 2 : tm * tn) * (g.batch > 1 ? g.batch : 1);
     };
     g.tile = tiles(64) >= 2 * sms ? 64 : 32;
     const int nt = tiles(g.tile);
@@ -245,7 +255,7 @@ isdf_status zgemm_auto(const ZGemm &g_in, double2 *partial, size_t partial_elems
         const int target = (g.kmode != ZG_K_ALL || g.k_to_m_end) ? 8 * sms : 4 * sms;
         int s = 1;
         while (s < 16 && nt * s * 2 <= target && g.K / (s * 2) >= 64 &&
-               (size_t)(s * 2) * g.M * g.N <= partial_elems)
+               (size_t)(s * 2) * g.M * g.N * (g.batch > 1 ? g.batch : 1) <= partial_elems)
             s *= 2;
         if (s > 1) {
             g.splits = s;

@@ -10,7 +10,8 @@ enum { ZG_K_ALL = 0, ZG_K_FROM_MAX_MN = 1, ZG_K_FROM_N0 = 2 };
 // C(m, n) = alpha * sum_k opA(m, k) opB(k, n) + beta * C(m, n)            (single)
 // C(m, n) = P1(m, n) * conj(P2(m, n)), P_i = sum_k opA_i(m, k) opB_i(k, n) (dual)
 // opA(m, k) = [conj] A[m*sam + k*sak], opB(k, n) = [conj] B[k*sbk + n*sbn],
-// all indices counted in complex elements.
+// all indices counted in complex elements. Batched (single) form: product b
+// uses A1 + b*bsa, B1 + b*bsb, C + b*bsc.
 struct ZOperand {
     const void *p;
     int64_t s0, s1;   // A: (m, k) strides; B: (k, n) strides
@@ -34,6 +35,8 @@ struct ZGemm {
     int splits;               // > 1: split-K into `partial`, then reduced
     double2 *partial;         // splits * M * N complex128
     int tile;                 // output tile edge: 64 (default) or 32
+    int batch;                // > 1: independent products, operands offset by the strides below
+    int64_t bsa, bsb, bsc;    // batch strides of A1, B1 and C (complex elements)
 };
 
 isdf_status zgemm(const ZGemm &g, cudaStream_t st);
