@@ -15,20 +15,39 @@
 namespace {
 
 constexpr int NB = 32;    // diagonal block edge
-constexpr int DT = 128;   // threads of the diagonal-block kernel
+constexpr int EW = 128;   // element threads of the diagonal-block kernel
+constexpr int DT = EW + 32;   // plus one pivot warp
+constexpr int MAXE = (NB * (NB + 1) / 2 + NB + EW - 1) / EW;   // elements per thread and step (<= 5)
+
+// 1/d for a positive normal d: a float seed (integer conversion, rcp.approx) refined by
+// two Newton-Raphson steps r <- r + r (1 - d r), each doubling the correct bits
+// (22 -> 44 -> 88), i.e. a result within about one ulp in four dependent FMAs.
+__device__ __forceinline__ double recip_pos(double d)
+{
+    const int e = (int)((__double_as_longlong(d) >> 52) & 0x7FF) - 1023;
+    if (e < -120 || e > 120) return 1.0 / d;
+    float f;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(f) : "f"(d2f_int(d)));
+    double r = f2d_int(f);
+    double t = fma(-d, r, 1.0);
+    r = fma(r, t, r);
+    t = fma(-d, r, 1.0);
+    return fma(r, t, r);
+}
 
 // Factor the nb x nb diagonal block at (k, k) of A (lower triangle used),
 // write L_kk back (upper part zeroed) and L_kk^-1 into Linv at (k, k).
 // A pivot not above 1e-13 of M's original diagonal entry (M0) is reported.
 //
-// GB300 issues FP64 at a low rate per SM, so what matters on this one-CTA
-// critical path is the number of FP64 warp instructions. The block is
-// factored as L^ D L^H by elimination on [A | I] (one barrier per pivot):
-// step j subtracts m_i conj(A_cj) from A_ic (j < c <= i) and m_i X_jc from
-// X_ic (c <= j < i), m_i = A_ij / d_j. The active elements of a step are
-// numbered contiguously and dealt round-robin to the threads, so warps run
-// full. The thread that updates the next pivot also forms its reciprocal.
-// Afterwards L = (A's eliminated columns) D^-1/2 and L^-1 = D^-1/2 X.
+// GB300 issues FP64 at a low rate per SM, so on this one-CTA critical path
+// the FP64 instruction count and its dependency chains set the time. The
+// block is factored as L^ D L^H by elimination on [A | I], one barrier per
+// pivot: step j subtracts m_i conj(A_cj) from A_ic (j < c <= i) and m_i X_jc
+// from X_ic (c <= j < i), m_i = A_ij / d_j. The active entries of a step are
+// numbered contiguously and dealt to 128 threads, each loading all of its
+// (up to 5) entries before computing them, so that their FP64 chains overlap
+// and warps run full. A fifth warp meanwhile updates the next pivot and forms
+// 1/d_{j+1}. Afterwards L = (eliminated columns) D^-1/2 and L^-1 = D^-1/2 X.
 __global__ void __launch_bounds__(DT) potrf_diag(double2 *A, int64_t lda, const double2 *M0, double2 *Linv,
                                                 int64_t ldi, int k, int nb, DeviceStatus *st)
 {
@@ -51,7 +70,7 @@ __global__ void __launch_bounds__(DT) potrf_diag(double2 *A, int64_t lda, const 
     if (tid == 0) {
         const double d = T[0][0].x;
         bad[0] = (!(d > 1e-13 * d0s[0]) || isinf(d)) ? 1 : 0;
-        rpiv[0] = 1.0 / d;
+        rpiv[0] = recip_pos(d);
     }
     __syncthreads();
     for (int j = 0; j < nb; ++j) {
@@ -62,36 +81,64 @@ __global__ void __launch_bounds__(DT) potrf_diag(double2 *A, int64_t lda, const 
         }
         const double r = rpiv[j];
         const int rows = nb - 1 - j;               // i = j+1 .. nb-1
-        const int nT = rows * (rows + 1) / 2;      // j < c <= i
-        const int nX = rows * (j + 1);             // c <= j < i
-        for (int e = tid; e < nT + nX; e += DT) {
-            if (e < nT) {
-                // counted from the last column backwards: column nb-1-p holds p+1 entries
-                const int q = nT - 1 - e;
-                int p = (int)((sqrtf(8.f * (float)q + 1.f) - 1.f) * 0.5f);
-                if ((p + 1) * (p + 2) / 2 <= q) ++p;
-                if (p * (p + 1) / 2 > q) --p;
-                const int c = nb - 1 - p, i = nb - 1 - (q - p * (p + 1) / 2);
-                const double2 a = T[i][j], b = T[c][j];
-                const double2 m = make_double2(a.x * r, a.y * r);
-                double2 t = T[i][c];
-                t.x -= m.x * b.x + m.y * b.y;
-                t.y -= m.y * b.x - m.x * b.y;
-                T[i][c] = t;
-                if (e == 0) {   // (j+1, j+1): the next pivot
-                    const double d = t.x;
-                    bad[(j + 1) & 1] = (!(d > 1e-13 * d0s[j + 1]) || isinf(d)) ? j + 2 : 0;
-                    rpiv[j + 1] = 1.0 / d;
+        const int nT = rows * (rows + 1) / 2;      // j < c <= i; entry 0 is the next pivot (j+1, j+1)
+        const int nA = nT + rows * (j + 1);        // plus c <= j < i
+        if (tid < EW) {
+            int ii[MAXE], cc[MAXE];
+            bool on[MAXE], tp[MAXE];
+            double2 av[MAXE], bv[MAXE], tv[MAXE];
+#pragma unroll
+            for (int q = 0; q < MAXE; ++q) {
+                const int e = 1 + tid + q * EW;
+                on[q] = e < nA;
+                tp[q] = e < nT;
+                int i = 0, c = 0;
+                if (on[q]) {
+                    if (tp[q]) {
+                        // counted from the last column backwards: column nb-1-p holds p+1 entries
+                        const int qq = nT - 1 - e;
+                        int p = (int)((sqrtf(8.f * (float)qq + 1.f) - 1.f) * 0.5f);
+                        if ((p + 1) * (p + 2) / 2 <= qq) ++p;
+                        if (p * (p + 1) / 2 > qq) --p;
+                        c = nb - 1 - p;
+                        i = nb - 1 - (qq - p * (p + 1) / 2);
+                        const double2 bb = T[c][j];
+                        bv[q] = make_double2(bb.x, -bb.y);
+                        tv[q] = T[i][c];
+                    } else {
+                        const int e2 = e - nT;
+                        i = j + 1 + e2 / (j + 1);
+                        c = e2 % (j + 1);
+                        bv[q] = X[j][c];
+                        tv[q] = X[i][c];
+                    }
+                    av[q] = T[i][j];
                 }
-            } else {
-                const int e2 = e - nT;
-                const int i = j + 1 + e2 / (j + 1), c = e2 % (j + 1);
-                const double2 a = T[i][j], b = X[j][c];
-                const double2 m = make_double2(a.x * r, a.y * r);
-                double2 x = X[i][c];
-                x.x -= m.x * b.x - m.y * b.y;
-                x.y -= m.x * b.y + m.y * b.x;
-                X[i][c] = x;
+                ii[q] = i;
+                cc[q] = c;
+            }
+#pragma unroll
+            for (int q = 0; q < MAXE; ++q) {
+                if (on[q]) {   // t -= m b, m = a / d_j
+                    const double mx = av[q].x * r, my = av[q].y * r;
+                    tv[q].x = fma(-mx, bv[q].x, fma(my, bv[q].y, tv[q].x));
+                    tv[q].y = fma(-mx, bv[q].y, fma(-my, bv[q].x, tv[q].y));
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < MAXE; ++q) {
+                if (on[q]) {
+                    if (tp[q]) T[ii[q]][cc[q]] = tv[q];
+                    else X[ii[q]][cc[q]] = tv[q];
+                }
+            }
+        } else if (tid == EW) {
+            if (nT > 0) {   // the next pivot: A_{j+1,j+1} -= |A_{j+1,j}|^2 / d_j
+                const double2 a = T[j + 1][j];
+                const double d = fma(-fma(a.x, a.x, a.y * a.y), r, T[j + 1][j + 1].x);
+                T[j + 1][j + 1] = make_double2(d, 0.0);
+                bad[(j + 1) & 1] = (!(d > 1e-13 * d0s[j + 1]) || isinf(d)) ? j + 2 : 0;
+                rpiv[j + 1] = recip_pos(d);
             }
         }
         __syncthreads();
@@ -205,28 +252,69 @@ isdf_status cholesky_inverse(const double2 *M0, double2 *L, double2 *Linv, doubl
     const int64_t ld = n;
     if (tp) timer_start(tp, 3, stream);
     ISDF_CUDA_TRY(cudaMemsetAsync(Linv, 0, sizeof(double2) * (size_t)n * n, stream));
-    for (int k = 0; k < n; k += NB) {
-        const int nb = n - k < NB ? n - k : NB;
-        potrf_diag<<<1, DT, 0, stream>>>(L, ld, M0, Linv, ld, k, nb, st); isdf_note_launch();
-        ISDF_LAUNCH_CHECK();
-        const int rest = n - k - nb;
-        if (rest <= 0) break;
-        // L21 = A21 * Lkk^-H, in place: the K partitions go to `part` and the reduction
+    // Look-ahead: after the panel of block k, a side stream updates block column k+1,
+    // factors its diagonal block and forms its panel while this stream updates the rest
+    // of the trailing matrix (disjoint columns). Each stream has its own split-K scratch.
+    cudaStream_t side = (tp && tp->side) ? tp->side : nullptr;
+    const size_t side_need = (size_t)4 * n * NB;
+    double2 *pside = nullptr, *pmain = part;
+    size_t nmain = part_n;
+    if (part && part_n >= 2 * side_need) {
+        pside = part + (part_n - side_need);
+        nmain = part_n - side_need;
+    } else {
+        side = nullptr;
+    }
+    auto panel = [&](int k, int nb, int rest, cudaStream_t s) -> isdf_status {
+        // L21 = A21 * Lkk^-H, in place: the K partitions go to scratch and the reduction
         // writes L21, so no CTA reads what another writes (N = nb is one tile column)
         ZGemm p = single(rest, nb, nb, op(L + (int64_t)(k + nb) * ld + k, ld, 1, 0),
                          op(Linv + (int64_t)k * ld + k, 1, ld, 1), L + (int64_t)(k + nb) * ld + k, ld, 1.0, 0);
         p.tile = 32;
-        if ((size_t)4 * rest * nb <= part_n && nb >= 32) {
+        if (pside && nb >= 32) {
             p.splits = 4;
-            p.partial = part;
+            p.partial = pside;
         }
-        ISDF_TRY(zgemm(p, stream));
-        // A22 -= L21 L21^H (lower tiles)
-        ZGemm u = single(rest, rest, nb, op(L + (int64_t)(k + nb) * ld + k, ld, 1, 0),
-                         op(L + (int64_t)(k + nb) * ld + k, 1, ld, 1), L + (int64_t)(k + nb) * ld + (k + nb), ld,
-                         -1.0, 1);
-        u.lower_only = 1;
-        ISDF_TRY(zgemm_auto(u, part, part_n, stream));
+        return zgemm(p, s);
+    };
+    {
+        const int nb = n < NB ? n : NB;
+        potrf_diag<<<1, DT, 0, stream>>>(L, ld, M0, Linv, ld, 0, nb, st); isdf_note_launch();
+        ISDF_LAUNCH_CHECK();
+        if (n - nb > 0) ISDF_TRY(panel(0, nb, n - nb, stream));
+    }
+    for (int k = 0; k + NB < n; k += NB) {
+        const int k1 = k + NB, rest = n - k1;              // next block at k1, rows below block k
+        const int nb1 = rest < NB ? rest : NB, rest1 = rest - nb1;
+        cudaStream_t s2 = side ? side : stream;
+        if (side) {
+            ISDF_CUDA_TRY(cudaEventRecord(tp->ev_fork, stream));
+            ISDF_CUDA_TRY(cudaStreamWaitEvent(side, tp->ev_fork, 0));
+        }
+        // side: A[k1:, k1:k1+nb1] -= L21 L21[0:nb1]^H, then factor block k1 and its panel
+        ZGemm a = single(rest, nb1, NB, op(L + (int64_t)k1 * ld + k, ld, 1, 0), op(L + (int64_t)k1 * ld + k, 1, ld, 1),
+                         L + (int64_t)k1 * ld + k1, ld, -1.0, 1);
+        a.tile = 32;
+        if (pside) {
+            a.splits = 4;
+            a.partial = pside;
+        }
+        ISDF_TRY(zgemm(a, s2));
+        potrf_diag<<<1, DT, 0, s2>>>(L, ld, M0, Linv, ld, k1, nb1, st); isdf_note_launch();
+        ISDF_LAUNCH_CHECK();
+        if (rest1 > 0) ISDF_TRY(panel(k1, nb1, rest1, s2));
+        // this stream: A[k1+nb1:, k1+nb1:] -= L21[nb1:] L21[nb1:]^H (lower tiles)
+        if (rest1 > 0) {
+            const double2 *l21 = L + (int64_t)(k1 + nb1) * ld + k;
+            ZGemm u = single(rest1, rest1, NB, op(l21, ld, 1, 0), op(l21, 1, ld, 1),
+                             L + (int64_t)(k1 + nb1) * ld + (k1 + nb1), ld, -1.0, 1);
+            u.lower_only = 1;
+            ISDF_TRY(zgemm_auto(u, pmain, nmain, stream));
+        }
+        if (side) {
+            ISDF_CUDA_TRY(cudaEventRecord(tp->ev_join, side));
+            ISDF_CUDA_TRY(cudaStreamWaitEvent(stream, tp->ev_join, 0));
+        }
     }
     {
         const int64_t total = (int64_t)n * n;

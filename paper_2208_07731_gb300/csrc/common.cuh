@@ -44,6 +44,41 @@ __device__ __forceinline__ void set_status(DeviceStatus *st, int32_t code, int32
 }
 
 // ---- complex arithmetic on double2 (re, im) --------------------------------
+// double -> float with integer operations only (the FP64 pipe is the scarce unit on
+// GB300): the mantissa is rounded half-up at bit 29 (error <= 2^-24 relative), values
+// below float's normal range become +-0, overflow becomes inf and a NaN stays a NaN.
+__device__ __forceinline__ float d2f_int(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+    const int e = (int)((b >> 52) & 0x7FF) - 1023 + 127;
+    unsigned int f;
+    if (e == 0x7FF - 1023 + 127)
+        f = 0x7F800000u | ((b & 0xFFFFFFFFFFFFFull) ? 0x400000u : 0u);
+    else if (e <= 0)
+        f = 0u;
+    else if (e >= 255)
+        f = 0x7F800000u;
+    else {
+        f = ((unsigned int)e << 23) | (unsigned int)((b >> 29) & 0x7FFFFFu);
+        f += (unsigned int)((b >> 28) & 1u);   // carries into the exponent when the mantissa is full
+        if (f > 0x7F800000u) f = 0x7F800000u;
+    }
+    return __uint_as_float(sign | f);
+}
+
+// float -> double by moving the bits (exact for normal floats; others take the conversion)
+__device__ __forceinline__ double f2d_int(float f)
+{
+    const unsigned int u = __float_as_uint(f);
+    const unsigned int e = (u >> 23) & 0xFFu;
+    if (e == 0u || e == 0xFFu) return (double)f;
+    const unsigned long long b = ((unsigned long long)(u >> 31) << 63) |
+                                 ((unsigned long long)(e - 127u + 1023u) << 52) |
+                                 ((unsigned long long)(u & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)b);
+}
+
 __device__ __forceinline__ double2 cload(const double2 *p, int64_t i) { return p[i]; }
 __device__ __forceinline__ double2 cload(const float2 *p, int64_t i)
 {

@@ -91,14 +91,16 @@ __global__ void absmax_rows(const T *x, int64_t ld, int n, int64_t n_r, unsigned
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
             rho = acc * (1.f + 1e-5f);
         } else {
-            double acc = 0.0;
+            // converted to float first: the bounds only set power-of-two scales
+            float acc = 0.f;
             for (int i = lane; i < n; i += 32) {
                 const double2 v = cload(x, r * ld + i);
-                ma = fmaxf(ma, (float)fmax(fabs(v.x), fabs(v.y)));
-                acc += v.x * v.x + v.y * v.y;
+                const float a = d2f_int(v.x), b = d2f_int(v.y);
+                ma = fmaxf(ma, fmaxf(fabsf(a), fabsf(b)));
+                acc = fmaf(a, a, fmaf(b, b, acc));
             }
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            rho = (float)acc * (1.f + 1e-6f);
+            rho = acc * (1.f + 1e-4f);
         }
         mr = fmaxf(mr, rho);
     }
@@ -160,13 +162,14 @@ __global__ void split_orbitals(const T *x, int64_t ld, int n, int64_t n_r, const
             la = __float2half_rn(a - __half2float(ha));
             lb = __float2half_rn(b - __half2float(hb));
         } else {
+            // one rounding to float (2^-24), below the split's own 2^-22; s is a power of two
             const double2 v = cload(x, r * ld + i);
-            const double s = (double)*scale;
-            const double a = v.x * s, b = v.y * s;
-            ha = __double2half(a);
-            hb = __double2half(b);
-            la = __double2half(a - (double)__half2float(ha));
-            lb = __double2half(b - (double)__half2float(hb));
+            const float s = *scale;
+            const float a = d2f_int(v.x) * s, b = d2f_int(v.y) * s;
+            ha = __float2half_rn(a);
+            hb = __float2half_rn(b);
+            la = __float2half_rn(a - __half2float(ha));
+            lb = __float2half_rn(b - __half2float(hb));
         }
         reinterpret_cast<__half2 *>(hi)[r * n + i] = __halves2half2(ha, hb);
         reinterpret_cast<__half2 *>(lo)[r * n + i] = __halves2half2(la, lb);
@@ -496,8 +499,17 @@ __global__ void split_transposed(const T *X, int64_t ld, int R, int C, int conj,
         const int r = r0 + i, c = c0 + tx;
         float2 v = make_float2(0.f, 0.f);
         if (r < R && c < C) {
-            const double2 d = cload(X, (int64_t)r * ld + c);
-            v = make_float2((float)(d.x * (double)s), (float)((conj ? -d.y : d.y) * (double)s));
+            float fx, fy;
+            if (sizeof(T) == 8) {
+                const float2 f = reinterpret_cast<const float2 *>(X)[(int64_t)r * ld + c];
+                fx = f.x;
+                fy = f.y;
+            } else {
+                const double2 d = cload(X, (int64_t)r * ld + c);
+                fx = d2f_int(d.x);
+                fy = d2f_int(d.y);
+            }
+            v = make_float2(fx * s, (conj ? -fy : fy) * s);
         }
         tile[i][tx] = v;
     }
@@ -536,11 +548,16 @@ __global__ void hadamard_adjoint_c64(const float2 *Yb, float2 *A, float2 *B, int
 __global__ void loss_c64(const float2 *T, const float2 *G, int64_t total, double *loss)
 {
     __shared__ double red[8];
-    double acc = 0.0;
+    // compensated FP32 sum per thread (error ~2^-24 whatever the count), then FP64 across threads
+    float sum = 0.f, comp = 0.f;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const float2 t = T[e], g = G[e];
-        acc += (double)t.x * g.x + (double)t.y * g.y;
+        const float y = fmaf(t.x, g.x, t.y * g.y) - comp;
+        const float u = sum + y;
+        comp = (u - sum) - y;
+        sum = u;
     }
+    double acc = (double)sum - (double)comp;
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();

@@ -290,6 +290,12 @@ extern "C" isdf_status isdf_plan_create(isdf_plan **plan, const void *phi, int64
     p->partial_elems = (size_t)4 * 608 * 64 * 64;
     PLAN_ALLOC(p->partial, p->partial_elems);
 #undef PLAN_ALLOC
+    if (cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        isdf_plan_destroy(p);
+        return ISDF_ERR_CUDA;
+    }
     if ((s = plan_compute(p, idx, st)) != ISDF_OK) {
         isdf_plan_destroy(p);
         return s;
@@ -581,5 +587,11 @@ extern "C" void isdf_plan_destroy(isdf_plan *p)
         if (b) cudaFree(b);
     mixed_release(p);
     timing_free(p);
+    if (p->side) {
+        cudaStreamSynchronize(p->side);
+        cudaStreamDestroy(p->side);
+    }
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    if (p->ev_join) cudaEventDestroy(p->ev_join);
     free(p);
 }

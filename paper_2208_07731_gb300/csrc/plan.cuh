@@ -24,6 +24,8 @@ struct isdf_plan {
     double2 *partial;                         // split-K partials
     size_t partial_elems;
     MixedBuffers *mixed;                      // tensor-core path (ISDF_MIXED)
+    cudaStream_t side;                        // look-ahead stream of the Cholesky factorisation
+    cudaEvent_t ev_fork, ev_join;             // its fork / join points
     // optional event timing: kinds 0 Gram kernel, 1 M^-1 application kernel,
     // 2 gather + M, 3 Cholesky factor, 4 triangular inverse, 5 M^-1 = L^-H L^-1,
     // 6 tensor-core operand preparation
