@@ -39,7 +39,7 @@ UNIT = "decompositions/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="medium")
@@ -57,8 +57,8 @@ def algorithmic_flops(w):
 
 # DRAM bytes (read + write) per launch of the two tensor-core kernels from one ncu capture
 # (profiles/tc_gemm_medium.md); only valid for the workload and kernel version profiled there
-NCU_TRAFFIC = {("medium", "apply"): 925.097984e6 + 869.177600e6,
-               ("medium", "gram"): 246.058752e6 + 859.929856e6}
+NCU_TRAFFIC = {("medium", "apply"): 932.196864e6 + 875.742976e6,
+               ("medium", "gram"): 258.377216e6 + 864.972544e6}
 
 
 def peaks():
@@ -120,7 +120,8 @@ def oracle_sample(w, phi_h, psi_h, init, *, km_iters=None, theta_rows=4096, thre
     t0 = time.perf_counter()
     wt = O.weights(phi_h, psi_h)
     t["weights"] = time.perf_counter() - t0
-    T_s = km_iters if km_iters is not None else max(1, min(w.iters, 10))
+    # at most 10 Lloyd passes, 2 on the largest grids (the oracle's K-means is brute force)
+    T_s = km_iters if km_iters is not None else max(1, min(w.iters, 10 if w.n_r * w.n_mu <= 2e9 else 2))
     t0 = time.perf_counter()
     km = O.kmeans(wt, (w.n,) * 3, (w.L,) * 3, w.n_mu, init, T_s)
     # T_s Lloyd updates plus the final pass and snap; scale the updates to T
@@ -339,19 +340,21 @@ def run_ours(args):
         clocks = ClockSampler(local)
         clocks.start()
         l0 = isdf.kernel_launches()
+        # the FP64 comparison path takes ~1 s per step on the default workload: at most 5 timed steps
+        steps = args.steps if mode == "mixed" else min(args.steps, 5)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        for _ in range(args.steps):
+        for _ in range(steps):
             km = run()
         e1.record()
         torch.cuda.synchronize()
         if launches is None:
-            launches = (isdf.kernel_launches() - l0) // args.steps
+            launches = (isdf.kernel_launches() - l0) // steps
         clk = clocks.stop()
-        ms = barrier_max(e0.elapsed_time(e1)) / args.steps
+        ms = barrier_max(e0.elapsed_time(e1)) / steps
         # kernel timings: the events of the last replay (graph) or of every timed step
         kt = {k: plan.kernel_time(k) for k in isdf.TIMER_KINDS}
-        nsteps_timed = args.steps if args.no_graph else 1
+        nsteps_timed = steps if args.no_graph else 1
         plan.check()
         stats = km["stats"].cpu().tolist()
         plan_stages = {k: kt[k][0] / nsteps_timed for k in ("gather_M", "cholesky", "tri_inverse", "minv",
@@ -385,6 +388,21 @@ def run_ours(args):
                          "frac": achieved / peak, "traffic": traffic, "peak_source": src,
                          "launches": n_k, "ms_per_launch": ms_k / n_k,
                          "algorithmic_flops_per_launch": per_launch_flops}
+        # the FP64 M^-1 chain (Cholesky, triangular inverse, L^-H L^-1): zgemm_kernel, potrf_diag and
+        # split-K reductions on two streams, timed per stage; algorithmic work = the complex LAPACK
+        # counts (4/3) n^3 real flops each for potrf, trtri and lauum
+        nt = r["kt"]["cholesky"][1]
+        if nt:
+            ms_chain = sum(r["kt"][k][0] for k in ("cholesky", "tri_inverse", "minv")) / nt
+            fl = 4.0 * float(w.n_mu) ** 3
+            achieved = fl / (ms_chain * 1e-3) / 1e12
+            out["fp64_chain"] = {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
+                                 "frac": achieved / 1.25, "traffic": None,
+                                 "peak_source": "FP64 pipe, nominal 1.25 TFLOP/s (152 SMs x 2 DFMA/clk x 2.07 GHz; "
+                                                "no FP64 tensor-core MMA on GB300)",
+                                 "launches": nt, "ms_per_launch": ms_chain,
+                                 "algorithmic_flops_per_launch": fl,
+                                 "kernels": "zgemm_kernel + potrf_diag + splitk_reduce (plan update, a9 + M^-1)"}
         return out
 
     mixed = res["mixed"]
@@ -400,9 +418,12 @@ def run_ours(args):
                        "launch": "host launches" if args.no_graph else "one CUDA graph replay per step",
                        "l2": f"inputs larger than L2: Phi+Psi {2 * phi.numel() * phi.element_size() / 1e6:.0f} MB, "
                              f"Theta {w.n_r * w.n_mu * 8 / 1e6:.0f} MB written per step"},
-            "roofline": rf.get("apply"), "roofline_gram": rf.get("gram"),
+            # the dominant kernel by measured time per step; the other two alongside
+            "roofline": None, "rooflines": rf,
             "stages_ms": mixed["stages"], "gpu_launches": mixed["launches"], "clocks": mixed["clocks"],
             "kmeans_stats": dict(zip(["updates", "near_ties", "empty", "fp64_decided"], mixed["stats"]))}
+    dom = max(rf, key=lambda k: rf[k]["ms_per_launch"] * rf[k]["launches"])
+    line["roofline"] = dict(rf[dom], kernel=dom)
     if "fp64" in res:
         f = res["fp64"]
         a = mixed["theta"].to(torch.complex128)
@@ -411,31 +432,32 @@ def run_ours(args):
         same_idx = bool(torch.equal(mixed["idx"], f["idx"]))
         rf64 = roof(f, "fp64")
         line["fp64"] = {"value": world * 1e3 / f["ms"], "unit": UNIT, "ms_per_step": f["ms"],
-                        "roofline": rf64.get("apply"), "roofline_gram": rf64.get("gram"), "stages_ms": f["stages"],
+                        "rooflines": rf64, "stages_ms": f["stages"],
                         "gpu_launches": f["launches"], "clocks": f["clocks"]}
         line["theta_rel_err"] = {"mixed_vs_fp64_gpu": err, "same_idx": same_idx}
         line["speedup_mixed_vs_fp64"] = f["ms"] / mixed["ms"]
         del a
 
-    # end to end through the public API: pinned host orbitals in, Theta and idx back to pinned host, every step
+    # end to end through the public API: pinned host orbitals in, every Theta row block and idx back to
+    # pinned host memory, every step (the plan and orbital buffers of the timed run are reused)
     plan = mixed["plan"]
+    theta_dev = mixed["theta"]
     ph_h = phi.cpu().pin_memory()
     qh_h = psi.cpu().pin_memory()
-    th_h = torch.empty(mixed["theta"].shape, dtype=mixed["theta"].dtype).pin_memory()
+    blk = min(w.n_r, 262144)
+    th_h = torch.empty((blk, w.n_mu), dtype=theta_dev.dtype).pin_memory()
     idx_h = torch.empty(w.n_mu, dtype=torch.int64).pin_memory()
-    p_dev, q_dev = torch.empty_like(phi), torch.empty_like(psi)
-    plan_e2e = isdf.Plan(p_dev.copy_(phi), q_dev.copy_(psi), mixed["idx"], mode="mixed",
-                         max_rows=min(w.n_r, 262144))
-    theta_e2e = mixed["theta"]
 
     def e2e_step():
-        p_dev.copy_(ph_h, non_blocking=True)
-        q_dev.copy_(qh_h, non_blocking=True)
-        isdf.weights(p_dev, q_dev, out=wbuf)
+        phi.copy_(ph_h, non_blocking=True)
+        psi.copy_(qh_h, non_blocking=True)
+        isdf.weights(phi, psi, out=wbuf)
         km = isdf.kmeans(wbuf, shape, cell, w.n_mu, init, w.iters, workspace=ws, labels=False, objective=False)
-        plan_e2e.update(km["idx"])
-        plan_e2e.fit_theta(out=theta_e2e)
-        th_h.copy_(theta_e2e, non_blocking=True)
+        plan.update(km["idx"])
+        for b0 in range(0, w.n_r, blk):
+            nb = min(blk, w.n_r - b0)
+            plan.fit_theta(b0, nb, out=theta_dev[:nb])
+            th_h[:nb].copy_(theta_dev[:nb], non_blocking=True)
         idx_h.copy_(km["idx"], non_blocking=True)
 
     for _ in range(args.warmup):
@@ -450,10 +472,11 @@ def run_ours(args):
     e1.record()
     torch.cuda.synchronize()
     e2e_ms = barrier_max(e0.elapsed_time(e1)) / args.steps
+    plan.fit_theta(out=theta_dev)   # untimed: the full Theta again for the error check below
     line["e2e"] = {"value": world * 1e3 / e2e_ms, "unit": UNIT, "ms_per_step": e2e_ms,
                    "h2d_bytes_per_step": 2 * phi.numel() * phi.element_size(),
-                   "d2h_bytes_per_step": th_h.numel() * th_h.element_size() + idx_h.numel() * 8}
-    plan_e2e.close()
+                   "d2h_bytes_per_step": w.n_r * w.n_mu * th_h.element_size() + idx_h.numel() * 8,
+                   "theta_block_rows": blk}
 
     if rank == 0 and world == 1 and not args.no_cpu:
         import oracle as O
