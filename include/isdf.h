@@ -62,13 +62,19 @@ typedef enum { ISDF_C128 = 0, ISDF_C64 = 1 } isdf_dtype;   /* interleaved comple
 typedef enum { ISDF_W_SSM = 0, ISDF_W_PSM = 1 } isdf_wkind;
 
 /* Precision of the Theta fit.
- *  ISDF_FP64:  every step in FP64 on the FP64 pipe; Theta is complex128.
+ *  ISDF_FP64:  every step in FP64; Theta is complex128.
  *  ISDF_MIXED: the two Gram GEMMs (with the Hadamard conjugate product fused)
  *              and the application of M^-1 run on the tcgen05 tensor cores as
  *              three FP16 products of a power-of-two-scaled hi+lo split with
  *              FP32 accumulation; M, its Cholesky factor and M^-1 stay FP64.
- *              Theta is complex64. */
+ *              Theta is complex64.
+ * In both modes the large FP64 products of the plan update (M, the upper
+ * levels of the triangular inverse, M^-1 = L^-H L^-1) run on the tensor cores
+ * as exact integer-sliced products accumulated in FP64 (the Ozaki scheme),
+ * whose error is that of an FP64 GEMM; OR-ing ISDF_PLAN_FP64_SIMT into the
+ * mode keeps them on the FP64 pipe. */
 typedef enum { ISDF_FP64 = 0, ISDF_MIXED = 1 } isdf_mode;
+#define ISDF_PLAN_FP64_SIMT 0x100   /* mode flag: plan-update products on the FP64 pipe only */
 
 /* isdf_kmeans flags */
 #define ISDF_KMEANS_EARLY_STOP 1   /* stop once the labels repeat (identical result, fewer passes) */
@@ -174,6 +180,7 @@ ISDF_API isdf_status isdf_kmeans_noalloc(const double *w, int32_t nx, int32_t ny
  * complex128 scratch); larger requests are processed in several blocks.
  * The plan allocates its own device memory (cudaMalloc) and frees it in
  * isdf_plan_destroy.
+ * mode: ISDF_FP64 or ISDF_MIXED, optionally OR ISDF_PLAN_FP64_SIMT.
  * Limits: 1 <= n_mu <= 8192; n_phi, n_psi <= 4096; in ISDF_MIXED mode
  * n_mu % 64 == 0 and n_phi, n_psi % 32 == 0.
  * ------------------------------------------------------------------------- */

@@ -25,6 +25,7 @@ _lib = None
 C128, C64 = 0, 1
 SSM, PSM = 0, 1
 FP64, MIXED = 0, 1
+PLAN_FP64_SIMT = 0x100   # mode flag: plan-update products on the FP64 pipe only
 EARLY_STOP = 1
 TIMER_KINDS = {"gram": 0, "apply": 1, "gather_M": 2, "cholesky": 3, "tri_inverse": 4, "minv": 5, "mixed_prep": 6}
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA runtime error", 3: "C C^H is not Hermitian positive definite",
@@ -152,10 +153,13 @@ def kmeans(w: torch.Tensor, shape, cell, n_mu: int, init_idx: torch.Tensor, max_
 
 class Plan:
     """Theta fit at fixed interpolation points (isdf_plan_*): gathers Phi_mu,
-    Psi_mu, forms M = C C^H in FP64, factors it and forms M^-1 on creation."""
+    Psi_mu, forms M = C C^H in FP64, factors it and forms M^-1 on creation.
+    fp64_products="tensor" runs the large FP64 products of that update on the
+    tensor cores by exact integer slicing (FP64-level error); "simt" keeps
+    them on the FP64 pipe."""
 
     def __init__(self, phi: torch.Tensor, psi: torch.Tensor, idx: torch.Tensor, mode: str = "fp64",
-                 max_rows: int = 65536, stream=None):
+                 max_rows: int = 65536, stream=None, fp64_products: str = "tensor"):
         a, lda, na, ca = _orbitals(phi)
         b, ldb, nb, cb = _orbitals(psi)
         if ca != cb or a.shape[0] != b.shape[0]:
@@ -166,8 +170,11 @@ class Plan:
         self.mode = MIXED if mode == "mixed" else FP64
         self.theta_dtype = torch.complex64 if self.mode == MIXED else torch.complex128
         self._h = ctypes.c_void_p(0)
+        if fp64_products not in ("tensor", "simt"):
+            raise ValueError("fp64_products is 'tensor' (exact-slicing tensor-core products) or 'simt'")
+        flags = PLAN_FP64_SIMT if fp64_products == "simt" else 0
         _check(lib().isdf_plan_create(ctypes.byref(self._h), _ptr(a), lda, _ptr(b), ldb, self.n_r, na, nb, ca,
-                                      _ptr(self.idx), self.n_mu, self.mode, int(max_rows), _stream(stream)),
+                                      _ptr(self.idx), self.n_mu, self.mode | flags, int(max_rows), _stream(stream)),
                "isdf_plan_create")
 
     def close(self):

@@ -11,6 +11,7 @@
 #include "chol.cuh"
 #include "plan.cuh"
 #include "zgemm.cuh"
+#include "ozaki.cuh"
 
 namespace {
 
@@ -198,13 +199,23 @@ ZGemm single(int M, int N, int K, ZOperand A, ZOperand B, double2 *C, int64_t ld
     return g;
 }
 
+// FP64 product: on the tensor cores by exact slicing when the plan enables it, the
+// shape is large enough to pay for the slicing and the scratch fits; else FP64 GEMM
+isdf_status product(const ZGemm &g, double2 *part, size_t part_n, const isdf_plan *tp, cudaStream_t st)
+{
+    if (tp && tp->use_oz && (int64_t)g.M * g.N * (g.batch > 1 ? g.batch : 1) >= (int64_t)256 * 256 &&
+        g.K >= 256 && oz_fits(g, tp->oz))
+        return oz_zgemm(g, tp->oz, tp->oz_err, st);
+    return zgemm_auto(g, part, part_n, st);
+}
+
 // L^-1 from the inverted 32-wide diagonal blocks already in Linv, merging
 // aligned groups of blocks bottom-up: at each level, every pair (left group
 // of h rows at o, right group of r <= h rows at o + h) gets
 //   tmp = L[o+h:, o:o+h] Linv[o:o+h, o:o+h],  Linv[o+h:, o:o+h] = -Linv[o+h:, o+h:] tmp,
 // all full pairs of a level in one batched launch, a ragged last pair apart.
 isdf_status tri_inv(const double2 *L, double2 *Linv, double2 *tmp, int64_t ld, int n, double2 *part,
-                    size_t part_n, cudaStream_t st)
+                    size_t part_n, const isdf_plan *tp, cudaStream_t st)
 {
     const int nblk = (n + NB - 1) / NB;
     for (int g = 1; g < nblk; g *= 2) {
@@ -218,7 +229,7 @@ isdf_status tri_inv(const double2 *L, double2 *Linv, double2 *tmp, int64_t ld, i
             g1.bsa = step;
             g1.bsb = step;
             g1.bsc = (int64_t)h * h;
-            ISDF_TRY(zgemm_auto(g1, part, part_n, st));
+            ISDF_TRY(product(g1, part, part_n, tp, st));
             ZGemm g2 = single(h, h, h, op(Linv + (int64_t)h * (ld + 1), ld, 1, 0), op(tmp, h, 1, 0),
                               Linv + (int64_t)h * ld, ld, -1.0, 0);
             g2.k_to_m_end = 1;         // Linv lower: k <= m
@@ -226,18 +237,18 @@ isdf_status tri_inv(const double2 *L, double2 *Linv, double2 *tmp, int64_t ld, i
             g2.bsa = step;
             g2.bsb = (int64_t)h * h;
             g2.bsc = step;
-            ISDF_TRY(zgemm_auto(g2, part, part_n, st));
+            ISDF_TRY(product(g2, part, part_n, tp, st));
         }
         const int o = full * 2 * h, r = n - o - h;
         if (r > 0) {
             ZGemm g1 = single(r, h, h, op(L + (int64_t)(o + h) * ld + o, ld, 1, 0),
                               op(Linv + (int64_t)o * ld + o, ld, 1, 0), tmp, h, 1.0, 0);
             g1.kmode = ZG_K_FROM_N0;
-            ISDF_TRY(zgemm_auto(g1, part, part_n, st));
+            ISDF_TRY(product(g1, part, part_n, tp, st));
             ZGemm g2 = single(r, h, r, op(Linv + (int64_t)(o + h) * ld + (o + h), ld, 1, 0), op(tmp, h, 1, 0),
                               Linv + (int64_t)(o + h) * ld + o, ld, -1.0, 0);
             g2.k_to_m_end = 1;
-            ISDF_TRY(zgemm_auto(g2, part, part_n, st));
+            ISDF_TRY(product(g2, part, part_n, tp, st));
         }
     }
     return ISDF_OK;
@@ -326,7 +337,7 @@ isdf_status cholesky_inverse(const double2 *M0, double2 *L, double2 *Linv, doubl
         timer_stop(tp, 3, stream, n);
         timer_start(tp, 4, stream);
     }
-    ISDF_TRY(tri_inv(L, Linv, tmp, ld, n, part, part_n, stream));
+    ISDF_TRY(tri_inv(L, Linv, tmp, ld, n, part, part_n, tp, stream));
     if (tp) {
         timer_stop(tp, 4, stream, n);
         timer_start(tp, 5, stream);
@@ -335,7 +346,7 @@ isdf_status cholesky_inverse(const double2 *M0, double2 *L, double2 *Linv, doubl
     ZGemm w = single(n, n, n, op(Linv, 1, ld, 1), op(Linv, ld, 1, 0), W, ld, 1.0, 0);
     w.kmode = ZG_K_FROM_MAX_MN;
     w.lower_only = 1;
-    ISDF_TRY(zgemm_auto(w, part, part_n, stream));
+    ISDF_TRY(product(w, part, part_n, tp, stream));
     ISDF_TRY(hermitian_mirror(W, n, ld, stream));
     if (tp) timer_stop(tp, 5, stream, n);
     return ISDF_OK;

@@ -141,6 +141,18 @@ isdf_status alloc(T **p, size_t count)
     return ISDF_OK;
 }
 
+// M = A_mu o conj(B_mu) on the lower triangle (rows i, columns j <= i)
+__global__ void hadamard_lower(const double2 *A, const double2 *B, double2 *M, int n)
+{
+    const int64_t total = (int64_t)n * n;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / n), j = (int)(e % n);
+        if (j > i) continue;
+        const double2 a = A[e], b = B[e];
+        M[e] = make_double2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+    }
+}
+
 // Y rows (and optionally the separate factors A, B) for rows [r0, r0 + rows)
 isdf_status gram_hadamard_fp64(isdf_plan *p, int64_t r0, int rows, double2 *Y, double2 *A, double2 *B,
                                cudaStream_t st)
@@ -205,7 +217,18 @@ isdf_status plan_compute(isdf_plan *p, const int64_t *idx, cudaStream_t st)
     g.C2 = p->Bmu;
     g.lower_only = 1;
     g.splits = 1;
-    ISDF_TRY(zgemm_auto(g, nullptr, 0, st));
+    ZGemm ga = gemm1(n_mu, n_mu, n_phi, g.A1, g.B1, p->Amu, n_mu, ZG_C128, 1.0, 0);
+    ZGemm gb = gemm1(n_mu, n_mu, n_psi, g.A2, g.B2, p->Bmu, n_mu, ZG_C128, 1.0, 0);
+    ga.lower_only = gb.lower_only = 1;
+    if (p->use_oz && (int64_t)n_mu * n_mu >= (int64_t)256 * 256 && oz_fits(ga, p->oz) && oz_fits(gb, p->oz)) {
+        // the two Gram products on the tensor cores (exact slicing), then the Hadamard product
+        ISDF_TRY(oz_zgemm(ga, p->oz, p->oz_err, st));
+        ISDF_TRY(oz_zgemm(gb, p->oz, p->oz_err, st));
+        hadamard_lower<<<grid_for(nn), 256, 0, st>>>(p->Amu, p->Bmu, p->M, n_mu); isdf_note_launch();
+        ISDF_LAUNCH_CHECK();
+    } else {
+        ISDF_TRY(zgemm_auto(g, nullptr, 0, st));
+    }
     for (double2 *m : {p->M, p->Amu, p->Bmu}) ISDF_TRY(hermitian_mirror(m, n_mu, n_mu, st));
     timer_stop(p, 2, st, n_mu);
     // a9: M = L L^H, L^-1, M^-1 (FP64)
@@ -232,7 +255,10 @@ extern "C" isdf_status isdf_plan_create(isdf_plan **plan, const void *phi, int64
     if (!phi || !psi || !idx || n_r < 1 || n_phi < 1 || n_psi < 1 || ld_phi < n_phi || ld_psi < n_psi)
         return ISDF_ERR_INVALID_ARG;
     if (dtype != ISDF_C128 && dtype != ISDF_C64) return ISDF_ERR_INVALID_ARG;
+    const int32_t mflags = mode & ~0xFF;
+    mode &= 0xFF;
     if (mode != ISDF_FP64 && mode != ISDF_MIXED) return ISDF_ERR_INVALID_ARG;
+    if (mflags & ~ISDF_PLAN_FP64_SIMT) return ISDF_ERR_INVALID_ARG;
     if (n_mu < 1 || n_mu > n_r || max_rows < 1) return ISDF_ERR_INVALID_ARG;
     if (n_mu > 8192 || n_phi > 4096 || n_psi > 4096) return ISDF_ERR_UNSUPPORTED;
     if (n_phi != n_psi) return ISDF_ERR_UNSUPPORTED;
@@ -289,6 +315,26 @@ extern "C" isdf_status isdf_plan_create(isdf_plan **plan, const void *phi, int64
     // split-K is used only while tiles * splits < 2 * 304, so 608 tiles of 64 x 64 bound the partials
     p->partial_elems = (size_t)4 * 608 * 64 * 64;
     PLAN_ALLOC(p->partial, p->partial_elems);
+    p->use_oz = (mflags & ISDF_PLAN_FP64_SIMT) ? 0 : 1;
+    if (p->use_oz) {
+        // slice scratch for the largest plan-update product, n_mu x n_mu x max(n_mu, n)
+        const int kmax = n_mu > n_phi ? n_mu : n_phi;
+        size_t ha, hb, ra, rb;
+        oz_sizes(n_mu, n_mu, kmax, 1, &ha, &hb, &ra, &rb);
+        p->oz.cap_a = ha;
+        p->oz.cap_b = hb;
+        p->oz.cap_ma = ra;
+        p->oz.cap_mb = rb;
+        PLAN_ALLOC(p->oz.sa, ha);
+        PLAN_ALLOC(p->oz.sb, hb);
+        PLAN_ALLOC(p->oz.ma, ra);
+        PLAN_ALLOC(p->oz.mb, rb);
+        PLAN_ALLOC(p->oz_err, 1);
+        if (cudaMemsetAsync(p->oz_err, 0, sizeof(int), st) != cudaSuccess) {
+            isdf_plan_destroy(p);
+            return ISDF_ERR_CUDA;
+        }
+    }
 #undef PLAN_ALLOC
     if (cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
@@ -554,6 +600,11 @@ extern "C" isdf_status isdf_plan_status(isdf_plan *p, int32_t *detail)
     if (h.code == 0) {
         int32_t m = 0;
         ISDF_TRY(mixed_status(p, &m));
+        if (!m && p->oz_err) {
+            int e = 0;
+            ISDF_CUDA_TRY(cudaMemcpy(&e, p->oz_err, sizeof(int), cudaMemcpyDeviceToHost));
+            if (e) m = ISDF_ERR_TIMEOUT;
+        }
         if (m && detail) *detail = -1;
         return (isdf_status)m;
     }
@@ -582,7 +633,8 @@ extern "C" void isdf_plan_destroy(isdf_plan *p)
     if (!p) return;
     if (p->last_stream) cudaStreamSynchronize(p->last_stream);
     void *bufs[] = {p->status, p->idx, p->phi_mu, p->psi_mu, p->M, p->Amu, p->Bmu, p->L, p->Linv, p->W, p->tmp, p->tmp2,
-                    p->Mbar, p->gphi_mu, p->gpsi_mu, p->blkY, p->blkT, p->blkA, p->blkB, p->blkG, p->partial};
+                    p->Mbar, p->gphi_mu, p->gpsi_mu, p->blkY, p->blkT, p->blkA, p->blkB, p->blkG, p->partial,
+                    p->oz.sa, p->oz.sb, p->oz.ma, p->oz.mb, p->oz_err};
     for (void *b : bufs)
         if (b) cudaFree(b);
     mixed_release(p);

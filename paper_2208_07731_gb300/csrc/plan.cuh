@@ -3,6 +3,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "ozaki.cuh"
 
 struct MixedBuffers;
 
@@ -24,6 +25,9 @@ struct isdf_plan {
     double2 *partial;                         // split-K partials
     size_t partial_elems;
     MixedBuffers *mixed;                      // tensor-core path (ISDF_MIXED)
+    int use_oz;                               // plan-update products on the tensor cores (exact slicing)
+    OzWork oz;                                // their slice scratch
+    int *oz_err;                              // device flag: a bounded wait of that kernel gave up
     cudaStream_t side;                        // look-ahead stream of the Cholesky factorisation
     cudaEvent_t ev_fork, ev_join;             // its fork / join points
     // optional event timing: kinds 0 Gram kernel, 1 M^-1 application kernel,

@@ -242,26 +242,33 @@ isdf_status zgemm_auto(const ZGemm &g_in, double2 *partial, size_t partial_elems
 {
     ZGemm g = g_in;
     const int sms = 152;
+    const size_t nbatch = g.batch > 1 ? (size_t)g.batch : 1;
     auto tiles = [&](int t) {
         const int tm = (g.M + t - 1) / t, tn = (g.N + t - 1) / t;
-        return (g.lower_only ? (tm * (tn + 1)) / 2 : tm * tn) * (g.batch > 1 ? g.batch : 1);
+        return (g.lower_only ? (tm * (tn + 1)) / 2 : tm * tn) * (int)nbatch;
     };
-    g.tile = tiles(64) >= 2 * sms ? 64 : 32;
-    const int nt = tiles(g.tile);
-    g.splits = 1;
-    if (!g.dual && partial) {
-        // tiles with a triangular K range carry up to twice the average work, so they get more
-        // splits; the target is ~8 CTAs per SM of balanced work
-        const int target = (g.kmode != ZG_K_ALL || g.k_to_m_end) ? 8 * sms : 4 * sms;
+    // tiles with a triangular K range carry up to twice the average work, so they get more
+    // splits; the target is ~8 (triangular) or ~4 CTAs of balanced work per SM
+    const int target = (g.kmode != ZG_K_ALL || g.k_to_m_end) ? 8 * sms : 4 * sms;
+    auto splits_for = [&](int nt) {
         int s = 1;
-        while (s < 16 && nt * s * 2 <= target && g.K / (s * 2) >= 64 &&
-               (size_t)(s * 2) * g.M * g.N * (g.batch > 1 ? g.batch : 1) <= partial_elems)
-            s *= 2;
-        if (s > 1) {
-            g.splits = s;
-            g.partial = partial;
-        }
+        if (!g.dual && partial)
+            while (s < 16 && nt * s * 2 <= target && g.K / (s * 2) >= 64 &&
+                   (size_t)(s * 2) * g.M * g.N * nbatch <= partial_elems)
+                s *= 2;
+        return s;
+    };
+    // 64-wide tiles keep the FP64 pipe busier (4 x 4 accumulators a thread); take them whenever
+    // they, with split-K, still give two CTAs per SM
+    const int s64 = splits_for(tiles(64));
+    if (tiles(64) * s64 >= 2 * sms) {
+        g.tile = 64;
+        g.splits = s64;
+    } else {
+        g.tile = 32;
+        g.splits = splits_for(tiles(32));
     }
+    if (g.splits > 1) g.partial = partial;
     return zgemm(g, st);
 }
 

@@ -189,6 +189,30 @@ def test_theta_fp64_tiny(isdf, tiny):
     assert np.abs(th[idx] - np.eye(len(idx))).max() < 1e-11
 
 
+@pytest.mark.parametrize("n_mu", [1024, 320])
+def test_plan_fp64_products_tensor_vs_fp64_pipe(isdf, medium, n_mu):
+    # M, L and M^-1 from the exact-slicing tensor-core products against the FP64-pipe GEMMs
+    # and against the oracle's M and its inverse (n_mu = 320: padded K and a ragged last tile)
+    w, phi, psi = medium
+    wt = O.weights(phi.numpy(), psi.numpy())
+    idx = W.init_indices(wt, n_mu, 77)
+    P, Q, I = phi.to(DEV), psi.to(DEV), torch.from_numpy(idx)
+    pt = isdf.Plan(P, Q, I, mode="fp64")
+    ps = isdf.Plan(P, Q, I, mode="fp64", fp64_products="simt")
+    pt.check()
+    ps.check()
+    pm, qm = O.gather(phi.numpy(), psi.numpy(), idx)
+    M_ref = O.form_M(pm, qm)
+    Minv_ref = np.linalg.inv(M_ref)
+    for name, tol in (("M", 1e-14), ("L", 1e-13), ("Minv", 1e-12)):
+        a, b = pt.matrix(name).cpu().numpy(), ps.matrix(name).cpu().numpy()
+        assert np.linalg.norm(a - b) <= tol * np.linalg.norm(b), name
+    M = pt.matrix("M").cpu().numpy()
+    assert np.abs(M - M_ref).max() < 1e-13 * np.abs(M_ref).max()
+    Minv = pt.matrix("Minv").cpu().numpy()
+    assert np.linalg.norm(Minv - Minv_ref) < 1e-12 * np.linalg.norm(Minv_ref)
+
+
 def test_theta_fp64_medium(isdf, medium):
     w, phi, psi = medium
     idx, plan = _theta_case(isdf, w, phi, psi)
