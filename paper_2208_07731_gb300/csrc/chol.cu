@@ -16,9 +16,9 @@
 namespace {
 
 constexpr int NB = 32;    // diagonal block edge
-constexpr int EW = 128;   // element threads of the diagonal-block kernel
+constexpr int EW = 256;   // element threads of the diagonal-block kernel (2 warps per SMSP hide FP64 latency)
 constexpr int DT = EW + 32;   // plus one pivot warp
-constexpr int MAXE = (NB * (NB + 1) / 2 + NB + EW - 1) / EW;   // elements per thread and step (<= 5)
+constexpr int MAXE = (NB * (NB + 1) / 2 + NB + EW - 1) / EW;   // elements per thread and step (<= 3)
 
 // 1/d for a positive normal d: a float seed (integer conversion, rcp.approx) refined by
 // two Newton-Raphson steps r <- r + r (1 - d r), each doubling the correct bits
@@ -45,8 +45,8 @@ __device__ __forceinline__ double recip_pos(double d)
 // block is factored as L^ D L^H by elimination on [A | I], one barrier per
 // pivot: step j subtracts m_i conj(A_cj) from A_ic (j < c <= i) and m_i X_jc
 // from X_ic (c <= j < i), m_i = A_ij / d_j. The active entries of a step are
-// numbered contiguously and dealt to 128 threads, each loading all of its
-// (up to 5) entries before computing them, so that their FP64 chains overlap
+// numbered contiguously and dealt to 256 threads, each loading all of its
+// (up to 3) entries before computing them, so that their FP64 chains overlap
 // and warps run full. A fifth warp meanwhile updates the next pivot and forms
 // 1/d_{j+1}. Afterwards L = (eliminated columns) D^-1/2 and L^-1 = D^-1/2 X.
 __global__ void __launch_bounds__(DT) potrf_diag(double2 *A, int64_t lda, const double2 *M0, double2 *Linv,

@@ -1,7 +1,7 @@
 // Step 2: weighted Lloyd K-means on the real-space grid (Sec. 2.2,
 // Eq. opt second form, Eq. r_k, Algorithm 1).
 //
-// Design (one CTA of 4 warps per 4 x 8 x 8 tile of the grid; each warp owns a
+// Design (one CTA of 8 warps per 8 x 8 x 8 tile of the grid; each warp owns a
 // 4 x 4 x 4 sub-cube, two points per lane):
 //  * exact two-level pruning: the CTA bounds every centroid's squared
 //    distance to its tile from below (LB) and above (UB) in FP32 with error
@@ -26,10 +26,8 @@
 
 namespace {
 
-// 4 x 8 x 8 tiles: 432 of them on a 48^3 grid spread over 152 SMs with a smaller
-// tail than 216 tiles of 8 x 8 x 8 (2.84 vs 1.42 tiles per SM)
-constexpr int TX = 4, TY = 8, TZ = 8;    // CTA tile
-constexpr int kThreads = 128;            // 4 warps x (4 x 4 x 4 sub-cube, 2 points per lane)
+constexpr int TX = 8, TY = 8, TZ = 8;    // CTA tile (smaller tiles repeat the per-tile centroid scan)
+constexpr int kThreads = 256;            // 8 warps x (4 x 4 x 4 sub-cube, 2 points per lane)
 constexpr int kWarpCap = 256;            // per-warp candidate list capacity (else the CTA list is used)
 constexpr int kSlots = 256;              // per-CTA shared accumulators (first candidates)
 constexpr int kMaxMu = 8192;

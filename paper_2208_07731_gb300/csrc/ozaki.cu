@@ -86,18 +86,26 @@ __device__ __forceinline__ void digits(double x, int E, int (&d)[NSLICE])
 
 // per-row max |Re|, |Im| (as double bits) of the operand rows r, entries X[r sr + k sk],
 // one 32 x 32 (r, k) tile per block of 32 x 8 threads, batch in blockIdx.z
-__global__ void oz_rowmax(const double2 *X, int64_t sr, int64_t sk, int64_t bsx, int R, int K,
-                          unsigned long long *maxbits)
+// complex128 entry, or complex64 widened exactly by moving bits (no FP64 instruction)
+__device__ __forceinline__ double2 load_c(const double2 *p, int64_t i) { return p[i]; }
+__device__ __forceinline__ double2 load_c(const float2 *p, int64_t i)
+{
+    const float2 v = p[i];
+    return make_double2(f2d_int(v.x), f2d_int(v.y));
+}
+
+template <typename T>
+__global__ void oz_rowmax(const T *X, int64_t sr, int64_t sk, int64_t bsx, int R, int K, unsigned long long *maxbits)
 {
     __shared__ unsigned long long t[32][33];
     const int k0 = blockIdx.x * 32, r0 = blockIdx.y * 32, b = blockIdx.z;
-    const double2 *Xb = X + (int64_t)b * bsx;
+    const T *Xb = X + (int64_t)b * bsx;
     const bool kfast = (sk == 1);
     for (int i = threadIdx.y; i < 32; i += 8) {
         const int r = kfast ? r0 + i : r0 + (int)threadIdx.x, k = kfast ? k0 + (int)threadIdx.x : k0 + i;
         unsigned long long v = 0ull;
         if (r < R && k < K) {
-            const double2 x = Xb[(int64_t)r * sr + (int64_t)k * sk];
+            const double2 x = load_c(Xb, (int64_t)r * sr + (int64_t)k * sk);
             const unsigned long long a = (unsigned long long)__double_as_longlong(x.x) & 0x7FFFFFFFFFFFFFFFull;
             const unsigned long long c = (unsigned long long)__double_as_longlong(x.y) & 0x7FFFFFFFFFFFFFFFull;
             v = a > c ? a : c;
@@ -117,18 +125,19 @@ __global__ void oz_rowmax(const double2 *X, int64_t sr, int64_t sk, int64_t bsx,
 // digit slices of the operand rows: plain (A role: real row r = (Re, Im) interleaved over k)
 // or rotated (B role: rows 2r and 2r+1 of Bh for x = value); slice s of row r of product b
 // at out[((b NSLICE + s) Rp + row) Kp + column]
-__global__ void oz_slice(const double2 *X, int64_t sr, int64_t sk, int64_t bsx, int R, int K, int conj,
-                         int rotated, const unsigned long long *maxbits, __half *out, int64_t Rp, int64_t Kp)
+template <typename T>
+__global__ void oz_slice(const T *X, int64_t sr, int64_t sk, int64_t bsx, int R, int K, int conj, int rotated,
+                         const unsigned long long *maxbits, __half *out, int64_t Rp, int64_t Kp)
 {
     __shared__ double2 t[32][33];
     const int k0 = blockIdx.x * 32, r0 = blockIdx.y * 32, b = blockIdx.z;
-    const double2 *Xb = X + (int64_t)b * bsx;
+    const T *Xb = X + (int64_t)b * bsx;
     const bool kfast = (sk == 1);
     for (int i = threadIdx.y; i < 32; i += 8) {
         const int r = kfast ? r0 + i : r0 + (int)threadIdx.x, k = kfast ? k0 + (int)threadIdx.x : k0 + i;
         double2 v = make_double2(0.0, 0.0);
         if (r < R && k < K) {
-            v = Xb[(int64_t)r * sr + (int64_t)k * sk];
+            v = load_c(Xb, (int64_t)r * sr + (int64_t)k * sk);
             if (conj) v.y = -v.y;
         }
         if (kfast) t[i][threadIdx.x] = v;
@@ -443,7 +452,7 @@ void oz_sizes(int M, int N, int K, int batch, size_t *halves_a, size_t *halves_b
 
 bool oz_fits(const ZGemm &g, const OzWork &w)
 {
-    if (g.dual || g.ctype != ZG_C128 || g.A1.type != ZG_C128 || g.B1.type != ZG_C128 || g.scn != 1) return false;
+    if (g.dual || g.ctype != ZG_C128 || g.scn != 1) return false;
     if (g.M < 1 || g.N < 1 || g.K < 1 || !w.sa || !w.sb || !w.ma || !w.mb) return false;
     const int batch = g.batch > 1 ? g.batch : 1;
     size_t ha, hb, ra, rb;
@@ -464,19 +473,28 @@ isdf_status oz_zgemm(const ZGemm &g, const OzWork &w, int *err, cudaStream_t st)
         ISDF_CUDA_TRY(cudaMemsetAsync(w.sb, 0, sizeof(__half) * (size_t)batch * NSLICE * Rb * Kp, st));
     ISDF_CUDA_TRY(cudaMemsetAsync(w.ma, 0, sizeof(unsigned long long) * (size_t)batch * g.M, st));
     ISDF_CUDA_TRY(cudaMemsetAsync(w.mb, 0, sizeof(unsigned long long) * (size_t)batch * g.N, st));
-    const double2 *A = static_cast<const double2 *>(g.A1.p), *B = static_cast<const double2 *>(g.B1.p);
     const dim3 blk(32, 8);
     // A role: rows m, entries A[m s0 + k s1]; B role: rows n, entries B[k s0 + n s1]
     const dim3 ga((g.K + 31) / 32, (g.M + 31) / 32, batch), gb((g.K + 31) / 32, (g.N + 31) / 32, batch);
-    oz_rowmax<<<ga, blk, 0, st>>>(A, g.A1.s0, g.A1.s1, g.bsa, g.M, g.K, w.ma);
-    isdf_note_launch();
-    oz_rowmax<<<gb, blk, 0, st>>>(B, g.B1.s1, g.B1.s0, g.bsb, g.N, g.K, w.mb);
-    isdf_note_launch();
-    oz_slice<<<ga, blk, 0, st>>>(A, g.A1.s0, g.A1.s1, g.bsa, g.M, g.K, g.A1.conj, 0, w.ma, w.sa, Ra, Kp);
-    isdf_note_launch();
+    auto slice = [&](const ZOperand &o, dim3 grid, int64_t sr, int64_t sk, int64_t bs, int R, int conj, int rot,
+                     unsigned long long *mx, __half *out, int64_t Rp) {
+        if (o.type == ZG_C64) {
+            const float2 *X = static_cast<const float2 *>(o.p);
+            oz_rowmax<float2><<<grid, blk, 0, st>>>(X, sr, sk, bs, R, g.K, mx);
+            isdf_note_launch();
+            oz_slice<float2><<<grid, blk, 0, st>>>(X, sr, sk, bs, R, g.K, conj, rot, mx, out, Rp, Kp);
+            isdf_note_launch();
+        } else {
+            const double2 *X = static_cast<const double2 *>(o.p);
+            oz_rowmax<double2><<<grid, blk, 0, st>>>(X, sr, sk, bs, R, g.K, mx);
+            isdf_note_launch();
+            oz_slice<double2><<<grid, blk, 0, st>>>(X, sr, sk, bs, R, g.K, conj, rot, mx, out, Rp, Kp);
+            isdf_note_launch();
+        }
+    };
+    slice(g.A1, ga, g.A1.s0, g.A1.s1, g.bsa, g.M, g.A1.conj, 0, w.ma, w.sa, Ra);
     // Bh is built from x = conj(op(B))
-    oz_slice<<<gb, blk, 0, st>>>(B, g.B1.s1, g.B1.s0, g.bsb, g.N, g.K, !g.B1.conj, 1, w.mb, w.sb, Rb, Kp);
-    isdf_note_launch();
+    slice(g.B1, gb, g.B1.s1, g.B1.s0, g.bsb, g.N, !g.B1.conj, 1, w.mb, w.sb, Rb);
     ISDF_LAUNCH_CHECK();
     CUtensorMap ta, tb;
     if (!oz_map(&ta, w.sa, (uint64_t)Kp, (uint64_t)batch * NSLICE * Ra) ||

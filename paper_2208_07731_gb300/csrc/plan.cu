@@ -141,6 +141,15 @@ isdf_status alloc(T **p, size_t count)
     return ISDF_OK;
 }
 
+// Y = A o conj(B) elementwise (rows x n_mu, leading dimension n_mu)
+__global__ void hadamard_full(const double2 *A, const double2 *B, double2 *Y, int64_t total)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const double2 a = A[e], b = B[e];
+        Y[e] = make_double2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+    }
+}
+
 // M = A_mu o conj(B_mu) on the lower triangle (rows i, columns j <= i)
 __global__ void hadamard_lower(const double2 *A, const double2 *B, double2 *M, int n)
 {
@@ -179,7 +188,61 @@ isdf_status gram_hadamard_fp64(isdf_plan *p, int64_t r0, int rows, double2 *Y, d
         // different K for the two products: run them as two single GEMMs + Hadamard
         return ISDF_ERR_UNSUPPORTED;
     }
+    if (p->use_oz && p->blkA && p->blkB) {
+        // the two products on the tensor cores (exact slicing), then the Hadamard product in FP64
+        double2 *pa = A ? A : p->blkA, *pb = B ? B : p->blkB;
+        ZGemm ga = gemm1(rows, p->n_mu, p->n_phi, g.A1, g.B1, pa, p->n_mu, ZG_C128, 1.0, 0);
+        ZGemm gb = gemm1(rows, p->n_mu, p->n_psi, g.A2, g.B2, pb, p->n_mu, ZG_C128, 1.0, 0);
+        if (oz_fits(ga, p->oz) && oz_fits(gb, p->oz)) {
+            ISDF_TRY(oz_zgemm(ga, p->oz, p->oz_err, st));
+            ISDF_TRY(oz_zgemm(gb, p->oz, p->oz_err, st));
+            const int64_t tot = (int64_t)rows * p->n_mu;
+            hadamard_full<<<grid_for(tot), 256, 0, st>>>(pa, pb, Y, tot); isdf_note_launch();
+            ISDF_LAUNCH_CHECK();
+            return ISDF_OK;
+        }
+    }
     return zgemm(g, st);
+}
+
+// an FP64 product of the fit or the adjoint: on the tensor cores by exact slicing when the
+// plan enables it and the scratch holds the slices, else on the FP64 pipe
+isdf_status fp64_product(isdf_plan *p, const ZGemm &g, cudaStream_t st)
+{
+    if (p->use_oz && oz_fits(g, p->oz)) return oz_zgemm(g, p->oz, p->oz_err, st);
+    return zgemm(g, st);
+}
+
+// grow the slice scratch to hold the adjoint's products over a block of grid rows
+// (K = max_rows for M-bar and Phi-bar_mu); a no-op once large enough
+isdf_status oz_reserve_adjoint(isdf_plan *p)
+{
+    const int nm = p->n_mu, n = p->n_phi > p->n_psi ? p->n_phi : p->n_psi;
+    const int64_t R = p->max_rows;
+    size_t need_a = 0, need_b = 0, need_ma = 0, need_mb = 0;
+    const int64_t shapes[4][3] = {{R, nm, nm}, {R, n, nm}, {nm, nm, R}, {nm, n, R}};
+    for (const auto &sh : shapes) {
+        size_t ha, hb, ra, rb;
+        oz_sizes((int)sh[0], (int)sh[1], (int)sh[2], 1, &ha, &hb, &ra, &rb);
+        need_a = ha > need_a ? ha : need_a;
+        need_b = hb > need_b ? hb : need_b;
+        need_ma = ra > need_ma ? ra : need_ma;
+        need_mb = rb > need_mb ? rb : need_mb;
+    }
+    auto grow = [](auto **buf, size_t &cap, size_t need) -> isdf_status {
+        if (cap >= need) return ISDF_OK;
+        if (*buf) cudaFree(*buf);
+        *buf = nullptr;
+        cap = 0;
+        ISDF_CUDA_TRY(cudaMalloc((void **)buf, sizeof(**buf) * need));
+        cap = need;
+        return ISDF_OK;
+    };
+    ISDF_TRY(grow(&p->oz.sa, p->oz.cap_a, need_a));
+    ISDF_TRY(grow(&p->oz.sb, p->oz.cap_b, need_b));
+    ISDF_TRY(grow(&p->oz.ma, p->oz.cap_ma, need_ma));
+    ISDF_TRY(grow(&p->oz.mb, p->oz.cap_mb, need_mb));
+    return ISDF_OK;
 }
 
 // a7-a9 for the current orbitals and interpolation points (no allocation)
@@ -317,10 +380,16 @@ extern "C" isdf_status isdf_plan_create(isdf_plan **plan, const void *phi, int64
     PLAN_ALLOC(p->partial, p->partial_elems);
     p->use_oz = (mflags & ISDF_PLAN_FP64_SIMT) ? 0 : 1;
     if (p->use_oz) {
-        // slice scratch for the largest plan-update product, n_mu x n_mu x max(n_mu, n)
+        // slice scratch for the largest product: n_mu x n_mu x max(n_mu, n) in the plan update, and
+        // in FP64 mode a row block max_rows x n_mu x max(n_mu, n) of the fit (with its two Gram products)
         const int kmax = n_mu > n_phi ? n_mu : n_phi;
+        const int64_t mrows = (mode == ISDF_FP64 && max_rows > n_mu) ? max_rows : n_mu;
         size_t ha, hb, ra, rb;
-        oz_sizes(n_mu, n_mu, kmax, 1, &ha, &hb, &ra, &rb);
+        oz_sizes((int)mrows, n_mu, kmax, 1, &ha, &hb, &ra, &rb);
+        if (mode == ISDF_FP64) {
+            PLAN_ALLOC(p->blkA, blk);
+            PLAN_ALLOC(p->blkB, blk);
+        }
         p->oz.cap_a = ha;
         p->oz.cap_b = hb;
         p->oz.cap_ma = ra;
@@ -371,7 +440,7 @@ extern "C" isdf_status isdf_fit_theta(isdf_plan *p, int64_t row_begin, int64_t r
         ZGemm g = gemm1(rows, p->n_mu, p->n_mu, opnd(p->blkY, p->n_mu, 1, 0, ZG_C128),
                         opnd(p->W, p->n_mu, 1, 0, ZG_C128), out, ld_theta, ZG_C128, 1.0, 0);
         timer_start(p, 1, st);
-        ISDF_TRY(zgemm(g, st));
+        ISDF_TRY(fp64_product(p, g, st));
         timer_stop(p, 1, st, rows);
     }
     return ISDF_OK;
@@ -400,15 +469,20 @@ extern "C" isdf_status isdf_fit_theta_backward(isdf_plan *p, int64_t row_begin, 
     if (!p->blkA) {
         ISDF_TRY(alloc(&p->blkA, (size_t)p->max_rows * nm));
         ISDF_TRY(alloc(&p->blkB, (size_t)p->max_rows * nm));
-        ISDF_TRY(alloc(&p->blkG, (size_t)p->max_rows * nm));
+    }
+    if (!p->blkG) ISDF_TRY(alloc(&p->blkG, (size_t)p->max_rows * nm));
+    if (p->use_oz) {
+        // the slice scratch may be reallocated: nothing queued may still read it
+        ISDF_CUDA_TRY(cudaStreamSynchronize(st));
+        ISDF_TRY(oz_reserve_adjoint(p));
     }
     for (int64_t r0 = row_begin; r0 < row_begin + row_count; r0 += p->max_rows) {
         const int rows = (int)((row_begin + row_count - r0) < p->max_rows ? (row_begin + row_count - r0) : p->max_rows);
         // recompute A_b, B_b and Y_b = A_b o conj(B_b)
         ISDF_TRY(gram_hadamard_fp64(p, r0, rows, p->blkY, p->blkA, p->blkB, st));
         // Theta_b = Y_b M^-1
-        ISDF_TRY(zgemm(gemm1(rows, nm, nm, opnd(p->blkY, nm, 1, 0, ZG_C128), opnd(p->W, nm, 1, 0, ZG_C128),
-                             p->blkT, nm, ZG_C128, 1.0, 0), st));
+        ISDF_TRY(fp64_product(p, gemm1(rows, nm, nm, opnd(p->blkY, nm, 1, 0, ZG_C128),
+                                       opnd(p->W, nm, 1, 0, ZG_C128), p->blkT, nm, ZG_C128, 1.0, 0), st));
         // G_b
         const void *G;
         int gtype;
@@ -420,8 +494,8 @@ extern "C" isdf_status isdf_fit_theta_backward(isdf_plan *p, int64_t row_begin, 
             ldg = ld_grad;
         } else {
             // G = 2 dV Theta conj(K)
-            ISDF_TRY(zgemm(gemm1(rows, nm, nm, opnd(p->blkT, nm, 1, 0, ZG_C128), opnd(K, nm, 1, 1, ZG_C128),
-                                 p->blkG, nm, ZG_C128, 2.0 * dV, 0), st));
+            ISDF_TRY(fp64_product(p, gemm1(rows, nm, nm, opnd(p->blkT, nm, 1, 0, ZG_C128),
+                                           opnd(K, nm, 1, 1, ZG_C128), p->blkG, nm, ZG_C128, 2.0 * dV, 0), st));
             G = p->blkG;
             gtype = ZG_C128;
             ldg = nm;
@@ -432,15 +506,20 @@ extern "C" isdf_status isdf_fit_theta_backward(isdf_plan *p, int64_t row_begin, 
             }
         }
         // Ybar = G M^-1 (into blkY)
-        ISDF_TRY(zgemm(gemm1(rows, nm, nm, opnd(G, ldg, 1, 0, gtype), opnd(p->W, nm, 1, 0, ZG_C128), p->blkY, nm,
-                             ZG_C128, 1.0, 0), st));
+        ISDF_TRY(fp64_product(p, gemm1(rows, nm, nm, opnd(G, ldg, 1, 0, gtype), opnd(p->W, nm, 1, 0, ZG_C128),
+                                       p->blkY, nm, ZG_C128, 1.0, 0), st));
         // Mbar -= Theta_b^H Ybar
         {
             ZGemm g = gemm1(nm, nm, rows, opnd(p->blkT, 1, nm, 1, ZG_C128), opnd(p->blkY, nm, 1, 0, ZG_C128), p->Mbar,
                             nm, ZG_C128, -1.0, 1);
             g.splits = split_count(nm, nm, rows, p->partial_elems);
             g.partial = p->partial;
-            ISDF_TRY(zgemm(g, st));
+            if (p->use_oz && oz_fits(g, p->oz)) {
+                g.splits = 1;
+                ISDF_TRY(oz_zgemm(g, p->oz, p->oz_err, st));
+            } else {
+                ISDF_TRY(zgemm(g, st));
+            }
         }
         // Abar = Ybar o B, Bbar = conj(Ybar) o A
         hadamard_adjoint<<<grid_for((int64_t)rows * nm), 256, 0, st>>>(p->blkY, p->blkA, p->blkB, (int64_t)rows * nm); isdf_note_launch();
@@ -448,10 +527,10 @@ extern "C" isdf_status isdf_fit_theta_backward(isdf_plan *p, int64_t row_begin, 
         // grad_phi[rows] += Abar Phi_mu, grad_psi[rows] += Bbar Psi_mu
         double2 *gp = static_cast<double2 *>(grad_phi) + r0 * ld_gphi;
         double2 *gq = static_cast<double2 *>(grad_psi) + r0 * ld_gpsi;
-        ISDF_TRY(zgemm(gemm1(rows, p->n_phi, nm, opnd(p->blkA, nm, 1, 0, ZG_C128),
-                             opnd(p->phi_mu, p->n_phi, 1, 0, ZG_C128), gp, ld_gphi, ZG_C128, 1.0, 1), st));
-        ISDF_TRY(zgemm(gemm1(rows, p->n_psi, nm, opnd(p->blkB, nm, 1, 0, ZG_C128),
-                             opnd(p->psi_mu, p->n_psi, 1, 0, ZG_C128), gq, ld_gpsi, ZG_C128, 1.0, 1), st));
+        ISDF_TRY(fp64_product(p, gemm1(rows, p->n_phi, nm, opnd(p->blkA, nm, 1, 0, ZG_C128),
+                                       opnd(p->phi_mu, p->n_phi, 1, 0, ZG_C128), gp, ld_gphi, ZG_C128, 1.0, 1), st));
+        ISDF_TRY(fp64_product(p, gemm1(rows, p->n_psi, nm, opnd(p->blkB, nm, 1, 0, ZG_C128),
+                                       opnd(p->psi_mu, p->n_psi, 1, 0, ZG_C128), gq, ld_gpsi, ZG_C128, 1.0, 1), st));
         // Phibar_mu += Abar^H Phi_b, Psibar_mu += Bbar^H Psi_b
         {
             ZGemm g = gemm1(nm, p->n_phi, rows, opnd(p->blkA, 1, nm, 1, ZG_C128),
@@ -459,13 +538,19 @@ extern "C" isdf_status isdf_fit_theta_backward(isdf_plan *p, int64_t row_begin, 
                             p->gphi_mu, p->n_phi, ZG_C128, 1.0, 1);
             g.splits = split_count(nm, p->n_phi, rows, p->partial_elems);
             g.partial = p->partial;
-            ISDF_TRY(zgemm(g, st));
             ZGemm h = gemm1(nm, p->n_psi, rows, opnd(p->blkB, 1, nm, 1, ZG_C128),
                             opnd(static_cast<const char *>(p->psi) + r0 * p->ld_psi * es, p->ld_psi, 1, 0, t),
                             p->gpsi_mu, p->n_psi, ZG_C128, 1.0, 1);
             h.splits = split_count(nm, p->n_psi, rows, p->partial_elems);
             h.partial = p->partial;
-            ISDF_TRY(zgemm(h, st));
+            for (ZGemm *q : {&g, &h}) {
+                if (p->use_oz && oz_fits(*q, p->oz)) {
+                    q->splits = 1;
+                    ISDF_TRY(oz_zgemm(*q, p->oz, p->oz_err, st));
+                } else {
+                    ISDF_TRY(zgemm(*q, st));
+                }
+            }
         }
     }
     return ISDF_OK;
