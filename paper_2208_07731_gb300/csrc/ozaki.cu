@@ -8,18 +8,20 @@
 // make (A Bh^T)[m][2n + p] part p of (op(A) op(B))[m][n].
 //
 // Slicing: every real row r gets E_r with max |x| < 2^E_r, and each entry is
-// written as floor(|x| 2^(56 - E_r)) = sum_{s=1..7} d_s 2^(56 - 8 s), digits
-// 0 <= d_s < 256, so x = sum_s sign(x) d_s 2^(E_r - 8 s) up to a truncation
-// below 2^(E_r - 56); integer operations only, no FP64 arithmetic.
+// rounded to F = round(x 2^(56 - E_r)) and written in balanced base 256,
+// F = sum_{s=1..7} d_s 2^(56 - 8 s) with d_2..d_7 in [-128, 127] and
+// |d_1| <= 256, so x = sum_s d_s 2^(E_r - 8 s) up to a rounding below
+// 2^(E_r - 57); integer operations only, no FP64 arithmetic.
 //
 // Products: for every pair (s, t) with s + t <= 8 (28 pairs), the FP16 GEMM
 // of the digit matrices over a K segment of 256 real terms is a sum of
-// integers of magnitude below 256 * 255^2 < 2^24, exact in the FP32
+// integers of magnitude at most 256 * 256 * 128 = 2^23, exact in the FP32
 // accumulator in any order. The epilogue converts each segment to int32 and
 // adds the segments of one group g = s + t exactly, then adds
 // alpha 2^(E_m + E_n - 8 g) times that integer to the FP64 output. The
-// neglected pairs (s + t > 8) and the truncation stay below ~2^-53 K max|a|
-// max|b| per output, the size of an FP64 GEMM's rounding error.
+// neglected pairs (s + t > 8, digits of either sign) and the rounding of the
+// operands stay below ~2^-55 K max|a| max|b| per output, the size of an
+// FP64 GEMM's rounding error.
 //
 // Kernel: persistent, one CTA per SM, 320 threads - a TMA warp (6-stage ring
 // of one 128 x 64 digit tile of A and one of B), an MMA warp (one elected
@@ -39,7 +41,7 @@ constexpr int OSTAGE = 2 * OTILE;
 constexpr int OSMEM = OSTAGES * OSTAGE + 1024;
 constexpr int NSLICE = 7, BETA = 8, GMAX = NSLICE + 1;
 constexpr int SEG = 4;                           // K chunks per TMEM accumulation (256 real terms)
-constexpr int FLUSH_AT = 120;                    // pair-segments per int32 group sum (< 2^31)
+constexpr int FLUSH_AT = 200;                    // pair-segments per int32 group sum (200 * 2^23 < 2^31)
 constexpr int OEPI = 8;
 constexpr int OTHREADS = 64 + 32 * OEPI;
 constexpr long long OWAIT = 200000000LL;         // SM cycles (~0.1 s)
@@ -66,26 +68,28 @@ __device__ __forceinline__ double pow2(int e)
     return __longlong_as_double((long long)(e + 1023) << 52);
 }
 
-// the 7 signed base-256 digits of x relative to 2^E (|x| < 2^E), from the bits of x
+// the 7 balanced base-256 digits of x relative to 2^E (|x| < 2^E), from the bits of x:
+// F = round(x 2^(56 - E)) (half away from zero), then d_7 .. d_2 in [-128, 127] taken from
+// the bottom and d_1 = what remains (|d_1| <= 256), so that x ~ sum_s d_s 2^(E - 8 s)
 __device__ __forceinline__ void digits(double x, int E, int (&d)[NSLICE])
 {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const int ef = (int)((b >> 52) & 0x7FF);
     const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (ef ? (1ull << 52) : 0ull);
-    const int sh = (ef ? ef : 1) - 1019 - E;   // floor(|x| 2^(56 - E)) = m 2^sh
-    unsigned long long f = 0ull;
-    if (sh >= 0 && sh < 8) f = m << sh;
-    else if (sh < 0 && sh > -64) f = m >> (-sh);
-    const bool neg = (b >> 63) != 0ull;
+    const int sh = (ef ? ef : 1) - 1019 - E;   // |x| 2^(56 - E) = m 2^sh
+    long long f = 0;
+    if (sh >= 0 && sh < 8) f = (long long)(m << sh);
+    else if (sh < 0 && sh > -64) f = (long long)((m + (1ull << (-sh - 1))) >> (-sh));
+    if (b >> 63) f = -f;
 #pragma unroll
-    for (int s = 0; s < NSLICE; ++s) {
-        const int v = (int)((f >> (48 - 8 * s)) & 0xFFull);
-        d[s] = neg ? -v : v;
+    for (int s = NSLICE - 1; s > 0; --s) {
+        const long long r = ((f + 128) & 255) - 128;
+        d[s] = (int)r;
+        f = (f - r) >> 8;
     }
+    d[0] = (int)f;
 }
 
-// per-row max |Re|, |Im| (as double bits) of the operand rows r, entries X[r sr + k sk],
-// one 32 x 32 (r, k) tile per block of 32 x 8 threads, batch in blockIdx.z
 // complex128 entry, or complex64 widened exactly by moving bits (no FP64 instruction)
 __device__ __forceinline__ double2 load_c(const double2 *p, int64_t i) { return p[i]; }
 __device__ __forceinline__ double2 load_c(const float2 *p, int64_t i)
@@ -94,6 +98,8 @@ __device__ __forceinline__ double2 load_c(const float2 *p, int64_t i)
     return make_double2(f2d_int(v.x), f2d_int(v.y));
 }
 
+// per-row max |Re|, |Im| (as double bits) of the operand rows r, entries X[r sr + k sk],
+// one 32 x 32 (r, k) tile per block of 32 x 8 threads, batch in blockIdx.z
 template <typename T>
 __global__ void oz_rowmax(const T *X, int64_t sr, int64_t sk, int64_t bsx, int R, int K, unsigned long long *maxbits)
 {
