@@ -3,10 +3,10 @@
 // Cholesky factor and M^-1 = L^-H L^-1.
 //
 // Right-looking Cholesky with 32-wide panels: one CTA factors the diagonal
-// block in shared memory and also inverts it; the panel below is L21 =
-// A21 L11^-H (a split-K GEMM with the inverted diagonal block); the trailing
-// lower triangle is updated by A22 -= L21 L21^H. L^-1 is then assembled
-// bottom-up from the inverted diagonal blocks, one batched launch per level:
+// block in shared memory; the panel below, L21 = A21 L11^-H, is a forward
+// substitution with L11 (one warp per row); the trailing lower triangle is
+// updated by A22 -= L21 L21^H. The diagonal blocks are then inverted together,
+// and L^-1 is assembled bottom-up from them, one batched launch per level:
 // inv([[A, 0], [B, C]]) = [[A^-1, 0], [-C^-1 B A^-1, C^-1]].
 #include "chol.cuh"
 #include "plan.cuh"
@@ -18,7 +18,7 @@ namespace {
 constexpr int NB = 32;    // diagonal block edge
 constexpr int EW = 256;   // element threads of the diagonal-block kernel (2 warps per SMSP hide FP64 latency)
 constexpr int DT = EW + 32;   // plus one pivot warp
-constexpr int MAXE = (NB * (NB + 1) / 2 + NB + EW - 1) / EW;   // elements per thread and step (<= 3)
+constexpr int MAXE = (NB * (NB + 1) / 2 + EW - 1) / EW;   // elements per thread and step (<= 3)
 
 // 1/d for a positive normal d: a float seed (integer conversion, rcp.approx) refined by
 // two Newton-Raphson steps r <- r + r (1 - d r), each doubling the correct bits
@@ -36,24 +36,25 @@ __device__ __forceinline__ double recip_pos(double d)
     return fma(r, t, r);
 }
 
-// Factor the nb x nb diagonal block at (k, k) of A (lower triangle used),
-// write L_kk back (upper part zeroed) and L_kk^-1 into Linv at (k, k).
-// A pivot not above 1e-13 of M's original diagonal entry (M0) is reported.
+// Factor the nb x nb diagonal block at (k, k) of A (lower triangle used) and
+// write L_kk back (upper part zeroed). A pivot not above 1e-13 of M's original
+// diagonal entry (M0) is reported.
 //
 // GB300 issues FP64 at a low rate per SM, so on this one-CTA critical path
 // the FP64 instruction count and its dependency chains set the time. The
-// block is factored as L^ D L^H by elimination on [A | I], one barrier per
-// pivot: step j subtracts m_i conj(A_cj) from A_ic (j < c <= i) and m_i X_jc
-// from X_ic (c <= j < i), m_i = A_ij / d_j. The active entries of a step are
-// numbered contiguously and dealt to 256 threads, each loading all of its
-// (up to 3) entries before computing them, so that their FP64 chains overlap
-// and warps run full. A fifth warp meanwhile updates the next pivot and forms
-// 1/d_{j+1}. Afterwards L = (eliminated columns) D^-1/2 and L^-1 = D^-1/2 X.
-__global__ void __launch_bounds__(DT) potrf_diag(double2 *A, int64_t lda, const double2 *M0, double2 *Linv,
-                                                int64_t ldi, int k, int nb, DeviceStatus *st)
+// block is factored as L^ D L^H by elimination, one barrier per pivot: step j
+// subtracts m_i conj(A_cj) from A_ic (j < c <= i), m_i = A_ij / d_j. The
+// active entries of a step are numbered contiguously and dealt to 256
+// threads, each loading all of its (up to 2) entries before computing them, so
+// that their FP64 chains overlap and warps run full. A ninth warp meanwhile
+// updates the next pivot and forms 1/d_{j+1}. Afterwards L = (eliminated
+// columns) D^-1/2. The inverse of L_kk is not on this critical path: the
+// panel is a forward substitution with L_kk (panel_solve) and the inverses of
+// all diagonal blocks are formed together after the factorisation (inv_diag).
+__global__ void __launch_bounds__(DT) potrf_diag(double2 *A, int64_t lda, const double2 *M0, int k, int nb,
+                                                DeviceStatus *st)
 {
     __shared__ double2 T[NB][NB + 1];
-    __shared__ double2 X[NB][NB + 1];
     __shared__ double d0s[NB];     // original diagonal entries of M
     __shared__ double rpiv[NB];    // 1 / d_j
     __shared__ double rs[NB];      // 1 / sqrt(d_j)
@@ -64,7 +65,6 @@ __global__ void __launch_bounds__(DT) potrf_diag(double2 *A, int64_t lda, const 
     for (int e = tid; e < NB * NB; e += DT) {
         const int i = e / NB, j = e % NB;
         T[i][j] = (i < nb && j <= i) ? A[(int64_t)(k + i) * lda + (k + j)] : make_double2(0.0, 0.0);
-        X[i][j] = make_double2(i == j && i < nb ? 1.0 : 0.0, 0.0);
     }
     if (tid < nb) d0s[tid] = M0[(int64_t)(k + tid) * lda + (k + tid)].x;
     __syncthreads();
@@ -83,36 +83,26 @@ __global__ void __launch_bounds__(DT) potrf_diag(double2 *A, int64_t lda, const 
         const double r = rpiv[j];
         const int rows = nb - 1 - j;               // i = j+1 .. nb-1
         const int nT = rows * (rows + 1) / 2;      // j < c <= i; entry 0 is the next pivot (j+1, j+1)
-        const int nA = nT + rows * (j + 1);        // plus c <= j < i
         if (tid < EW) {
             int ii[MAXE], cc[MAXE];
-            bool on[MAXE], tp[MAXE];
+            bool on[MAXE];
             double2 av[MAXE], bv[MAXE], tv[MAXE];
 #pragma unroll
             for (int q = 0; q < MAXE; ++q) {
                 const int e = 1 + tid + q * EW;
-                on[q] = e < nA;
-                tp[q] = e < nT;
+                on[q] = e < nT;
                 int i = 0, c = 0;
                 if (on[q]) {
-                    if (tp[q]) {
-                        // counted from the last column backwards: column nb-1-p holds p+1 entries
-                        const int qq = nT - 1 - e;
-                        int p = (int)((sqrtf(8.f * (float)qq + 1.f) - 1.f) * 0.5f);
-                        if ((p + 1) * (p + 2) / 2 <= qq) ++p;
-                        if (p * (p + 1) / 2 > qq) --p;
-                        c = nb - 1 - p;
-                        i = nb - 1 - (qq - p * (p + 1) / 2);
-                        const double2 bb = T[c][j];
-                        bv[q] = make_double2(bb.x, -bb.y);
-                        tv[q] = T[i][c];
-                    } else {
-                        const int e2 = e - nT;
-                        i = j + 1 + e2 / (j + 1);
-                        c = e2 % (j + 1);
-                        bv[q] = X[j][c];
-                        tv[q] = X[i][c];
-                    }
+                    // counted from the last column backwards: column nb-1-p holds p+1 entries
+                    const int qq = nT - 1 - e;
+                    int p = (int)((sqrtf(8.f * (float)qq + 1.f) - 1.f) * 0.5f);
+                    if ((p + 1) * (p + 2) / 2 <= qq) ++p;
+                    if (p * (p + 1) / 2 > qq) --p;
+                    c = nb - 1 - p;
+                    i = nb - 1 - (qq - p * (p + 1) / 2);
+                    const double2 bb = T[c][j];
+                    bv[q] = make_double2(bb.x, -bb.y);
+                    tv[q] = T[i][c];
                     av[q] = T[i][j];
                 }
                 ii[q] = i;
@@ -120,27 +110,21 @@ __global__ void __launch_bounds__(DT) potrf_diag(double2 *A, int64_t lda, const 
             }
 #pragma unroll
             for (int q = 0; q < MAXE; ++q) {
-                if (on[q]) {   // t -= m b, m = a / d_j
+                if (on[q]) {   // t -= m conj(b), m = a / d_j
                     const double mx = av[q].x * r, my = av[q].y * r;
                     tv[q].x = fma(-mx, bv[q].x, fma(my, bv[q].y, tv[q].x));
                     tv[q].y = fma(-mx, bv[q].y, fma(-my, bv[q].x, tv[q].y));
                 }
             }
 #pragma unroll
-            for (int q = 0; q < MAXE; ++q) {
-                if (on[q]) {
-                    if (tp[q]) T[ii[q]][cc[q]] = tv[q];
-                    else X[ii[q]][cc[q]] = tv[q];
-                }
-            }
-        } else if (tid == EW) {
-            if (nT > 0) {   // the next pivot: A_{j+1,j+1} -= |A_{j+1,j}|^2 / d_j
-                const double2 a = T[j + 1][j];
-                const double d = fma(-fma(a.x, a.x, a.y * a.y), r, T[j + 1][j + 1].x);
-                T[j + 1][j + 1] = make_double2(d, 0.0);
-                bad[(j + 1) & 1] = (!(d > 1e-13 * d0s[j + 1]) || isinf(d)) ? j + 2 : 0;
-                rpiv[j + 1] = recip_pos(d);
-            }
+            for (int q = 0; q < MAXE; ++q)
+                if (on[q]) T[ii[q]][cc[q]] = tv[q];
+        } else if (tid == EW && nT > 0) {   // the next pivot: A_{j+1,j+1} -= |A_{j+1,j}|^2 / d_j
+            const double2 a = T[j + 1][j];
+            const double d = fma(-fma(a.x, a.x, a.y * a.y), r, T[j + 1][j + 1].x);
+            T[j + 1][j + 1] = make_double2(d, 0.0);
+            bad[(j + 1) & 1] = (!(d > 1e-13 * d0s[j + 1]) || isinf(d)) ? j + 2 : 0;
+            rpiv[j + 1] = recip_pos(d);
         }
         __syncthreads();
     }
@@ -148,16 +132,84 @@ __global__ void __launch_bounds__(DT) potrf_diag(double2 *A, int64_t lda, const 
     __syncthreads();
     for (int e = tid; e < nb * nb; e += DT) {
         const int i = e / nb, j = e % nb;
-        double2 l = make_double2(0.0, 0.0), li = make_double2(0.0, 0.0);
-        if (j < i) {
-            l = make_double2(T[i][j].x * rs[j], T[i][j].y * rs[j]);
-            li = make_double2(X[i][j].x * rs[i], X[i][j].y * rs[i]);
-        } else if (j == i) {
-            l = make_double2(T[i][i].x * rs[i], 0.0);   // sqrt(d_i)
-            li = make_double2(rs[i], 0.0);
-        }
+        double2 l = make_double2(0.0, 0.0);
+        if (j < i) l = make_double2(T[i][j].x * rs[j], T[i][j].y * rs[j]);
+        else if (j == i) l = make_double2(T[i][i].x * rs[i], 0.0);   // sqrt(d_i)
         A[(int64_t)(k + i) * lda + (k + j)] = l;
-        Linv[(int64_t)(k + i) * ldi + (k + j)] = li;
+    }
+}
+
+// Panel below block k in place: row x of L21 solves x L_kk^H = a (the row of A21),
+// x_c = (a_c - sum_{l<c} x_l conj(L_cl)) / L_cc, one warp per row, lane c holding column c.
+constexpr int PW = 8;   // rows (warps) per CTA
+__global__ void __launch_bounds__(32 * PW) panel_solve(double2 *L, int64_t ld, int k, int nb, int rows,
+                                                       const DeviceStatus *st)
+{
+    __shared__ double2 Lk[NB][NB + 1];
+    __shared__ double rd[NB];
+    if (st->code != 0) return;
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        const int i = e / NB, j = e % NB;
+        Lk[i][j] = (i < nb && j <= i) ? L[(int64_t)(k + i) * ld + (k + j)] : make_double2(0.0, 0.0);
+    }
+    if (threadIdx.x < nb) rd[threadIdx.x] = 1.0 / L[(int64_t)(k + threadIdx.x) * ld + (k + threadIdx.x)].x;
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int r = blockIdx.x * PW + warp; r < rows; r += gridDim.x * PW) {
+        double2 *row = L + (int64_t)(k + nb + r) * ld + k;
+        double2 acc = lane < nb ? row[lane] : make_double2(0.0, 0.0);
+        double2 x = make_double2(0.0, 0.0);
+        for (int s = 0; s < nb; ++s) {
+            double2 xs = make_double2(acc.x * rd[s], acc.y * rd[s]);
+            xs.x = __shfl_sync(0xffffffffu, xs.x, s);
+            xs.y = __shfl_sync(0xffffffffu, xs.y, s);
+            if (lane == s) x = xs;
+            if (lane > s && lane < nb) {   // acc -= x_s conj(L_cs)
+                const double2 b = Lk[lane][s];
+                acc.x = fma(-xs.x, b.x, fma(-xs.y, b.y, acc.x));
+                acc.y = fma(-xs.y, b.x, fma(xs.x, b.y, acc.y));
+            }
+        }
+        if (lane < nb) row[lane] = x;
+    }
+}
+
+// Inverses of all diagonal blocks of L (one CTA each): with L^ = L D^-1 (unit
+// diagonal), X = L^^-1 by elimination on [L^ | I] (step j: X_ic -= L^_ij X_jc,
+// c <= j < i, one barrier per step), then L_kk^-1 = D^-1 X.
+__global__ void __launch_bounds__(EW) inv_diag(const double2 *L, int64_t ld, double2 *Linv, int64_t ldi, int n,
+                                              const DeviceStatus *st)
+{
+    __shared__ double2 T[NB][NB + 1];
+    __shared__ double2 X[NB][NB + 1];
+    __shared__ double rs[NB];   // 1 / L_jj
+    if (st->code != 0) return;
+    const int k = blockIdx.x * NB, nb = min(NB, n - k), tid = threadIdx.x;
+    for (int e = tid; e < NB * NB; e += EW) {
+        const int i = e / NB, j = e % NB;
+        T[i][j] = (i < nb && j <= i) ? L[(int64_t)(k + i) * ld + (k + j)] : make_double2(0.0, 0.0);
+        X[i][j] = make_double2(i == j && i < nb ? 1.0 : 0.0, 0.0);
+    }
+    __syncthreads();
+    if (tid < nb) rs[tid] = 1.0 / T[tid][tid].x;
+    __syncthreads();
+    for (int j = 0; j < nb; ++j) {
+        const int nX = (nb - 1 - j) * (j + 1);   // at most 16 x 16 = 256 = EW
+        for (int e = tid; e < nX; e += EW) {
+            const int i = j + 1 + e / (j + 1), c = e % (j + 1);
+            const double2 a = T[i][j], b = X[j][c];
+            const double mx = a.x * rs[j], my = a.y * rs[j];
+            double2 x = X[i][c];
+            x.x = fma(-mx, b.x, fma(my, b.y, x.x));
+            x.y = fma(-mx, b.y, fma(-my, b.x, x.y));
+            X[i][c] = x;
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < nb * nb; e += EW) {
+        const int i = e / nb, j = e % nb;
+        Linv[(int64_t)(k + i) * ldi + (k + j)] =
+            j <= i ? make_double2(X[i][j].x * rs[i], X[i][j].y * rs[i]) : make_double2(0.0, 0.0);
     }
 }
 
@@ -277,20 +329,14 @@ isdf_status cholesky_inverse(const double2 *M0, double2 *L, double2 *Linv, doubl
         side = nullptr;
     }
     auto panel = [&](int k, int nb, int rest, cudaStream_t s) -> isdf_status {
-        // L21 = A21 * Lkk^-H, in place: the K partitions go to scratch and the reduction
-        // writes L21, so no CTA reads what another writes (N = nb is one tile column)
-        ZGemm p = single(rest, nb, nb, op(L + (int64_t)(k + nb) * ld + k, ld, 1, 0),
-                         op(Linv + (int64_t)k * ld + k, 1, ld, 1), L + (int64_t)(k + nb) * ld + k, ld, 1.0, 0);
-        p.tile = 32;
-        if (pside && nb >= 32) {
-            p.splits = 4;
-            p.partial = pside;
-        }
-        return zgemm(p, s);
+        const int g = (rest + PW - 1) / PW;
+        panel_solve<<<g < 4096 ? g : 4096, 32 * PW, 0, s>>>(L, ld, k, nb, rest, st); isdf_note_launch();
+        ISDF_LAUNCH_CHECK();
+        return ISDF_OK;
     };
     {
         const int nb = n < NB ? n : NB;
-        potrf_diag<<<1, DT, 0, stream>>>(L, ld, M0, Linv, ld, 0, nb, st); isdf_note_launch();
+        potrf_diag<<<1, DT, 0, stream>>>(L, ld, M0, 0, nb, st); isdf_note_launch();
         ISDF_LAUNCH_CHECK();
         if (n - nb > 0) ISDF_TRY(panel(0, nb, n - nb, stream));
     }
@@ -311,7 +357,7 @@ isdf_status cholesky_inverse(const double2 *M0, double2 *L, double2 *Linv, doubl
             a.partial = pside;
         }
         ISDF_TRY(zgemm(a, s2));
-        potrf_diag<<<1, DT, 0, s2>>>(L, ld, M0, Linv, ld, k1, nb1, st); isdf_note_launch();
+        potrf_diag<<<1, DT, 0, s2>>>(L, ld, M0, k1, nb1, st); isdf_note_launch();
         ISDF_LAUNCH_CHECK();
         if (rest1 > 0) ISDF_TRY(panel(k1, nb1, rest1, s2));
         // this stream: A[k1+nb1:, k1+nb1:] -= L21[nb1:] L21[nb1:]^H (lower tiles)
@@ -331,6 +377,8 @@ isdf_status cholesky_inverse(const double2 *M0, double2 *L, double2 *Linv, doubl
         const int64_t total = (int64_t)n * n;
         const unsigned gr = (unsigned)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
         zero_strict_upper<<<gr, 256, 0, stream>>>(L, n, ld); isdf_note_launch();
+        // the inverted diagonal blocks of L, all at once (the first level of L^-1)
+        inv_diag<<<(n + NB - 1) / NB, EW, 0, stream>>>(L, ld, Linv, ld, n, st); isdf_note_launch();
         ISDF_LAUNCH_CHECK();
     }
     if (tp) {
