@@ -108,7 +108,7 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ CPU oracle (baseline / reference arm)
-def oracle_sample(w, phi_h, psi_h, init, *, km_iters=None, theta_rows=4096, threads=None):
+def oracle_sample(w, phi_h, psi_h, init, *, km_iters=None, theta_rows=4096, threads=None, updates=None):
     """Time the CPU FP64 oracle on a bounded sample of one decomposition and
     extrapolate to seconds per full decomposition."""
     import numpy as np
@@ -124,8 +124,10 @@ def oracle_sample(w, phi_h, psi_h, init, *, km_iters=None, theta_rows=4096, thre
     T_s = km_iters if km_iters is not None else max(1, min(w.iters, 10 if w.n_r * w.n_mu <= 2e9 else 2))
     t0 = time.perf_counter()
     km = O.kmeans(wt, (w.n,) * 3, (w.L,) * 3, w.n_mu, init, T_s)
-    # T_s Lloyd updates plus the final pass and snap; scale the updates to T
-    t["kmeans"] = (time.perf_counter() - t0) * (w.iters + 1) / (T_s + 1)
+    # T_s Lloyd updates plus the final pass and snap; scaled to the updates the GPU run performed
+    # (T, or fewer when the labels repeat earlier and the exact early stop ends the loop)
+    T_full = w.iters if updates is None else updates
+    t["kmeans"] = (time.perf_counter() - t0) * (T_full + 1) / (T_s + 1)
     idx = km["idx"]
     t0 = time.perf_counter()
     phi_mu, psi_mu = O.gather(phi_h, psi_h, idx)
@@ -136,8 +138,8 @@ def oracle_sample(w, phi_h, psi_h, init, *, km_iters=None, theta_rows=4096, thre
     O.theta_rows(phi_h, psi_h, phi_mu, psi_mu, L, rows)
     t["theta"] = (time.perf_counter() - t0) * w.n_r / len(rows)
     total = sum(t.values())
-    sample = (f"weights on all {w.n_r} rows; K-means {T_s} of {w.iters} Lloyd updates (+final pass) on the full "
-              f"grid, scaled to {w.iters}; M and Cholesky in full; Theta on {len(rows)} of {w.n_r} rows, scaled")
+    sample = (f"weights on all {w.n_r} rows; K-means {T_s} of {T_full} Lloyd updates (+final pass) on the full "
+              f"grid, scaled to {T_full}; M and Cholesky in full; Theta on {len(rows)} of {w.n_r} rows, scaled")
     return total, t, sample
 
 
@@ -281,12 +283,13 @@ def run_ours(args):
     def run_mode(mode):
         theta = torch.empty((w.n_r, w.n_mu), dtype=torch.complex64 if mode == "mixed" else torch.complex128,
                             device=dev)
-        km0 = isdf.kmeans(wbuf, shape, cell, w.n_mu, init, w.iters, workspace=ws)
+        km0 = isdf.kmeans(wbuf, shape, cell, w.n_mu, init, w.iters, workspace=ws, early_stop=True)
         plan = isdf.Plan(phi, psi, km0["idx"], mode=mode, max_rows=min(w.n_r, 262144))
 
         def step(p_in=phi, q_in=psi):
             isdf.weights(p_in, q_in, out=wbuf)
-            km = isdf.kmeans(wbuf, shape, cell, w.n_mu, init, w.iters, workspace=ws, labels=False, objective=False)
+            km = isdf.kmeans(wbuf, shape, cell, w.n_mu, init, w.iters, workspace=ws, labels=False, objective=False,
+                           early_stop=True)
             plan.update(km["idx"])
             plan.fit_theta(out=theta)
             return km
@@ -301,7 +304,8 @@ def run_ours(args):
         ev[0].record()
         isdf.weights(phi, psi, out=wbuf)
         ev[1].record()
-        km = isdf.kmeans(wbuf, shape, cell, w.n_mu, init, w.iters, workspace=ws, labels=False, objective=False)
+        km = isdf.kmeans(wbuf, shape, cell, w.n_mu, init, w.iters, workspace=ws, labels=False, objective=False,
+                           early_stop=True)
         ev[2].record()
         plan.update(km["idx"])
         ev[3].record()
@@ -424,7 +428,10 @@ def run_ours(args):
                      "K-means decisions, M, Cholesky, M^-1",
             "data": "synthetic: seeded random plane-wave Bloch orbitals, orthonormalised (no DFT data available)",
             "config": {"workload": w.name, "grid": f"{w.n}^3", "n_r": w.n_r, "L_bohr": w.L, "n_orb": w.n_orb,
-                       "n_mu": w.n_mu, "lloyd_iters": w.iters, "orbital_dtype": w.dtype, "mode": "mixed",
+                       "n_mu": w.n_mu, "lloyd_iters": w.iters,
+                       "early_stop": "exact: the loop ends once the labels repeat (identical result); "
+                                     "kmeans_stats.updates counts the Lloyd updates performed",
+                       "orbital_dtype": w.dtype, "mode": "mixed",
                        "launch": "host launches" if args.no_graph else "one CUDA graph replay per step",
                        "l2": f"inputs larger than L2: Phi+Psi {2 * phi.numel() * phi.element_size() / 1e6:.0f} MB, "
                              f"Theta {w.n_r * w.n_mu * 8 / 1e6:.0f} MB written per step"},
@@ -463,7 +470,8 @@ def run_ours(args):
         phi.copy_(ph_h, non_blocking=True)
         psi.copy_(qh_h, non_blocking=True)
         isdf.weights(phi, psi, out=wbuf)
-        km = isdf.kmeans(wbuf, shape, cell, w.n_mu, init, w.iters, workspace=ws, labels=False, objective=False)
+        km = isdf.kmeans(wbuf, shape, cell, w.n_mu, init, w.iters, workspace=ws, labels=False, objective=False,
+                           early_stop=True)
         plan.update(km["idx"])
         for b0 in range(0, w.n_r, blk):
             nb = min(blk, w.n_r - b0)
@@ -493,7 +501,7 @@ def run_ours(args):
         import oracle as O
         O.load()
         phi_h, psi_h = phi.cpu().numpy(), psi.cpu().numpy()
-        total, parts, sample = oracle_sample(w, phi_h, psi_h, init_h)
+        total, parts, sample = oracle_sample(w, phi_h, psi_h, init_h, updates=int(mixed["stats"][0]))
         line["cpu_baseline"] = {"value": 1.0 / total, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                                 "sample": sample, "seconds_by_stage": parts}
         # Theta error of both GPU modes against the oracle on a row sample

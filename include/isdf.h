@@ -77,7 +77,8 @@ typedef enum { ISDF_FP64 = 0, ISDF_MIXED = 1 } isdf_mode;
 #define ISDF_PLAN_FP64_SIMT 0x100   /* mode flag: plan-update products on the FP64 pipe only */
 
 /* isdf_kmeans flags */
-#define ISDF_KMEANS_EARLY_STOP 1   /* stop once the labels repeat (identical result, fewer passes) */
+#define ISDF_KMEANS_EARLY_STOP 1   /* stop once the labels repeat (identical result, fewer passes); detected as
+                                      an update that leaves every centroid bit-identical, one pass later */
 
 /* ---------------------------------------------------------------------------
  * Step 1: weight function (Sec. 2.2).

@@ -36,7 +36,7 @@ struct KmCtl {
     unsigned long long wmax_bits;
     unsigned long long ties;
     unsigned long long refined;
-    unsigned int changed[2];
+    unsigned int moved[2];     // update t sets moved[t & 1] when any centroid changed
     int error;
     int converged;
     int n_iter;
@@ -170,8 +170,8 @@ __global__ void km_init(KmArgs a, const int64_t *__restrict__ init_idx, int64_t 
         a.ctl->wmax_bits = 0ull;
         a.ctl->ties = 0ull;
         a.ctl->refined = 0ull;
-        a.ctl->changed[0] = 0u;
-        a.ctl->changed[1] = 0u;
+        a.ctl->moved[0] = 0u;
+        a.ctl->moved[1] = 0u;
         a.ctl->error = 0;
         a.ctl->converged = 0;
         a.ctl->n_iter = 0;
@@ -266,6 +266,19 @@ __global__ void __launch_bounds__(kThreads, 1) km_assign(KmArgs a, int t)
 {
     if (a.ctl->error) return;
     if (!FINAL && a.ctl->converged) return;
+    if (!FINAL && a.early_stop && t >= 2 && a.ctl->moved[(t - 1) & 1] == 0u) {
+        // update t-1 left every centroid bit-identical, so this and every later pass would
+        // repeat the labels and sums of pass t-1: the loop has converged. The labels first
+        // repeated at pass t-1 (labels repeat, so the sums and then the centroids repeat one
+        // update later), which is the count reported; objective entries and near-tie counts
+        // of passes 0 .. t-1 are complete. (Points of zero weight can change cluster without
+        // moving a centroid; then the count is one below the first pass whose labels repeat.)
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            a.ctl->n_iter = t - 1;
+            a.ctl->converged = 1;
+        }
+        return;
+    }
 
     extern __shared__ float4 cand[];  // n_mu entries: (qx, qy, qz, mu bits), tile-local FP32 coordinates
     __shared__ unsigned long long slot[kSlots][8];
@@ -420,7 +433,6 @@ __global__ void __launch_bounds__(kThreads, 1) km_assign(KmArgs a, int t)
 
     double jv = 0.0;
     unsigned long long my_ties = 0, my_ref = 0;
-    unsigned int my_changed = 0;
     const int s_fix = FINAL ? 0 : fixed_scale(a);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -469,10 +481,6 @@ __global__ void __launch_bounds__(kThreads, 1) km_assign(KmArgs a, int t)
             const double wr = a.w[r];
             if (FINAL || a.want_obj) jv = __dadd_rn(jv, __dmul_rn(wr, win_d));
             if (!FINAL) {
-                if (a.early_stop) {
-                    my_changed += (a.labels[r] != win_mu) ? 1u : 0u;
-                    a.labels[r] = win_mu;
-                }
                 key = win_j;
                 v[0] = fixed_of(wr, s_fix);
                 v[1] = fixed_of(__dmul_rn(wr, x), s_fix);
@@ -493,8 +501,6 @@ __global__ void __launch_bounds__(kThreads, 1) km_assign(KmArgs a, int t)
     const unsigned long long rr = block_sum_u64(my_ref, redu);
     if (tid == 0 && rr) atomicAdd(&a.ctl->refined, rr);
     if (!FINAL) {
-        const unsigned long long cc = block_sum_u64(my_changed, redu);
-        if (tid == 0 && cc) atomicAdd(&a.ctl->changed[t & 1], (unsigned int)cc);
         __syncthreads();
         for (int j = tid; j < ns; j += kThreads) {
             unsigned long long *src = &slot[j][0];
@@ -519,32 +525,31 @@ __global__ void km_update(KmArgs a, int t, int n_tiles, double *objective)
 {
     __shared__ double red[32];
     if (a.ctl->error || a.ctl->converged) return;
-    const unsigned int changed = a.ctl->changed[t & 1];
     if (blockIdx.x == 0) {
-        const double J = sum_partials(a.jpart, n_tiles, red);
+        if (objective) {
+            const double J = sum_partials(a.jpart, n_tiles, red);
+            if (threadIdx.x == 0) objective[t] = J;
+        }
         if (threadIdx.x == 0) {
-            if (objective) objective[t] = J;
-            a.ctl->changed[(t + 1) & 1] = 0u;
+            a.ctl->moved[(t + 1) & 1] = 0u;   // read by pass t (done), next written by update t + 1
+            a.ctl->n_iter = t + 1;
         }
     }
-    if (a.early_stop && t > 0 && changed == 0u) {
-        // labels repeated: the sums equal the previous ones, so the centroids
-        // would not move; later passes are skipped
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            a.ctl->converged = 1;
-            a.ctl->n_iter = t;
-        }
-        return;
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->n_iter = t + 1;
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= a.n_mu) return;
     unsigned long long *q = &a.acc[8 * (int64_t)m];
     if ((q[0] | q[1]) != 0ull) {
         const double sw = u128_to_double(q[0], q[1]);
-        a.cent[3 * m + 0] = __ddiv_rn(u128_to_double(q[2], q[3]), sw);
-        a.cent[3 * m + 1] = __ddiv_rn(u128_to_double(q[4], q[5]), sw);
-        a.cent[3 * m + 2] = __ddiv_rn(u128_to_double(q[6], q[7]), sw);
+        const double cx = __ddiv_rn(u128_to_double(q[2], q[3]), sw);
+        const double cy = __ddiv_rn(u128_to_double(q[4], q[5]), sw);
+        const double cz = __ddiv_rn(u128_to_double(q[6], q[7]), sw);
+        if (a.early_stop && (__double_as_longlong(cx) != __double_as_longlong(a.cent[3 * m]) ||
+                             __double_as_longlong(cy) != __double_as_longlong(a.cent[3 * m + 1]) ||
+                             __double_as_longlong(cz) != __double_as_longlong(a.cent[3 * m + 2])))
+            atomicOr(&a.ctl->moved[t & 1], 1u);
+        a.cent[3 * m + 0] = cx;
+        a.cent[3 * m + 1] = cy;
+        a.cent[3 * m + 2] = cz;
         a.c32[m] = make_float4((float)a.cent[3 * m], (float)a.cent[3 * m + 1], (float)a.cent[3 * m + 2], 0.f);
     }
 #pragma unroll

@@ -118,6 +118,15 @@ def test_kmeans_early_stop(isdf, tiny):
     _km_compare(isdf, wt, (w.n,) * 3, (w.L,) * 3, w.n_mu, init, 400, early=True)
 
 
+def test_kmeans_medium_early_stop(isdf, medium):
+    # converges before T = 100 (about 85 updates): count, labels, objective and ties as the oracle's
+    w, phi, psi = medium
+    wt = O.weights(phi.numpy(), psi.numpy())
+    init = W.init_indices(wt, w.n_mu, 1000 + w.seed)
+    ref, got = _km_compare(isdf, wt, (w.n,) * 3, (w.L,) * 3, w.n_mu, init, w.iters, early=True)
+    assert ref["n_iter"] < w.iters
+
+
 @pytest.mark.parametrize("shape,cell,n_mu,iters", [
     ((10, 7, 13), (3.0, 2.1, 3.9), 17, 12),       # ragged tiles on every axis
     ((5, 5, 5), (2.0, 2.0, 2.0), 1, 4),           # one cluster
