@@ -2,7 +2,7 @@
 // normal equations with a linear solver, Sec. 2.4), the inverse of the
 // Cholesky factor and M^-1 = L^-H L^-1.
 //
-// Right-looking Cholesky with 32-wide panels: one CTA factors the diagonal
+// Right-looking Cholesky with 16-wide panels: one CTA factors the diagonal
 // block in shared memory; the panel below, L21 = A21 L11^-H, is a forward
 // substitution with L11 (one warp per row); the trailing lower triangle is
 // updated by A22 -= L21 L21^H. The diagonal blocks are then inverted together,
@@ -15,10 +15,10 @@
 
 namespace {
 
-constexpr int NB = 32;    // diagonal block edge
+constexpr int NB = 16;    // diagonal block edge (short per-block FP64 chains on the critical path)
 constexpr int EW = 256;   // element threads of the diagonal-block kernel (2 warps per SMSP hide FP64 latency)
 constexpr int DT = EW + 32;   // plus one pivot warp
-constexpr int MAXE = (NB * (NB + 1) / 2 + EW - 1) / EW;   // elements per thread and step (<= 3)
+constexpr int MAXE = (NB * (NB + 1) / 2 + EW - 1) / EW;   // elements per thread and step
 
 // 1/d for a positive normal d: a float seed (integer conversion, rcp.approx) refined by
 // two Newton-Raphson steps r <- r + r (1 - d r), each doubling the correct bits
@@ -261,7 +261,7 @@ isdf_status product(const ZGemm &g, double2 *part, size_t part_n, const isdf_pla
     return zgemm_auto(g, part, part_n, st);
 }
 
-// L^-1 from the inverted 32-wide diagonal blocks already in Linv, merging
+// L^-1 from the inverted diagonal blocks (NB wide) already in Linv, merging
 // aligned groups of blocks bottom-up: at each level, every pair (left group
 // of h rows at o, right group of r <= h rows at o + h) gets
 //   tmp = L[o+h:, o:o+h] Linv[o:o+h, o:o+h],  Linv[o+h:, o:o+h] = -Linv[o+h:, o+h:] tmp,
@@ -353,7 +353,7 @@ isdf_status cholesky_inverse(const double2 *M0, double2 *L, double2 *Linv, doubl
                          L + (int64_t)k1 * ld + k1, ld, -1.0, 1);
         a.tile = 32;
         if (pside) {
-            a.splits = 4;
+            a.splits = NB >= 32 ? 4 : 2;   // K = NB in chunks of 8
             a.partial = pside;
         }
         ISDF_TRY(zgemm(a, s2));
