@@ -56,6 +56,7 @@ struct OzArgs {
     double2 *C;
     int64_t ldc, bsc;
     const unsigned long long *ma, *mb;   // row maxima (batch-major: M and N per product)
+    int *gsum;              // buffered epilogue: exact group sums [b][g - 2][M][2N] (int32), or NULL
     int *err;
 };
 
@@ -363,7 +364,27 @@ __global__ void __launch_bounds__(OTHREADS, 1)
                         if (lane == 0) tc::mbar_arrive(&tempty[accb]);
                         ++pending;
                         const bool last = (s == s_hi) && (s0 + SEG >= ke);
-                        if (pending == FLUSH_AT || last) {
+                        if (a.gsum && last) {
+                            // buffered: the group's exact sums go out as integers; oz_combine
+                            // forms the FP64 result (no FP64 work and no reads of C here)
+                            if (rv) {
+                                int *gr = a.gsum + (((int64_t)b * NSLICE + (g - 2)) * a.M + row) * (2 * (int64_t)a.N);
+                                const int c0r = 2 * cb;
+                                if (c0r + 64 <= 2 * a.N && (a.N % 2) == 0) {
+#pragma unroll
+                                    for (int q = 0; q < 16; ++q)
+                                        reinterpret_cast<int4 *>(gr + c0r)[q] =
+                                            make_int4(acc32[4 * q], acc32[4 * q + 1], acc32[4 * q + 2], acc32[4 * q + 3]);
+                                } else {
+#pragma unroll
+                                    for (int q = 0; q < 64; ++q)
+                                        if (c0r + q < 2 * a.N) gr[c0r + q] = acc32[q];
+                                }
+                            }
+                            pending = 0;
+#pragma unroll
+                            for (int i = 0; i < 64; ++i) acc32[i] = 0;
+                        } else if (!a.gsum && (pending == FLUSH_AT || last)) {
                             // C += alpha 2^(E_row + E_col - 8 g) * (exact integer sum)
                             if (rv) {
 #pragma unroll
@@ -391,6 +412,40 @@ __global__ void __launch_bounds__(OTHREADS, 1)
     tc::fence_before();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, 2 * OTN);
+}
+
+// FP64 result of a buffered product: C = beta C + alpha sum_g 2^(E_m + E_n - 8 g) S_g, one
+// thread per complex output of the computed tiles (the GEMM's tile and K-range rules)
+__global__ void oz_combine(OzArgs a)
+{
+    const int64_t total = (int64_t)a.batch * a.M * a.N;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int b = (int)(e / ((int64_t)a.M * a.N));
+        const int64_t rem = e % ((int64_t)a.M * a.N);
+        const int row = (int)(rem / a.N), c = (int)(rem % a.N);
+        const int m0 = (row / OTM) * OTM, n0 = ((2 * c) / OTN) * OTN;
+        if (a.lower_only && n0 / 2 > m0 + OTM - 1) continue;   // tile not computed: C untouched
+        int kb, ke;
+        tile_krange(a, m0, n0 / 2, kb, ke);
+        double2 *cp = a.C + (int64_t)b * a.bsc + (int64_t)row * a.ldc + c;
+        double2 o = a.beta ? *cp : make_double2(0.0, 0.0);
+        if (kb < ke) {
+            const int ea = row_exp(a.ma[(int64_t)b * a.M + row]), eb = row_exp(a.mb[(int64_t)b * a.N + c]);
+            const int *gp = a.gsum + ((int64_t)b * NSLICE * a.M + row) * (2 * (int64_t)a.N) + 2 * c;
+            const int64_t gstride = (int64_t)a.M * 2 * a.N;
+            double vx = 0.0, vy = 0.0;
+#pragma unroll
+            for (int g = 2; g <= GMAX; ++g) {
+                const int2 sg = *reinterpret_cast<const int2 *>(gp + (g - 2) * gstride);
+                const double sc = pow2(ea + eb - BETA * g);
+                vx = fma((double)sg.x, sc, vx);
+                vy = fma((double)sg.y, sc, vy);
+            }
+            o.x = fma(a.alpha, vx, o.x);
+            o.y = fma(a.alpha, vy, o.y);
+        }
+        *cp = o;
+    }
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 oz_encode()
@@ -527,10 +582,20 @@ isdf_status oz_zgemm(const ZGemm &g, const OzWork &w, int *err, cudaStream_t st)
     a.ma = w.ma;
     a.mb = w.mb;
     a.err = err;
+    // buffered epilogue when the group sums fit the scratch and no group needs a partial flush
+    const int64_t segs = (a.kchunks + SEG - 1) / SEG;
+    const size_t gneed = (size_t)batch * NSLICE * g.M * 2 * (size_t)g.N;
+    a.gsum = (w.gsum && gneed <= w.cap_g && NSLICE * segs <= FLUSH_AT) ? w.gsum : nullptr;
     const int work = batch * a.n_tm * a.n_tn;
     const unsigned grid = (unsigned)(work < oz_sms() ? work : oz_sms());
     oz_gemm<<<grid, OTHREADS, OSMEM, st>>>(ta, tb, a);
     isdf_note_launch();
+    if (a.gsum) {
+        const int64_t tot = (int64_t)batch * g.M * g.N;
+        const unsigned gc = (unsigned)((tot + 255) / 256 < 8192 ? (tot + 255) / 256 : 8192);
+        oz_combine<<<gc, 256, 0, st>>>(a);
+        isdf_note_launch();
+    }
     ISDF_LAUNCH_CHECK();
     return ISDF_OK;
 }

@@ -15,6 +15,8 @@ struct OzWork {
     size_t cap_a, cap_b;             // capacity in halves
     unsigned long long *ma, *mb;     // per-row max |x| (double bits)
     size_t cap_ma, cap_mb;           // capacity in rows
+    int *gsum;                       // exact int32 group sums of a buffered product (or NULL)
+    size_t cap_g;                    // capacity in ints
 };
 
 // Halves and rows needed for an M x N x K product (batch products).

@@ -398,6 +398,12 @@ extern "C" isdf_status isdf_plan_create(isdf_plan **plan, const void *phi, int64
         PLAN_ALLOC(p->oz.sb, hb);
         PLAN_ALLOC(p->oz.ma, ra);
         PLAN_ALLOC(p->oz.mb, rb);
+        // exact group sums of the plan-update products (n_mu x n_mu outputs), up to 1 GB
+        const size_t gints = (size_t)7 * n_mu * 2 * (size_t)n_mu;
+        if (gints * sizeof(int) <= ((size_t)1 << 30)) {
+            PLAN_ALLOC(p->oz.gsum, gints);
+            p->oz.cap_g = gints;
+        }
         PLAN_ALLOC(p->oz_err, 1);
         if (cudaMemsetAsync(p->oz_err, 0, sizeof(int), st) != cudaSuccess) {
             isdf_plan_destroy(p);
@@ -719,7 +725,7 @@ extern "C" void isdf_plan_destroy(isdf_plan *p)
     if (p->last_stream) cudaStreamSynchronize(p->last_stream);
     void *bufs[] = {p->status, p->idx, p->phi_mu, p->psi_mu, p->M, p->Amu, p->Bmu, p->L, p->Linv, p->W, p->tmp, p->tmp2,
                     p->Mbar, p->gphi_mu, p->gpsi_mu, p->blkY, p->blkT, p->blkA, p->blkB, p->blkG, p->partial,
-                    p->oz.sa, p->oz.sb, p->oz.ma, p->oz.mb, p->oz_err};
+                    p->oz.sa, p->oz.sb, p->oz.ma, p->oz.mb, p->oz.gsum, p->oz_err};
     for (void *b : bufs)
         if (b) cudaFree(b);
     mixed_release(p);
