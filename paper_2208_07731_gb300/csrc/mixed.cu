@@ -669,11 +669,13 @@ static isdf_status mixed_alloc(isdf_plan *p)
     return ISDF_OK;
 }
 
-isdf_status mixed_prepare(isdf_plan *p, cudaStream_t st)
+// The part that depends on the orbitals only: their scale bounds and FP16 hi/lo splits
+// (the Gram kernel's A operands). It may run concurrently with the FP64 plan update.
+isdf_status mixed_prepare_orbitals(isdf_plan *p, cudaStream_t st)
 {
     if (!p->mixed) ISDF_TRY(mixed_alloc(p));
     MixedBuffers *b = p->mixed;
-    const int n = p->n_phi, nm = p->n_mu;
+    const int n = p->n_phi;
     ISDF_CUDA_TRY(cudaMemsetAsync(b->sc, 0, sizeof(MixScales), st));
 
     const unsigned g = 152 * 8;
@@ -688,8 +690,7 @@ isdf_status mixed_prepare(isdf_plan *p, cudaStream_t st)
         absmax_rows<float2><<<g, 256, 0, st>>>(static_cast<const float2 *>(p->psi), p->ld_psi, n, p->n_r,
                                                &b->sc->maxabs_psi, &b->sc->maxrho_psi); isdf_note_launch();
     }
-    absmax_rows<double2><<<grid_for((int64_t)nm * 32), 256, 0, st>>>(p->W, nm, nm, nm, &b->sc->maxabs_w, nullptr); isdf_note_launch();
-    compute_scales<<<1, 1, 0, st>>>(b->sc); isdf_note_launch();
+    compute_scales<<<1, 1, 0, st>>>(b->sc); isdf_note_launch();   // s_phi, s_psi (final); M^-1's later
     ISDF_LAUNCH_CHECK();
     const int64_t tot = p->n_r * n;
     if (p->dtype == ISDF_C128) {
@@ -703,6 +704,18 @@ isdf_status mixed_prepare(isdf_plan *p, cudaStream_t st)
         split_orbitals<float2><<<grid_for(tot, 152 * 64), 256, 0, st>>>(
             static_cast<const float2 *>(p->psi), p->ld_psi, n, p->n_r, &b->sc->s_psi, b->a2h, b->a2l); isdf_note_launch();
     }
+    ISDF_LAUNCH_CHECK();
+    return ISDF_OK;
+}
+
+// The rest, after M^-1: its scale (compute_scales again: the orbital scales come out the same)
+// and the rotated B operands of Phi_mu, Psi_mu and M^-1.
+isdf_status mixed_prepare(isdf_plan *p, cudaStream_t st)
+{
+    MixedBuffers *b = p->mixed;
+    const int n = p->n_phi, nm = p->n_mu;
+    absmax_rows<double2><<<grid_for((int64_t)nm * 32), 256, 0, st>>>(p->W, nm, nm, nm, &b->sc->maxabs_w, nullptr); isdf_note_launch();
+    compute_scales<<<1, 1, 0, st>>>(b->sc); isdf_note_launch();
     build_rotated<<<grid_for((int64_t)nm * n), 256, 0, st>>>(p->phi_mu, n, nm, n, &b->sc->s_phi, b->b1h, b->b1l); isdf_note_launch();
     build_rotated<<<grid_for((int64_t)nm * n), 256, 0, st>>>(p->psi_mu, n, nm, n, &b->sc->s_psi, b->b2h, b->b2l); isdf_note_launch();
     build_rotated<<<grid_for((int64_t)nm * nm), 256, 0, st>>>(p->W, nm, nm, nm, &b->sc->s_w, b->bwh, b->bwl); isdf_note_launch();

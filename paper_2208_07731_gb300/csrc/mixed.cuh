@@ -4,6 +4,9 @@
 #include "plan.cuh"
 
 bool mixed_supported(int n, int n_mu, int64_t ld_phi, int64_t ld_psi, int dtype);
+// scale bounds and FP16 splits of the orbitals (independent of the interpolation points)
+isdf_status mixed_prepare_orbitals(isdf_plan *p, cudaStream_t st);
+// after M^-1: its scale and the rotated B operands (needs mixed_prepare_orbitals first)
 isdf_status mixed_prepare(isdf_plan *p, cudaStream_t st);
 isdf_status mixed_fit(isdf_plan *p, int64_t row_begin, int64_t row_count, void *theta, int64_t ld_theta,
                       cudaStream_t st);

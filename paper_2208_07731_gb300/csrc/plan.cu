@@ -255,6 +255,15 @@ isdf_status plan_compute(isdf_plan *p, const int64_t *idx, cudaStream_t st)
     ISDF_CUDA_TRY(cudaMemsetAsync(p->Mbar, 0, sizeof(double2) * nn, st));
     ISDF_CUDA_TRY(cudaMemsetAsync(p->gphi_mu, 0, sizeof(double2) * n_mu * n_phi, st));
     ISDF_CUDA_TRY(cudaMemsetAsync(p->gpsi_mu, 0, sizeof(double2) * n_mu * n_psi, st));
+    // the orbitals' FP16 operands (mixed mode) do not depend on the points: prepared on a
+    // third stream while this one runs the FP64 update
+    const bool fork_aux = p->mode == ISDF_MIXED && p->aux;
+    if (fork_aux) {
+        ISDF_CUDA_TRY(cudaEventRecord(p->ev_aux_fork, st));
+        ISDF_CUDA_TRY(cudaStreamWaitEvent(p->aux, p->ev_aux_fork, 0));
+        ISDF_TRY(mixed_prepare_orbitals(p, p->aux));
+        ISDF_CUDA_TRY(cudaEventRecord(p->ev_aux_join, p->aux));
+    }
     // a7: Phi_mu = Phi[idx], Psi_mu = Psi[idx]  (Eq. Cmu)
     timer_start(p, 2, st);
     gather_rows<<<grid_for((int64_t)n_mu * n_phi), 256, 0, st>>>(p->phi, p->ld_phi, p->dtype, n_phi, p->idx, n_mu,
@@ -299,6 +308,10 @@ isdf_status plan_compute(isdf_plan *p, const int64_t *idx, cudaStream_t st)
     ISDF_TRY(cholesky_inverse(p->M, p->L, p->Linv, p->W, p->tmp, n_mu, p->partial, p->partial_elems, p->status, st,
                               p));
     if (p->mode == ISDF_MIXED) {
+        if (fork_aux)
+            ISDF_CUDA_TRY(cudaStreamWaitEvent(st, p->ev_aux_join, 0));
+        else
+            ISDF_TRY(mixed_prepare_orbitals(p, st));
         timer_start(p, 6, st);
         ISDF_TRY(mixed_prepare(p, st));
         timer_stop(p, 6, st, p->n_r);
@@ -413,7 +426,10 @@ extern "C" isdf_status isdf_plan_create(isdf_plan **plan, const void *phi, int64
 #undef PLAN_ALLOC
     if (cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_aux_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_aux_join, cudaEventDisableTiming) != cudaSuccess) {
         isdf_plan_destroy(p);
         return ISDF_ERR_CUDA;
     }
@@ -736,5 +752,11 @@ extern "C" void isdf_plan_destroy(isdf_plan *p)
     }
     if (p->ev_fork) cudaEventDestroy(p->ev_fork);
     if (p->ev_join) cudaEventDestroy(p->ev_join);
+    if (p->aux) {
+        cudaStreamSynchronize(p->aux);
+        cudaStreamDestroy(p->aux);
+    }
+    if (p->ev_aux_fork) cudaEventDestroy(p->ev_aux_fork);
+    if (p->ev_aux_join) cudaEventDestroy(p->ev_aux_join);
     free(p);
 }

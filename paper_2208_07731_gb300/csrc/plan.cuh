@@ -30,6 +30,8 @@ struct isdf_plan {
     int *oz_err;                              // device flag: a bounded wait of that kernel gave up
     cudaStream_t side;                        // look-ahead stream of the Cholesky factorisation
     cudaEvent_t ev_fork, ev_join;             // its fork / join points
+    cudaStream_t aux;                         // orbital operand preparation, concurrent with a8-a9
+    cudaEvent_t ev_aux_fork, ev_aux_join;
     // optional event timing: kinds 0 Gram kernel, 1 M^-1 application kernel,
     // 2 gather + M, 3 Cholesky factor, 4 triangular inverse, 5 M^-1 = L^-H L^-1,
     // 6 tensor-core operand preparation
