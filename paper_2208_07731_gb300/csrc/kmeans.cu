@@ -150,19 +150,6 @@ __device__ double block_sum(double v, double *red)
     return s;  // valid in thread 0
 }
 
-__device__ unsigned long long block_sum_u64(unsigned long long v, unsigned long long *red)
-{
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) red[wid] = v;
-    __syncthreads();
-    unsigned long long s = 0;
-    if (threadIdx.x == 0)
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
-    return s;
-}
-
 __global__ void km_init(KmArgs a, const int64_t *__restrict__ init_idx, int64_t n_r)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -288,6 +275,7 @@ __global__ void __launch_bounds__(kThreads, 1) km_assign(KmArgs a, int t)
     __shared__ float minub_sh[kThreads / 32];
     __shared__ double red[kThreads / 32];
     __shared__ unsigned long long redu[kThreads / 32];
+    __shared__ unsigned long long redu2[kThreads / 32];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int b = blockIdx.x;
@@ -494,14 +482,33 @@ __global__ void __launch_bounds__(kThreads, 1) km_assign(KmArgs a, int t)
         }
         if (!FINAL) warp_accumulate(key, v, slot, a.acc, cand, lane);
     }
-    const double jt = block_sum(jv, red);
-    if (tid == 0) a.jpart[b] = jt;
-    const unsigned long long tt = block_sum_u64(my_ties, redu);
-    if (tid == 0 && tt) atomicAdd(&a.ctl->ties, tt);
-    const unsigned long long rr = block_sum_u64(my_ref, redu);
-    if (tid == 0 && rr) atomicAdd(&a.ctl->refined, rr);
+    // the objective partial (fixed shuffle pattern and warp order: deterministic) and the two
+    // counts, reduced together with one barrier, which also completes the shared slots
+    const bool want_j = FINAL || a.want_obj;
+    for (int o = 16; o > 0; o >>= 1) {
+        if (want_j) jv = __dadd_rn(jv, __shfl_down_sync(0xffffffffu, jv, o));
+        my_ties += __shfl_down_sync(0xffffffffu, my_ties, o);
+        my_ref += __shfl_down_sync(0xffffffffu, my_ref, o);
+    }
+    if (lane == 0) {
+        red[warp] = jv;
+        redu[warp] = my_ties;
+        redu2[warp] = my_ref;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double jt = 0.0;
+        unsigned long long tt = 0ull, rr = 0ull;
+        for (int i = 0; i < kThreads / 32; ++i) {
+            jt = __dadd_rn(jt, red[i]);
+            tt += redu[i];
+            rr += redu2[i];
+        }
+        if (want_j) a.jpart[b] = jt;
+        if (tt) atomicAdd(&a.ctl->ties, tt);
+        if (rr) atomicAdd(&a.ctl->refined, rr);
+    }
     if (!FINAL) {
-        __syncthreads();
         for (int j = tid; j < ns; j += kThreads) {
             unsigned long long *src = &slot[j][0];
             if ((src[0] | src[1]) == 0ull) continue;
