@@ -17,5 +17,5 @@ invariances and finite differences. No function is parity-unpinned.
 from .oracle import (  # noqa: F401
     load, weights, kmeans, fixed_point_scale, gather, form_M, cholesky, gram_hadamard,
     theta_rows, fit_theta, surrogate_loss, surrogate_grad_theta, theta_backward,
-    grid_coords, explicit_Z,
+    grid_coords, explicit_Z, isdf_error, cluster_residual,
 )

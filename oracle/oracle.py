@@ -226,3 +226,42 @@ def explicit_Z(phi, psi) -> np.ndarray:
     (the transposed Khatri-Rao product, Sec. 1). Small inputs only."""
     phi, psi = _c128(phi), _c128(psi)
     return (phi[:, :, None] * psi.conj()[:, None, :]).reshape(phi.shape[0], -1)
+
+
+# --------------------------------------------------------------------------
+# Diagnostics of the decomposition (Appendix A).
+def isdf_error(phi, psi, idx, block: int = 65536) -> dict:
+    """||Z - Theta C||_F^2 and ||Z||_F^2 without forming Z: Theta solves the least-squares
+    problem min ||Z - Theta C|| (Eq. theta), so ||Z - Theta C||^2 = ||Z||^2 - Re tr(Theta^H Y)
+    with Y = Z C^H (Eq. muRownuCol), and ||Z(r)||^2 = (sum_i |phi_i(r)|^2)(sum_j |psi_j(r)|^2)
+    (Eq. Zmu). Returns z2, trace, the squared residual and the relative error."""
+    phi, psi = _c128(phi), _c128(psi)
+    phi_mu, psi_mu = gather(phi, psi, idx)
+    L = cholesky(form_M(phi_mu, psi_mu))
+    z2 = float(np.sum(np.sum(np.abs(phi) ** 2, 1) * np.sum(np.abs(psi) ** 2, 1)))
+    tr = 0.0
+    for b in range(0, phi.shape[0], block):
+        rows = np.arange(b, min(phi.shape[0], b + block))
+        Y = gram_hadamard(phi[rows], psi[rows], phi_mu, psi_mu)
+        T = theta_rows(phi, psi, phi_mu, psi_mu, L, rows)
+        tr += float(np.real(np.sum(T.conj() * Y)))
+    res2 = max(z2 - tr, 0.0)
+    return {"z2": z2, "trace": tr, "residual2": res2, "error": float(np.sqrt(res2 / z2))}
+
+
+def cluster_residual(phi, psi, labels, idx) -> dict:
+    """R of Eq. errorISDF: every row Z(r) of cluster mu projected on the row Z(r_mu) of its
+    selected point (Eq. proj), summed squared distances, written with Eq. Zmu:
+    R = sum_r [p(r) q(r) - |a(r)|^2 |b(r)|^2 / (p(r_mu) q(r_mu))], p = sum_i |phi_i|^2,
+    q = sum_j |psi_j|^2, a(r) = Phi(r) . Phi*(r_mu), b(r) = Psi(r) . Psi*(r_mu).
+    Returns R and z2 = ||Z||_F^2."""
+    phi, psi = _c128(phi), _c128(psi)
+    labels = np.asarray(labels, dtype=np.int64)
+    idx = np.asarray(idx, dtype=np.int64)
+    p = np.sum(np.abs(phi) ** 2, 1)
+    q = np.sum(np.abs(psi) ** 2, 1)
+    s = idx[labels]
+    a = np.sum(phi * phi[s].conj(), 1)
+    b = np.sum(psi * psi[s].conj(), 1)
+    R = float(np.sum(p * q - (np.abs(a) ** 2) * (np.abs(b) ** 2) / (p[s] * q[s])))
+    return {"R": R, "z2": float(np.sum(p * q))}
