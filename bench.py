@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-graph", action="store_true", help="launch every kernel from the host instead of "
                     "replaying one captured CUDA graph per step")
+    ap.add_argument("--study", choices=["weights"], default=None,
+                    help="instead of timing: the weight-function accuracy study (Appendix A diagnostics)")
     return ap.parse_args()
 
 
@@ -237,6 +239,55 @@ def run_adjoint(args):
             "fp64": {"value": 1e3 / b["ms"], "ms_per_step": b["ms"], "steps": b["steps"]},
             "grad_rel_diff_mixed_vs_fp64": rel, "loss": {"mixed": a["loss"], "fp64": b["loss"]}}
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_study(args):
+    """Weight-function study (Sec. 2.2, Appendix A): for SSM with alpha = 1..4, PSM and uniformly
+    random points, the K-means interpolation points' fit error ||Z - Theta C||_F / ||Z||_F (FP64
+    plan), the cluster residual R of Eq. errorISDF relative to ||Z||_F^2, and how delocalised the
+    points are (mean density at the points over the grid's mean density). All on the GPU path."""
+    import numpy as np
+    import torch
+
+    from paper_2208_07731_gb300 import build
+    build.build()
+    import paper_2208_07731_gb300 as isdf
+    from paper_2208_07731_gb300 import workload as W
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    w = W.WORKLOADS[args.workload]
+    phi, psi = W.make_pair(w, device=dev)
+    phi, psi = W.storage(phi, w).contiguous(), W.storage(psi, w).contiguous()
+    shape, cell = (w.n,) * 3, (w.L,) * 3
+    rho = isdf.weights(phi, psi, "ssm", 2.0)          # |phi|^2 + |psi|^2 summed: twice the density
+    rho_mean = float(rho.mean())
+    rows = []
+    for name, kind, alpha in [("ssm_a2", "ssm", 2.0), ("ssm_a1", "ssm", 1.0), ("ssm_a3", "ssm", 3.0),
+                              ("ssm_a4", "ssm", 4.0), ("psm", "psm", 2.0), ("uniform_random", None, None)]:
+        t0 = time.perf_counter()
+        if kind is None:
+            idx = torch.from_numpy(W.init_indices(np.ones(w.n_r), w.n_mu, 1000 + w.seed)).to(dev)
+            labels = None
+        else:
+            wt = isdf.weights(phi, psi, kind, alpha)
+            init = torch.from_numpy(W.init_indices(wt.cpu().numpy(), w.n_mu, 1000 + w.seed)).to(dev)
+            km = isdf.kmeans(wt, shape, cell, w.n_mu, init, w.iters, early_stop=True)
+            idx, labels = km["idx"], km["labels"]
+        plan = isdf.Plan(phi, psi, idx, mode="fp64", max_rows=min(w.n_r, 131072))
+        fe = plan.fit_error()
+        plan.check()
+        plan.close()
+        row = {"points": name, "fit_error_rel": fe["error"],
+               "rho_at_points_rel": float(rho[idx].mean()) / rho_mean}
+        if labels is not None:
+            cr = isdf.cluster_residual(phi, psi, labels, idx)
+            row["cluster_residual_rel"] = cr["R"] / cr["z2"]
+        torch.cuda.synchronize()
+        row["seconds"] = time.perf_counter() - t0
+        rows.append(row)
+    print(json.dumps({"study": "weights", "workload": w.name, "grid": f"{w.n}^3", "n_orb": w.n_orb,
+                      "n_mu": w.n_mu, "kmeans_iters": w.iters, "theta": "FP64 plan", "rows": rows}), flush=True)
     return 0
 
 
@@ -528,6 +579,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.study == "weights":
+        return run_study(args)
     if args.workload == "adjoint":
         return run_adjoint(args)
     return run_ours(args)

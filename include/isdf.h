@@ -231,6 +231,43 @@ ISDF_API isdf_status isdf_fit_theta_backward_finalize(isdf_plan *plan, void *gra
  * sizes do not. */
 ISDF_API isdf_status isdf_plan_update(isdf_plan *plan, const int64_t *idx, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Decomposition diagnostics (Appendix A).
+ *
+ * isdf_fit_error: the least-squares residual of the ISDF fit over grid rows
+ * [row_begin, row_begin + row_count), with Z(r) = [phi_i(r) conj(psi_j(r))]
+ * and C = Z[idx]:  ||Z - Theta C||_F^2 = ||Z||_F^2 - Re tr(Theta^H Y), since
+ * Theta C C^H = Z C^H = Y at the fitted Theta.  ||Z(r)||^2 =
+ * (sum_i |phi_i(r)|^2)(sum_j |psi_j(r)|^2) (the factorisation of Eq. Zmu at
+ * any r), so Z is never formed.
+ * sums: device array of 2 doubles, ACCUMULATED into (the caller zeroes it):
+ * sums[0] += ||Z_b||_F^2, sums[1] += Re tr(Theta_b^H Y_b).  The residual is
+ * sums[0] - sums[1]; the relative error sqrt(1 - sums[1] / sums[0]).
+ * ISDF_FP64 plans only (ISDF_ERR_UNSUPPORTED otherwise): in ISDF_MIXED mode
+ * the difference would drown in the mixed products' rounding.  Uses the
+ * plan's block scratch; ordered on stream like isdf_fit_theta.
+ *
+ * isdf_cluster_residual: R of Eq. errorISDF, the residual of projecting every
+ * row Z(r) of cluster mu = labels[r] on the single row Z(idx[mu]) (Eq. proj).
+ * With a = Phi(r) . conj(Phi(r_mu)), b = Psi(r) . conj(Psi(r_mu)),
+ * p = |Phi(r)|^2, q = |Psi(r)|^2 (Eq. Zmu and the first lines of Eq. error2),
+ * the row's term is p q - |a|^2 |b|^2 / (p(r_mu) q(r_mu)), or p q where Z(r_mu)
+ * is zero.  phi, psi: device, row-major n_r x n_phi / n_r x n_psi with leading
+ * dimensions ld_phi >= n_phi, ld_psi >= n_psi, complex128 (ISDF_C128) or
+ * complex64 (ISDF_C64, widened to FP64).  labels: device int32[n_r] (the
+ * labels isdf_kmeans writes), idx: device int64[n_mu].  sums: device double[2],
+ * ACCUMULATED: sums[0] += ||Z||_F^2, sums[1] += R.  bad: device int32, set to 1
+ * if a label lies outside [0, n_mu) or an index outside [0, n_r); those rows
+ * are skipped.  Returns ISDF_ERR_INVALID_ARG for null or misaligned pointers
+ * and bad sizes.
+ * ------------------------------------------------------------------------- */
+ISDF_API isdf_status isdf_fit_error(isdf_plan *plan, int64_t row_begin, int64_t row_count, double *sums,
+                                    void *stream);
+ISDF_API isdf_status isdf_cluster_residual(const void *phi, int64_t ld_phi, int32_t n_phi, const void *psi,
+                                           int64_t ld_psi, int32_t n_psi, int64_t n_r, int32_t dtype,
+                                           const int32_t *labels, const int64_t *idx, int32_t n_mu, double *sums,
+                                           int32_t *bad, void *stream);
+
 /* Synchronises the plan's last stream and returns the first device-side
  * failure (ISDF_OK, ISDF_ERR_NOT_HPD with *detail = failing pivot index,
  * ISDF_ERR_NONFINITE, ISDF_ERR_TIMEOUT). detail may be NULL. */

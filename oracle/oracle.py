@@ -230,18 +230,21 @@ def explicit_Z(phi, psi) -> np.ndarray:
 
 # --------------------------------------------------------------------------
 # Diagnostics of the decomposition (Appendix A).
-def isdf_error(phi, psi, idx, block: int = 65536) -> dict:
+def isdf_error(phi, psi, idx, block: int = 65536, row_range=None) -> dict:
     """||Z - Theta C||_F^2 and ||Z||_F^2 without forming Z: Theta solves the least-squares
     problem min ||Z - Theta C|| (Eq. theta), so ||Z - Theta C||^2 = ||Z||^2 - Re tr(Theta^H Y)
     with Y = Z C^H (Eq. muRownuCol), and ||Z(r)||^2 = (sum_i |phi_i(r)|^2)(sum_j |psi_j(r)|^2)
-    (Eq. Zmu). Returns z2, trace, the squared residual and the relative error."""
+    (Eq. Zmu). row_range = (begin, end) restricts both sums to those grid rows (C still
+    comes from idx over the whole grid). Returns z2, trace, the squared residual and the
+    relative error."""
     phi, psi = _c128(phi), _c128(psi)
     phi_mu, psi_mu = gather(phi, psi, idx)
     L = cholesky(form_M(phi_mu, psi_mu))
-    z2 = float(np.sum(np.sum(np.abs(phi) ** 2, 1) * np.sum(np.abs(psi) ** 2, 1)))
+    r0, r1 = (0, phi.shape[0]) if row_range is None else (int(row_range[0]), int(row_range[1]))
+    z2 = float(np.sum(np.sum(np.abs(phi[r0:r1]) ** 2, 1) * np.sum(np.abs(psi[r0:r1]) ** 2, 1)))
     tr = 0.0
-    for b in range(0, phi.shape[0], block):
-        rows = np.arange(b, min(phi.shape[0], b + block))
+    for b in range(r0, r1, block):
+        rows = np.arange(b, min(r1, b + block))
         Y = gram_hadamard(phi[rows], psi[rows], phi_mu, psi_mu)
         T = theta_rows(phi, psi, phi_mu, psi_mu, L, rows)
         tr += float(np.real(np.sum(T.conj() * Y)))

@@ -61,6 +61,8 @@ def lib():
         L.isdf_plan_status.argtypes = [P, P]
         L.isdf_plan_copy_matrix.argtypes = [P, I32, P, P]
         L.isdf_plan_update.argtypes = [P, P, P]
+        L.isdf_fit_error.argtypes = [P, I64, I64, P, P]
+        L.isdf_cluster_residual.argtypes = [P, I64, I32, P, I64, I32, I64, I32, P, P, I32, P, P, P]
         L.isdf_plan_enable_timing.argtypes = [P, I32]
         L.isdf_plan_kernel_time.argtypes = [P, I32, P, P, P]
         L.isdf_kernel_launches.argtypes = []
@@ -235,6 +237,18 @@ class Plan:
                                     _stream(stream)), "isdf_fit_theta")
         return th
 
+    def fit_error(self, row_begin: int = 0, row_count: int | None = None, stream=None) -> dict:
+        """Least-squares residual of the fit (Appendix A): device scalars z2 = ||Z||_F^2,
+        trace = Re tr(Theta^H Y), and the relative error sqrt(1 - trace / z2) as a float."""
+        if row_count is None:
+            row_count = self.n_r - row_begin
+        sums = torch.zeros(2, dtype=torch.float64, device=self.phi.device)
+        _check(lib().isdf_fit_error(self._h, int(row_begin), int(row_count), _ptr(sums), _stream(stream)),
+               "isdf_fit_error")
+        z2, tr = (float(v) for v in sums.cpu())
+        return {"z2": z2, "trace": tr, "residual2": z2 - tr,
+                "error": max(0.0, 1.0 - tr / z2) ** 0.5 if z2 > 0 else 0.0}
+
     def backward(self, row_begin: int, row_count: int, grad_phi: torch.Tensor, grad_psi: torch.Tensor,
                  grad_theta: torch.Tensor | None = None, K: torch.Tensor | None = None, dV: float = 1.0,
                  loss: torch.Tensor | None = None, stream=None):
@@ -255,6 +269,28 @@ class Plan:
         _check(lib().isdf_fit_theta_backward_finalize(self._h, _ptr(grad_phi), grad_phi.stride(0), _ptr(grad_psi),
                                                       grad_psi.stride(0), _stream(stream)),
                "isdf_fit_theta_backward_finalize")
+
+
+def cluster_residual(phi: torch.Tensor, psi: torch.Tensor, labels: torch.Tensor, idx: torch.Tensor,
+                     stream=None) -> dict:
+    """R of Eq. errorISDF: every row Z(r) projected on the row of its cluster's point
+    idx[labels[r]] (Appendix A); returns {"R", "z2"} as floats."""
+    a, lda, na, ca = _orbitals(phi)
+    b, ldb, nb, cb = _orbitals(psi)
+    if ca != cb or a.shape[0] != b.shape[0]:
+        raise ValueError("phi and psi must share dtype and row count")
+    lab = labels.to(device=a.device, dtype=torch.int32).contiguous()
+    ix = idx.to(device=a.device, dtype=torch.int64).contiguous()
+    if lab.numel() != a.shape[0]:
+        raise ValueError("labels must hold one entry per grid point")
+    sums = torch.zeros(2, dtype=torch.float64, device=a.device)
+    bad = torch.zeros(1, dtype=torch.int32, device=a.device)
+    _check(lib().isdf_cluster_residual(_ptr(a), lda, na, _ptr(b), ldb, nb, a.shape[0], ca, _ptr(lab), _ptr(ix),
+                                       ix.numel(), _ptr(sums), _ptr(bad), _stream(stream)), "isdf_cluster_residual")
+    if int(bad.item()):
+        raise ValueError("labels or idx out of range")
+    z2, R = (float(v) for v in sums.cpu())
+    return {"R": R, "z2": z2}
 
 
 def kernel_launches() -> int:

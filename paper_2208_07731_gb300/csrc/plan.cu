@@ -141,6 +141,54 @@ isdf_status alloc(T **p, size_t count)
     return ISDF_OK;
 }
 
+// Decomposition error of a row block (Appendix A diagnostics): per row, ||Z(r)||^2 =
+// (sum_i |phi_i|^2)(sum_j |psi_j|^2) and Re sum_mu conj(Theta_r,mu) Y_r,mu; one warp per row,
+// accumulated into sums[0], sums[1]
+template <typename T>
+__global__ void fit_error_kernel(const T *phi, int64_t ldp, int n_phi, const T *psi, int64_t ldq, int n_psi,
+                                 const double2 *Y, const double2 *Th, int rows, int nm, double *sums)
+{
+    __shared__ double red[2][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double zs = 0.0, ts = 0.0;
+    for (int r = blockIdx.x * (blockDim.x >> 5) + warp; r < rows; r += gridDim.x * (blockDim.x >> 5)) {
+        double pp = 0.0, qq = 0.0, tt = 0.0;
+        for (int i = lane; i < n_phi; i += 32) {
+            const double2 a = cload(phi, (int64_t)r * ldp + i);
+            pp += a.x * a.x + a.y * a.y;
+        }
+        for (int j = lane; j < n_psi; j += 32) {
+            const double2 b = cload(psi, (int64_t)r * ldq + j);
+            qq += b.x * b.x + b.y * b.y;
+        }
+        for (int m = lane; m < nm; m += 32) {
+            const double2 t = Th[(int64_t)r * nm + m], y = Y[(int64_t)r * nm + m];
+            tt += t.x * y.x + t.y * y.y;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            pp += __shfl_xor_sync(0xffffffffu, pp, o);
+            qq += __shfl_xor_sync(0xffffffffu, qq, o);
+            tt += __shfl_xor_sync(0xffffffffu, tt, o);
+        }
+        zs += pp * qq;
+        ts += tt;
+    }
+    if (lane == 0) {
+        red[0][warp] = zs;
+        red[1][warp] = ts;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            a += red[0][i];
+            b += red[1][i];
+        }
+        atomicAdd(sums, a);
+        atomicAdd(sums + 1, b);
+    }
+}
+
 // Y = A o conj(B) elementwise (rows x n_mu, leading dimension n_mu)
 __global__ void hadamard_full(const double2 *A, const double2 *B, double2 *Y, int64_t total)
 {
@@ -464,6 +512,40 @@ extern "C" isdf_status isdf_fit_theta(isdf_plan *p, int64_t row_begin, int64_t r
         timer_start(p, 1, st);
         ISDF_TRY(fp64_product(p, g, st));
         timer_stop(p, 1, st, rows);
+    }
+    return ISDF_OK;
+}
+
+extern "C" isdf_status isdf_fit_error(isdf_plan *p, int64_t row_begin, int64_t row_count, double *sums,
+                                      void *stream)
+{
+    if (!p || !sums || row_begin < 0 || row_count < 0 || row_begin + row_count > p->n_r) return ISDF_ERR_INVALID_ARG;
+    if (p->mode != ISDF_FP64) return ISDF_ERR_UNSUPPORTED;
+    if (!aligned(sums, 8)) return ISDF_ERR_INVALID_ARG;
+    if (row_count == 0) return ISDF_OK;
+    cudaStream_t st = as_stream(stream);
+    p->last_stream = st;
+    const int nm = p->n_mu;
+    const size_t es = p->dtype == ISDF_C128 ? 16 : 8;
+    if (!p->blkT) ISDF_TRY(alloc(&p->blkT, (size_t)p->max_rows * nm));
+    for (int64_t r0 = row_begin; r0 < row_begin + row_count; r0 += p->max_rows) {
+        const int rows = (int)((row_begin + row_count - r0) < p->max_rows ? (row_begin + row_count - r0) : p->max_rows);
+        ISDF_TRY(gram_hadamard_fp64(p, r0, rows, p->blkY, nullptr, nullptr, st));
+        ISDF_TRY(fp64_product(p, gemm1(rows, nm, nm, opnd(p->blkY, nm, 1, 0, ZG_C128), opnd(p->W, nm, 1, 0, ZG_C128),
+                                       p->blkT, nm, ZG_C128, 1.0, 0), st));
+        const unsigned g = (unsigned)((rows + 7) / 8 < 4096 ? (rows + 7) / 8 : 4096);
+        const char *pr = static_cast<const char *>(p->phi) + r0 * p->ld_phi * es;
+        const char *qr = static_cast<const char *>(p->psi) + r0 * p->ld_psi * es;
+        if (p->dtype == ISDF_C128)
+            fit_error_kernel<double2><<<g, 256, 0, st>>>(reinterpret_cast<const double2 *>(pr), p->ld_phi, p->n_phi,
+                                                         reinterpret_cast<const double2 *>(qr), p->ld_psi, p->n_psi,
+                                                         p->blkY, p->blkT, rows, nm, sums);
+        else
+            fit_error_kernel<float2><<<g, 256, 0, st>>>(reinterpret_cast<const float2 *>(pr), p->ld_phi, p->n_phi,
+                                                        reinterpret_cast<const float2 *>(qr), p->ld_psi, p->n_psi,
+                                                        p->blkY, p->blkT, rows, nm, sums);
+        isdf_note_launch();
+        ISDF_LAUNCH_CHECK();
     }
     return ISDF_OK;
 }

@@ -75,6 +75,22 @@ def test_host_side_validation(lib):
     assert lib.isdf_plan_create(ctypes.byref(plan), dummy, 4, dummy, 4, 100, 4, 4, 0, dummy, 8, 5, 64, None) == 1
     assert lib.isdf_fit_theta(None, 0, 1, dummy, 8, None) == 1
     assert lib.isdf_plan_status(None, None) == 1
+    assert lib.isdf_fit_error(None, 0, 1, dummy, None) == 1
+    lab, ix = P(512), P(1024)
+    # cluster residual: null labels, n_psi < 1, ld < n, bad dtype, misaligned sums
+    assert lib.isdf_cluster_residual(dummy, 4, 4, dummy, 4, 4, ctypes.c_int64(10), 0, None, ix, 2, dummy, lab,
+                                     None) == 1
+    assert lib.isdf_cluster_residual(dummy, 4, 4, dummy, 4, 0, ctypes.c_int64(10), 0, lab, ix, 2, dummy, lab,
+                                     None) == 1
+    assert lib.isdf_cluster_residual(dummy, 3, 4, dummy, 4, 4, ctypes.c_int64(10), 0, lab, ix, 2, dummy, lab,
+                                     None) == 1
+    assert lib.isdf_cluster_residual(dummy, 4, 4, dummy, 4, 4, ctypes.c_int64(10), 5, lab, ix, 2, dummy, lab,
+                                     None) == 1
+    assert lib.isdf_cluster_residual(dummy, 4, 4, dummy, 4, 4, ctypes.c_int64(10), 0, lab, ix, 2, P(260), lab,
+                                     None) == 1
+    # empty grid is a no-op
+    assert lib.isdf_cluster_residual(dummy, 4, 4, dummy, 4, 4, ctypes.c_int64(0), 0, lab, ix, 2, dummy, lab,
+                                     None) == 0
 
 
 def test_oracle_builds_and_loads():
