@@ -268,3 +268,71 @@ def cluster_residual(phi, psi, labels, idx) -> dict:
     b = np.sum(psi * psi[s].conj(), 1)
     R = float(np.sum(p * q - (np.abs(a) ** 2) * (np.abs(b) ** 2) / (p[s] * q[s])))
     return {"R": R, "z2": float(np.sum(p * q))}
+
+
+# --------------------------------------------------------------------------
+# ISDF exchange application, Sec. 2.4 (Eq. v, Eq. v2, Eq. V_mu).
+# Periodic cell [0, L_x) x [0, L_y) x [0, L_z). A column f of grid samples is
+# read as the band-limited periodic function sum_G c(G) exp(i G.r) with
+# c = fftn(f) / N_r. A pair product that carries a Bloch phase exp(i q.r)
+# (orbitals at different k) is passed as its periodic part: q then only
+# enters the kernel as |G + q|, and the result is the periodic part of V.
+# --------------------------------------------------------------------------
+def kernel_hat(shape, cell, kind: str = "coulomb", omega: float = 0.0, q=(0.0, 0.0, 0.0)) -> np.ndarray:
+    """Fourier coefficients of the interaction on the FFT grid, as an (nx, ny, nz) array:
+    4 pi / |G + q|^2 for the bare Coulomb kernel 1/|r - r'| of Eq. V_mu (the G + q = 0 term
+    set to zero: the neutralising background), and 4 pi (1 - exp(-|G + q|^2 / (4 omega^2)))
+    / |G + q|^2 for the short-range erfc(omega |r - r'|) / |r - r'| kernel of screened
+    hybrid functionals (finite at zero: pi / omega^2). G = 2 pi m / L with m the signed
+    FFT frequency of each index (numpy's fftfreq order)."""
+    axes = []
+    for n, L, qa in zip(shape, cell, q):
+        m = np.fft.fftfreq(int(n), d=1.0 / int(n))          # 0, 1, ..., -1 (integers as floats)
+        axes.append(2.0 * np.pi * m / float(L) + float(qa))
+    gx, gy, gz = np.meshgrid(*axes, indexing="ij")
+    g2 = gx * gx + gy * gy + gz * gz
+    out = np.zeros_like(g2)
+    nz_ = g2 > 0.0
+    if kind == "coulomb":
+        out[nz_] = 4.0 * np.pi / g2[nz_]
+    elif kind == "erfc":
+        if omega <= 0.0:
+            raise ValueError("the erfc kernel needs omega > 0")
+        out[nz_] = -4.0 * np.pi * np.expm1(-g2[nz_] / (4.0 * omega * omega)) / g2[nz_]
+        out[~nz_] = np.pi / (omega * omega)
+    else:
+        raise ValueError(kind)
+    return out
+
+
+def poisson(zeta, shape, cell, kind: str = "coulomb", omega: float = 0.0, q=(0.0, 0.0, 0.0)) -> np.ndarray:
+    """V_mu(r) = int zeta_mu(r') v(r - r') dr' for every column mu of zeta (N_r x N_mu, grid
+    order r = (ix*ny + iy)*nz + iz), Eq. V_mu, solved in reciprocal space: V = ifftn(K^ fftn(zeta))."""
+    z = _c128(zeta)
+    nx, ny, nz = (int(v) for v in shape)
+    n_mu = z.shape[1]
+    cube = z.T.reshape(n_mu, nx, ny, nz)
+    Vh = np.fft.fftn(cube, axes=(1, 2, 3)) * kernel_hat(shape, cell, kind, omega, q)[None]
+    return np.ascontiguousarray(np.fft.ifftn(Vh, axes=(1, 2, 3)).reshape(n_mu, nx * ny * nz).T)
+
+
+def exchange_apply(phi, psi, idx, V, rows=None) -> np.ndarray:
+    """(V_X psi_j)(r) ~ -sum_mu V_mu(r) sum_i phi_i(r) phi_i*(r_mu) psi_j(r_mu), Eq. v2, for
+    grid rows `rows` (all by default): -(V o (Phi Phi_mu^H)) Psi_mu, N_rows x N_psi."""
+    phi, psi, V = _c128(phi), _c128(psi), _c128(V)
+    idx = np.asarray(idx, dtype=np.int64)
+    sel = slice(None) if rows is None else np.asarray(rows)
+    A = phi[sel] @ phi[idx].conj().T                      # sum_i phi_i(r) phi_i*(r_mu)
+    return -(V[sel] * A) @ psi[idx]
+
+
+def exchange_direct(phi, psi, shape, cell, kind: str = "coulomb", omega: float = 0.0,
+                    q=(0.0, 0.0, 0.0)) -> np.ndarray:
+    """(V_X psi_j)(r) = -sum_i phi_i(r) int phi_i*(r') psi_j(r') v(r - r') dr', Eq. v, with one
+    Poisson solve per pair (i, j): N_phi N_psi solves, for small cases only."""
+    phi, psi = _c128(phi), _c128(psi)
+    out = np.zeros((phi.shape[0], psi.shape[1]), dtype=np.complex128)
+    for i in range(phi.shape[1]):
+        pair = phi[:, i].conj()[:, None] * psi                  # phi_i*(r') psi_j(r'), all j
+        out -= phi[:, i][:, None] * poisson(pair, shape, cell, kind, omega, q)
+    return out
