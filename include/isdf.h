@@ -263,6 +263,62 @@ ISDF_API isdf_status isdf_plan_update(isdf_plan *plan, const int64_t *idx, void 
  * ------------------------------------------------------------------------- */
 ISDF_API isdf_status isdf_fit_error(isdf_plan *plan, int64_t row_begin, int64_t row_count, double *sums,
                                     void *stream);
+
+/* ---------------------------------------------------------------------------
+ * ISDF exchange application (Sec. 2.4, Eq. v2 and Eq. V_mu).
+ *
+ * Step A, isdf_exchange_potential: V_mu(r) = int zeta_mu(r') v(r - r') dr' for
+ * every column mu of Theta (the interpolation vectors), on the periodic grid
+ * of the K-means (r = (ix*ny + iy)*nz + iz, orthorhombic cell of edges
+ * cell[0..2]).  A column is read as the band-limited periodic function
+ * sum_G c(G) exp(i G.r), c = (1/N_r) sum_r f(r) exp(-i G.r), and
+ *     V = sum_G K(G + q) c(G) exp(i G.r),  G = 2 pi m / L,
+ * m the signed frequency of the index (n/2 of an even axis reads as -n/2), with
+ *     ISDF_KERNEL_COULOMB: K = 4 pi / |G+q|^2, zero where G + q = 0
+ *                          (the interaction 1/|r - r'| of Eq. v);
+ *     ISDF_KERNEL_ERFC:    K = 4 pi (1 - exp(-|G+q|^2 / (4 omega^2))) / |G+q|^2,
+ *                          pi / omega^2 at zero (erfc(omega |r-r'|) / |r-r'|,
+ *                          the short-range exchange of screened hybrids).
+ * q (3 doubles, or NULL for zero) shifts the reciprocal vectors for pair
+ * products with a Bloch phase exp(i q.r); the data are their periodic parts.
+ * theta, v: n_r x n_mu row-major, leading dimensions >= n_mu, complex128 in
+ * ISDF_FP64 mode (FP64 FFT) and complex64 in ISDF_MIXED mode (FP32 FFT).
+ * v may equal theta (in place); otherwise theta is only read.
+ * For the exchange, Theta must interpolate the pair products phi_i*(r) psi_j(r)
+ * of Eq. v2: with isdf_plan_create that is the pair passed as (Psi, Phi).
+ *
+ * Step B, isdf_exchange_apply: rows [row_begin, row_begin + row_count) of
+ *     out(r, j) = -sum_mu V_mu(r) sum_i phi_i(r) phi_i*(r_mu) psi_j(r_mu)
+ *               = -[(V o (Phi Phi_mu^H)) Psi_mu](r, j),   r_mu = grid point idx[mu].
+ * phi, psi: n_r x n_phi / n_r x n_psi (orb_dtype), idx: device int64[n_mu],
+ * v: as written by step A, out: row_count x n_psi complex128 (device,
+ * leading dimension ld_out >= n_psi, row 0 = grid row row_begin). Both
+ * products run on the tensor cores by exact integer slicing with FP64-grade
+ * results in both modes; rows are processed in blocks of max_rows.
+ *
+ * isdf_exchange_create sizes and allocates every buffer (cudaMalloc; about
+ * max_rows * (n_mu * 16 + 28 * max(n_mu, n_phi) * 2) bytes) and computes the
+ * FFT twiddles; nothing is allocated later.  Axis lengths must be products of
+ * 2, 3 and 5 and at most 256 (else ISDF_ERR_UNSUPPORTED); n_mu <= 8192,
+ * n_phi, n_psi <= 4096.  isdf_exchange_status reports (synchronously) a bounded
+ * device wait that gave up (ISDF_ERR_TIMEOUT) or an index of idx outside
+ * [0, n_r) (ISDF_ERR_INVALID_ARG; those rows of Phi_mu, Psi_mu were zero).
+ * ------------------------------------------------------------------------- */
+typedef enum { ISDF_KERNEL_COULOMB = 0, ISDF_KERNEL_ERFC = 1 } isdf_kernel;
+typedef struct isdf_exchange isdf_exchange;
+
+ISDF_API isdf_status isdf_exchange_create(isdf_exchange **ex, int32_t nx, int32_t ny, int32_t nz, const double *cell,
+                                          int32_t n_mu, int32_t n_phi, int32_t n_psi, int32_t orb_dtype,
+                                          int32_t mode, int32_t kernel, double omega, const double *q,
+                                          int64_t max_rows, void *stream);
+ISDF_API isdf_status isdf_exchange_potential(isdf_exchange *ex, const void *theta, int64_t ld_theta, void *v,
+                                             int64_t ld_v, void *stream);
+ISDF_API isdf_status isdf_exchange_apply(isdf_exchange *ex, const void *phi, int64_t ld_phi, const void *psi,
+                                         int64_t ld_psi, const int64_t *idx, const void *v, int64_t ld_v,
+                                         int64_t row_begin, int64_t row_count, void *out, int64_t ld_out,
+                                         void *stream);
+ISDF_API isdf_status isdf_exchange_status(isdf_exchange *ex);
+ISDF_API void isdf_exchange_destroy(isdf_exchange *ex);
 ISDF_API isdf_status isdf_cluster_residual(const void *phi, int64_t ld_phi, int32_t n_phi, const void *psi,
                                            int64_t ld_psi, int32_t n_psi, int64_t n_r, int32_t dtype,
                                            const int32_t *labels, const int64_t *idx, int32_t n_mu, double *sums,

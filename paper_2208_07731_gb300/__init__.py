@@ -63,6 +63,12 @@ def lib():
         L.isdf_plan_update.argtypes = [P, P, P]
         L.isdf_fit_error.argtypes = [P, I64, I64, P, P]
         L.isdf_cluster_residual.argtypes = [P, I64, I32, P, I64, I32, I64, I32, P, P, I32, P, P, P]
+        L.isdf_exchange_create.argtypes = [P, I32, I32, I32, P, I32, I32, I32, I32, I32, I32, D, P, I64, P]
+        L.isdf_exchange_potential.argtypes = [P, P, I64, P, I64, P]
+        L.isdf_exchange_apply.argtypes = [P, P, I64, P, I64, P, P, I64, I64, I64, P, I64, P]
+        L.isdf_exchange_status.argtypes = [P]
+        L.isdf_exchange_destroy.argtypes = [P]
+        L.isdf_exchange_destroy.restype = None
         L.isdf_plan_enable_timing.argtypes = [P, I32]
         L.isdf_plan_kernel_time.argtypes = [P, I32, P, P, P]
         L.isdf_kernel_launches.argtypes = []
@@ -72,7 +78,9 @@ def lib():
         L.isdf_status_string.restype = ctypes.c_char_p
         for f in ("isdf_weights", "isdf_kmeans_workspace", "isdf_kmeans", "isdf_plan_create", "isdf_fit_theta",
                   "isdf_fit_theta_backward", "isdf_fit_theta_backward_finalize", "isdf_plan_status",
-                  "isdf_plan_copy_matrix", "isdf_plan_update", "isdf_plan_enable_timing", "isdf_plan_kernel_time"):
+                  "isdf_plan_copy_matrix", "isdf_plan_update", "isdf_plan_enable_timing", "isdf_plan_kernel_time",
+                  "isdf_fit_error", "isdf_cluster_residual", "isdf_exchange_create", "isdf_exchange_potential",
+                  "isdf_exchange_apply", "isdf_exchange_status"):
             getattr(L, f).restype = ctypes.c_int32
         _lib = L
     return _lib
@@ -291,6 +299,80 @@ def cluster_residual(phi: torch.Tensor, psi: torch.Tensor, labels: torch.Tensor,
         raise ValueError("labels or idx out of range")
     z2, R = (float(v) for v in sums.cpu())
     return {"R": R, "z2": z2}
+
+
+class Exchange:
+    """ISDF exchange application (Sec. 2.4, isdf_exchange_*): potential() solves the periodic
+    Poisson problems V_mu = v * zeta_mu (Eq. V_mu) for all columns of Theta by FFT, apply()
+    forms (V_X psi_j)(r) = -[(V o (Phi Phi_mu^H)) Psi_mu](r, j) (Eq. v2). kernel is "coulomb"
+    (1/r) or "erfc" (erfc(omega r)/r). Theta must interpolate phi_i* psi_j, i.e. come from a
+    Plan built on the pair (Psi, Phi)."""
+
+    KERNELS = {"coulomb": 0, "erfc": 1}
+
+    def __init__(self, shape, cell, n_mu: int, n_phi: int, n_psi: int, orb_dtype=torch.complex128,
+                 mode: str = "fp64", kernel: str = "coulomb", omega: float = 0.0, q=None,
+                 max_rows: int = 65536, device=None, stream=None):
+        nx, ny, nz = (int(v) for v in shape)
+        self.shape, self.n_r = (nx, ny, nz), nx * ny * nz
+        self.n_mu, self.n_phi, self.n_psi = int(n_mu), int(n_phi), int(n_psi)
+        self.mode = MIXED if mode == "mixed" else FP64
+        self.v_dtype = torch.complex64 if self.mode == MIXED else torch.complex128
+        self.orb_dtype = orb_dtype
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        cellh = (ctypes.c_double * 3)(*[float(c) for c in cell])
+        qh = (ctypes.c_double * 3)(*[float(c) for c in q]) if q is not None else None
+        self._h = ctypes.c_void_p(0)
+        with torch.cuda.device(self.device):
+            _check(lib().isdf_exchange_create(ctypes.byref(self._h), nx, ny, nz, cellh, self.n_mu, self.n_phi,
+                                              self.n_psi, C64 if orb_dtype == torch.complex64 else C128, self.mode,
+                                              self.KERNELS[kernel], float(omega), qh, int(max_rows),
+                                              _stream(stream)), "isdf_exchange_create")
+
+    def close(self):
+        if self._h and self._h.value:
+            lib().isdf_exchange_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self):
+        rc = lib().isdf_exchange_status(self._h)
+        if rc != 0:
+            raise ISDFError(rc, "isdf_exchange_status")
+
+    def potential(self, theta: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """V (n_r x n_mu, the dtype of the mode); out may be theta itself (in place)."""
+        if theta.dtype != self.v_dtype or theta.stride(1) != 1 or tuple(theta.shape) != (self.n_r, self.n_mu):
+            raise ValueError("theta must be n_r x n_mu with contiguous rows in the mode's dtype")
+        v = out if out is not None else torch.empty_like(theta)
+        if v.dtype != self.v_dtype or v.stride(1) != 1:
+            raise ValueError("output has the wrong dtype or layout")
+        _check(lib().isdf_exchange_potential(self._h, _ptr(theta), theta.stride(0), _ptr(v), v.stride(0),
+                                             _stream(stream)), "isdf_exchange_potential")
+        return v
+
+    def apply(self, phi: torch.Tensor, psi: torch.Tensor, idx: torch.Tensor, v: torch.Tensor,
+              row_begin: int = 0, row_count: int | None = None, out=None, stream=None) -> torch.Tensor:
+        """(V_X psi_j)(r) for rows [row_begin, row_begin + row_count), complex128."""
+        a, lda, _, ca = _orbitals(phi)
+        b, ldb, _, cb = _orbitals(psi)
+        if row_count is None:
+            row_count = self.n_r - row_begin
+        if a.dtype != self.orb_dtype or b.dtype != self.orb_dtype:
+            raise ValueError("orbitals must have the dtype the exchange was created for")
+        ix = idx.to(device=a.device, dtype=torch.int64).contiguous()
+        o = out if out is not None else torch.empty((row_count, self.n_psi), dtype=torch.complex128, device=a.device)
+        if v.dtype != self.v_dtype or v.stride(1) != 1 or o.dtype != torch.complex128 or o.stride(1) != 1:
+            raise ValueError("v or out has the wrong dtype or layout")
+        _check(lib().isdf_exchange_apply(self._h, _ptr(a), lda, _ptr(b), ldb, _ptr(ix), _ptr(v), v.stride(0),
+                                         int(row_begin), int(row_count), _ptr(o), o.stride(0), _stream(stream)),
+               "isdf_exchange_apply")
+        return o
 
 
 def kernel_launches() -> int:

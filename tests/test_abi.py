@@ -88,6 +88,18 @@ def test_host_side_validation(lib):
                                      None) == 1
     assert lib.isdf_cluster_residual(dummy, 4, 4, dummy, 4, 4, ctypes.c_int64(10), 0, lab, ix, 2, P(260), lab,
                                      None) == 1
+    ex = P(0)
+    cell3 = (ctypes.c_double * 3)(4.0, 4.0, 4.0)
+    # exchange: bad grid, kernel, omega, cell; axis lengths with a factor 7 or above 256 are unsupported
+    assert lib.isdf_exchange_create(ctypes.byref(ex), 0, 8, 8, cell3, 4, 2, 2, 0, 0, 0, 0.0, None, 64, None) == 1
+    assert lib.isdf_exchange_create(ctypes.byref(ex), 8, 8, 8, cell3, 4, 2, 2, 0, 0, 5, 0.0, None, 64, None) == 1
+    assert lib.isdf_exchange_create(ctypes.byref(ex), 8, 8, 8, cell3, 4, 2, 2, 0, 0, 1, 0.0, None, 64, None) == 1
+    assert lib.isdf_exchange_create(ctypes.byref(ex), 8, 8, 8, bad_cell, 4, 2, 2, 0, 0, 0, 0.0, None, 64, None) == 1
+    assert lib.isdf_exchange_create(ctypes.byref(ex), 8, 7, 8, cell3, 4, 2, 2, 0, 0, 0, 0.0, None, 64, None) == 8
+    assert lib.isdf_exchange_create(ctypes.byref(ex), 8, 512, 8, cell3, 4, 2, 2, 0, 0, 0, 0.0, None, 64, None) == 8
+    assert lib.isdf_exchange_potential(None, dummy, 4, dummy, 4, None) == 1
+    assert lib.isdf_exchange_apply(None, dummy, 4, dummy, 4, dummy, dummy, 4, 0, 1, dummy, 4, None) == 1
+    assert lib.isdf_exchange_status(None) == 1
     # empty grid is a no-op
     assert lib.isdf_cluster_residual(dummy, 4, 4, dummy, 4, 4, ctypes.c_int64(0), 0, lab, ix, 2, dummy, lab,
                                      None) == 0
