@@ -293,16 +293,21 @@ ISDF_API isdf_status isdf_fit_error(isdf_plan *plan, int64_t row_begin, int64_t 
  * phi, psi: n_r x n_phi / n_r x n_psi (orb_dtype), idx: device int64[n_mu],
  * v: as written by step A, out: row_count x n_psi complex128 (device,
  * leading dimension ld_out >= n_psi, row 0 = grid row row_begin). Both
- * products run on the tensor cores by exact integer slicing with FP64-grade
- * results in both modes; rows are processed in blocks of max_rows.
+ * products run on the tcgen05 tensor cores, in blocks of max_rows rows: in
+ * ISDF_MIXED mode, when n_phi, n_psi % 32 == 0 and n_mu % 64 == 0, as
+ * split-FP16 x3 products with FP32 accumulation (relative error ~1e-6, the
+ * Hadamard product with V fused into the first product); otherwise by exact
+ * integer slicing with FP64-grade results.
  *
  * isdf_exchange_create sizes and allocates every buffer (cudaMalloc; about
- * max_rows * (n_mu * 16 + 28 * max(n_mu, n_phi) * 2) bytes) and computes the
- * FFT twiddles; nothing is allocated later.  Axis lengths must be products of
+ * max_rows * (n_mu * 16 + 28 * max(n_mu, n_phi) * 2) bytes for the sliced
+ * products, n_r * n_phi * 8 + max_rows * n_mu * 8 for the split ones) and
+ * computes the FFT twiddles; nothing is allocated later.  Axis lengths must be products of
  * 2, 3 and 5 and at most 256 (else ISDF_ERR_UNSUPPORTED); n_mu <= 8192,
  * n_phi, n_psi <= 4096.  isdf_exchange_status reports (synchronously) a bounded
  * device wait that gave up (ISDF_ERR_TIMEOUT) or an index of idx outside
- * [0, n_r) (ISDF_ERR_INVALID_ARG; those rows of Phi_mu, Psi_mu were zero).
+ * [0, n_r) (ISDF_ERR_INVALID_ARG; those rows of Phi_mu, Psi_mu were zero),
+ * or a non-finite operand bound in the split products (ISDF_ERR_NONFINITE).
  * ------------------------------------------------------------------------- */
 typedef enum { ISDF_KERNEL_COULOMB = 0, ISDF_KERNEL_ERFC = 1 } isdf_kernel;
 typedef struct isdf_exchange isdf_exchange;

@@ -13,12 +13,16 @@
 // in natural order). Five passes over the data: forward x, forward y, then
 // forward z, multiplication by the kernel's Fourier coefficients (with the
 // 1/N_r of the inverse) and inverse z fused in one pass, inverse y, inverse x.
-// The products of the application run on the tensor cores by exact integer
-// slicing (FP64-grade results, see ozaki.cuh); V o (Phi Phi_mu^H) is formed
-// between them.
+// The products of the application run on the tcgen05 tensor cores: in
+// ISDF_MIXED mode as split-FP16 products with FP32 accumulation, the Hadamard
+// product with V fused into the first product's epilogue (mixed.cu); in
+// ISDF_FP64 mode (or for sizes the split kernels do not take) by exact
+// integer slicing with FP64-grade results (ozaki.cuh), V o (Phi Phi_mu^H)
+// formed between them.
 #include <math.h>
 
 #include "common.cuh"
+#include "mixed.cuh"
 #include "ozaki.cuh"
 #include "zgemm.cuh"
 
@@ -302,6 +306,7 @@ struct isdf_exchange {
     double2 *phi_mu, *psi_mu;   // gathered rows, complex128
     double2 *blkG;              // max_rows x n_mu
     OzWork oz;
+    MixedExchange *mixed;       // split-FP16 tensor-core products (ISDF_MIXED), or NULL
     int *flags;                 // [0]: Ozaki bounded-wait error, [1]: bad interpolation index
 };
 
@@ -426,6 +431,7 @@ void release(isdf_exchange *ex)
     cudaFree(ex->oz.ma);
     cudaFree(ex->oz.mb);
     cudaFree(ex->flags);
+    mixed_exchange_release(ex->mixed);
     delete ex;
 }
 
@@ -497,18 +503,22 @@ extern "C" isdf_status isdf_exchange_create(isdf_exchange **out, int32_t nx, int
     }
     EX_TRY(alloc(&ex->phi_mu, (size_t)n_mu * n_phi));
     EX_TRY(alloc(&ex->psi_mu, (size_t)n_mu * n_psi));
-    EX_TRY(alloc(&ex->blkG, (size_t)ex->max_rows * n_mu));
-    size_t ha1, hb1, ra1, rb1, ha2, hb2, ra2, rb2;
-    oz_sizes((int)ex->max_rows, n_mu, n_phi, 1, &ha1, &hb1, &ra1, &rb1);
-    oz_sizes((int)ex->max_rows, n_psi, n_mu, 1, &ha2, &hb2, &ra2, &rb2);
-    ex->oz.cap_a = ha1 > ha2 ? ha1 : ha2;
-    ex->oz.cap_b = hb1 > hb2 ? hb1 : hb2;
-    ex->oz.cap_ma = ra1 > ra2 ? ra1 : ra2;
-    ex->oz.cap_mb = rb1 > rb2 ? rb1 : rb2;
-    EX_TRY(alloc(&ex->oz.sa, ex->oz.cap_a));
-    EX_TRY(alloc(&ex->oz.sb, ex->oz.cap_b));
-    EX_TRY(alloc(&ex->oz.ma, ex->oz.cap_ma));
-    EX_TRY(alloc(&ex->oz.mb, ex->oz.cap_mb));
+    if (mode == ISDF_MIXED && mixed_exchange_supported(n_phi, n_psi, n_mu)) {
+        EX_TRY(mixed_exchange_create(&ex->mixed, n_r, n_phi, n_psi, n_mu, ex->max_rows));
+    } else {
+        EX_TRY(alloc(&ex->blkG, (size_t)ex->max_rows * n_mu));
+        size_t ha1, hb1, ra1, rb1, ha2, hb2, ra2, rb2;
+        oz_sizes((int)ex->max_rows, n_mu, n_phi, 1, &ha1, &hb1, &ra1, &rb1);
+        oz_sizes((int)ex->max_rows, n_psi, n_mu, 1, &ha2, &hb2, &ra2, &rb2);
+        ex->oz.cap_a = ha1 > ha2 ? ha1 : ha2;
+        ex->oz.cap_b = hb1 > hb2 ? hb1 : hb2;
+        ex->oz.cap_ma = ra1 > ra2 ? ra1 : ra2;
+        ex->oz.cap_mb = rb1 > rb2 ? rb1 : rb2;
+        EX_TRY(alloc(&ex->oz.sa, ex->oz.cap_a));
+        EX_TRY(alloc(&ex->oz.sb, ex->oz.cap_b));
+        EX_TRY(alloc(&ex->oz.ma, ex->oz.cap_ma));
+        EX_TRY(alloc(&ex->oz.mb, ex->oz.cap_mb));
+    }
     ex->oz.gsum = nullptr;
     ex->oz.cap_g = 0;
     EX_TRY(alloc(&ex->flags, 2));
@@ -562,6 +572,10 @@ extern "C" isdf_status isdf_exchange_apply(isdf_exchange *ex, const void *phi, i
     isdf_note_launch();
     isdf_note_launch();
     ISDF_LAUNCH_CHECK();
+    if (ex->mixed)
+        return mixed_exchange_apply(ex->mixed, phi, ld_phi, ex->orb_dtype, ex->phi_mu, ex->psi_mu,
+                                    static_cast<const float2 *>(v), ld_v, row_begin, row_count,
+                                    static_cast<double2 *>(out), ld_out, st);
     for (int64_t r0 = row_begin; r0 < row_begin + row_count; r0 += ex->max_rows) {
         const int rows = (int)((row_begin + row_count - r0) < ex->max_rows ? (row_begin + row_count - r0)
                                                                             : ex->max_rows);
@@ -595,6 +609,7 @@ extern "C" isdf_status isdf_exchange_status(isdf_exchange *ex)
     ISDF_CUDA_TRY(cudaMemcpy(h, ex->flags, sizeof(h), cudaMemcpyDeviceToHost));
     if (h[0]) return ISDF_ERR_TIMEOUT;
     if (h[1]) return ISDF_ERR_INVALID_ARG;
+    if (ex->mixed) return (isdf_status)mixed_exchange_error(ex->mixed);
     return ISDF_OK;
 }
 

@@ -196,7 +196,7 @@ __global__ void build_rotated(const double2 *X, int64_t ld, int nb, int n, const
     }
 }
 
-enum { OUT_C64 = 0, OUT_ADD_C128 = 1, OUT_ATOMIC_C128 = 2 };
+enum { OUT_C64 = 0, OUT_ADD_C128 = 1, OUT_ATOMIC_C128 = 2, OUT_C128 = 3, OUT_SPLIT_HV = 4 };
 
 struct EpiParams {
     // Gram-Hadamard (DUAL): split Y, and optionally P^phi, P^psi as complex64
@@ -214,6 +214,10 @@ struct EpiParams {
     int ncols;            // valid real output columns (multiple of 64)
     const MixScales *sc;
     int *err;
+    // OUT_SPLIT_HV: H = (acc * *fvh) o V written split (hi + lo FP16) to yh / yl like Y
+    const float2 *vmat;   // complex64, leading dimension ldv (complex), row 0 = the block's first row
+    int64_t ldv;
+    const float *fvh;
 };
 
 // One persistent CTA per SM walks the output tiles (row-block major, so
@@ -445,10 +449,40 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                         db[q] = make_float2(sb[(2 * q) % (DUAL ? HC : 1)] * fb, sb[(2 * q + 1) % (DUAL ? HC : 1)] * fb);
                     }
                 }
+            } else if (ep.out_mode == OUT_SPLIT_HV) {
+                // exchange: H = P o V for the next product, P = acc / s^2 carried in *fvh with H's scale
+                const float f = *ep.fvh;
+                const float2 *vr = ep.vmat + row * ep.ldv + ((n0 + half * HC) >> 1);
+#pragma unroll
+                for (int j = 0; j < HC / 32; ++j) {
+                    __half2 hv[16], lv[16];
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const float2 vv = vr[16 * j + q];
+                        const float ar = sa[32 * j + 2 * q] * f, ai = sa[32 * j + 2 * q + 1] * f;
+                        const float yr = ar * vv.x - ai * vv.y, yi = ar * vv.y + ai * vv.x;
+                        const __half2 h = __floats2half2_rn(yr, yi);
+                        const float2 hf = __half22float2(h);
+                        hv[q] = h;
+                        lv[q] = __floats2half2_rn(yr - hf.x, yi - hf.y);
+                    }
+                    uint4 *dh = reinterpret_cast<uint4 *>(ep.yh + row * ep.ldy + n0 + half * HC + 32 * j);
+                    uint4 *dl = reinterpret_cast<uint4 *>(ep.yl + row * ep.ldy + n0 + half * HC + 32 * j);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        dh[q] = reinterpret_cast<const uint4 *>(hv)[q];
+                        dl[q] = reinterpret_cast<const uint4 *>(lv)[q];
+                    }
+                }
             } else {
                 const float f = ep.alpha / ((*ep.sa) * (*ep.sb));
                 const int64_t col = (n0 + half * HC) >> 1;
-                if (ep.out_mode == OUT_C64) {
+                if (ep.out_mode == OUT_C128) {
+                    double2 *dst = static_cast<double2 *>(ep.out) + row * ep.ldo + col;
+#pragma unroll
+                    for (int q = 0; q < HC / 2; ++q)
+                        dst[q] = make_double2((double)(sa[2 * q] * f), (double)(sa[2 * q + 1] * f));
+                } else if (ep.out_mode == OUT_C64) {
                     float2 *dst = static_cast<float2 *>(ep.out) + row * ep.ldo + col;
 #pragma unroll
                     for (int q = 0; q < HC / 2; ++q) dst[q] = make_float2(sa[2 * q] * f, sa[2 * q + 1] * f);
@@ -1064,4 +1098,184 @@ void mixed_release(isdf_plan *p)
         if (x) cudaFree(x);
     free(b);
     p->mixed = nullptr;
+}
+
+
+// ---------------------------------------------------------------- exchange application (Eq. v2)
+struct MixedExchange {
+    __half *ah, *al;      // n_r x 2 N_phi split Phi
+    __half *bh, *bl;      // 2 N_mu x 2 N_phi rotated Phi_mu
+    __half *hh, *hl;      // max_rows x 2 N_mu split H = (Phi_b Phi_mu^H) o V_b
+    __half *qh, *ql;      // 2 N_psi x 2 N_mu rotated Psi_mu^H
+    unsigned int *mx;     // max |Phi|, max rho_Phi, max |V|, max |Psi_mu| (float bits)
+    float *sc;            // s_phi, s_h, s_q, f_vh = s_h / s_phi^2
+    int *err;
+    int64_t n_r, max_rows;
+    int n_phi, n_psi, n_mu;
+    CUtensorMap m_ah, m_al, m_bh, m_bl, m_hh, m_hl, m_qh, m_ql;
+};
+
+namespace {
+
+// power-of-two scales of the exchange products from the maxima (bounds with margins):
+// |Re, Im of H| <= |P| |V| <= max rho_Phi * sqrt(2) max |V| (Cauchy-Schwarz on P = Phi_b Phi_mu^H)
+__global__ void exchange_scales(const unsigned int *mx, float *sc, int *err)
+{
+    const float ma_phi = __uint_as_float(mx[0]), mr_phi = __uint_as_float(mx[1]);
+    const float ma_v = __uint_as_float(mx[2]), ma_q = __uint_as_float(mx[3]);
+    const int e_phi = scale_exp(ma_phi), e_q = scale_exp(ma_q);
+    const int e_h = scale_exp(mr_phi * ma_v * 1.4143f * 1.01f);
+    sc[0] = ldexpf(1.f, e_phi);
+    sc[1] = ldexpf(1.f, e_h);
+    sc[2] = ldexpf(1.f, e_q);
+    sc[3] = ldexpf(1.f, e_h - 2 * e_phi);
+    if (!isfinite(ma_phi) || !isfinite(mr_phi) || !isfinite(ma_v) || !isfinite(ma_q)) atomicExch(err, 2);
+}
+
+}  // namespace
+
+bool mixed_exchange_supported(int n_phi, int n_psi, int n_mu)
+{
+    return n_phi % 32 == 0 && n_phi >= 32 && n_psi % 32 == 0 && n_psi >= 32 && n_mu % 64 == 0 && n_mu >= 64;
+}
+
+isdf_status mixed_exchange_create(MixedExchange **out, int64_t n_r, int n_phi, int n_psi, int n_mu, int64_t max_rows)
+{
+    *out = nullptr;
+    MixedExchange *x = static_cast<MixedExchange *>(calloc(1, sizeof(MixedExchange)));
+    if (!x) return ISDF_ERR_CUDA;
+    x->n_r = n_r;
+    x->max_rows = max_rows;
+    x->n_phi = n_phi;
+    x->n_psi = n_psi;
+    x->n_mu = n_mu;
+    isdf_status s = ISDF_OK;
+    auto take = [&](isdf_status t) {
+        if (s == ISDF_OK) s = t;
+    };
+    take(halloc(&x->ah, (size_t)n_r * 2 * n_phi));
+    take(halloc(&x->al, (size_t)n_r * 2 * n_phi));
+    take(halloc(&x->bh, (size_t)2 * n_mu * 2 * n_phi));
+    take(halloc(&x->bl, (size_t)2 * n_mu * 2 * n_phi));
+    take(halloc(&x->hh, (size_t)max_rows * 2 * n_mu));
+    take(halloc(&x->hl, (size_t)max_rows * 2 * n_mu));
+    take(halloc(&x->qh, (size_t)2 * n_psi * 2 * n_mu));
+    take(halloc(&x->ql, (size_t)2 * n_psi * 2 * n_mu));
+    take(halloc(&x->mx, 4));
+    take(halloc(&x->sc, 4));
+    take(halloc(&x->err, 1));
+    if (s == ISDF_OK && cudaMemset(x->err, 0, sizeof(int)) != cudaSuccess) s = ISDF_ERR_CUDA;
+    if (s == ISDF_OK) {
+        bool ok = true;
+        ok &= make_map(&x->m_ah, x->ah, 2 * n_phi, n_r);
+        ok &= make_map(&x->m_al, x->al, 2 * n_phi, n_r);
+        ok &= make_map(&x->m_bh, x->bh, 2 * n_phi, 2 * n_mu);
+        ok &= make_map(&x->m_bl, x->bl, 2 * n_phi, 2 * n_mu);
+        ok &= make_map(&x->m_hh, x->hh, 2 * n_mu, max_rows);
+        ok &= make_map(&x->m_hl, x->hl, 2 * n_mu, max_rows);
+        ok &= make_map(&x->m_qh, x->qh, 2 * n_mu, 2 * n_psi);
+        ok &= make_map(&x->m_ql, x->ql, 2 * n_mu, 2 * n_psi);
+        if (!ok) s = ISDF_ERR_CUDA;
+    }
+    if (s == ISDF_OK &&
+        (cudaFuncSetAttribute(tc_gemm_persist<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) !=
+         cudaSuccess))
+        s = ISDF_ERR_CUDA;
+    if (s != ISDF_OK) {
+        mixed_exchange_release(x);
+        return s;
+    }
+    *out = x;
+    return ISDF_OK;
+}
+
+template <typename T>
+static isdf_status exchange_operands(MixedExchange *x, const T *phi, int64_t ld_phi, const double2 *phi_mu,
+                                     const double2 *psi_mu, const float2 *V, int64_t ld_v, int64_t row_begin,
+                                     int64_t row_count, cudaStream_t st)
+{
+    const int n = x->n_phi, nm = x->n_mu;
+    ISDF_CUDA_TRY(cudaMemsetAsync(x->mx, 0, 4 * sizeof(unsigned int), st));
+    // every row of Phi bounds rho(r_mu); the split covers the requested rows only
+    absmax_rows<T><<<grid_for(x->n_r * 32, 152 * 8), 256, 0, st>>>(phi, ld_phi, n, x->n_r, x->mx, x->mx + 1);
+    absmax_rows<float2><<<grid_for(row_count * 32, 152 * 8), 256, 0, st>>>(V + row_begin * ld_v, ld_v, nm,
+                                                                           row_count, x->mx + 2, nullptr);
+    absmax_rows<double2><<<grid_for((int64_t)nm * 32, 152 * 8), 256, 0, st>>>(psi_mu, x->n_psi, x->n_psi, nm,
+                                                                              x->mx + 3, nullptr);
+    exchange_scales<<<1, 1, 0, st>>>(x->mx, x->sc, x->err);
+    for (int i = 0; i < 4; ++i) isdf_note_launch();
+    split_orbitals<T><<<grid_for(row_count * n), 256, 0, st>>>(phi + row_begin * ld_phi, ld_phi, n, row_count, x->sc,
+                                                              x->ah + row_begin * 2 * n, x->al + row_begin * 2 * n);
+    build_rotated<<<grid_for((int64_t)nm * n), 256, 0, st>>>(phi_mu, n, nm, n, x->sc, x->bh, x->bl);
+    // B of the second product: rotated X = Psi_mu^H, i.e. x[mu][j] = conj(Psi_mu[mu][j]) read transposed
+    dim3 tg((nm + 31) / 32, (x->n_psi + 31) / 32);
+    split_transposed<double2, true><<<tg, 256, 0, st>>>(psi_mu, x->n_psi, nm, x->n_psi, 1, x->sc + 2, x->qh, x->ql,
+                                                         2 * (int64_t)nm);
+    for (int i = 0; i < 3; ++i) isdf_note_launch();
+    ISDF_LAUNCH_CHECK();
+    return ISDF_OK;
+}
+
+isdf_status mixed_exchange_apply(MixedExchange *x, const void *phi, int64_t ld_phi, int orb_dtype,
+                                 const double2 *phi_mu, const double2 *psi_mu, const float2 *V, int64_t ld_v,
+                                 int64_t row_begin, int64_t row_count, double2 *out, int64_t ld_out, cudaStream_t st)
+{
+    const int n = x->n_phi, nm = x->n_mu;
+    if (orb_dtype == ISDF_C128)
+        ISDF_TRY(exchange_operands<double2>(x, static_cast<const double2 *>(phi), ld_phi, phi_mu, psi_mu, V, ld_v,
+                                            row_begin, row_count, st));
+    else
+        ISDF_TRY(exchange_operands<float2>(x, static_cast<const float2 *>(phi), ld_phi, phi_mu, psi_mu, V, ld_v,
+                                           row_begin, row_count, st));
+    for (int64_t r0 = row_begin; r0 < row_begin + row_count; r0 += x->max_rows) {
+        const int rows = (int)((row_begin + row_count - r0) < x->max_rows ? (row_begin + row_count - r0) : x->max_rows);
+        // H_b = (Phi_b Phi_mu^H) o V_b, split for the next product
+        EpiParams e1{};
+        e1.out_mode = OUT_SPLIT_HV;
+        e1.yh = x->hh;
+        e1.yl = x->hl;
+        e1.ldy = 2 * nm;
+        e1.vmat = V + r0 * ld_v;
+        e1.ldv = ld_v;
+        e1.fvh = x->sc + 3;
+        e1.err = x->err;
+        e1.ksplit = 1;
+        e1.ncols = 2 * nm;
+        const int n_tiles_n = (2 * nm) / TN, m_tiles = (rows + TM - 1) / TM;
+        const int n_tiles = n_tiles_n * m_tiles;
+        const unsigned grid = (unsigned)(n_tiles < num_sms() ? n_tiles : num_sms());
+        tc_gemm_persist<false><<<grid, GEMM_THREADS, SMEM_BYTES, st>>>(x->m_ah, x->m_al, x->m_bh, x->m_bl, x->m_ah,
+                                                                       x->m_al, x->m_bh, x->m_bl, (2 * n) / TK, (int)r0,
+                                                                       rows, n_tiles_n, n_tiles, kGramSegment, e1);
+        isdf_note_launch();
+        ISDF_LAUNCH_CHECK();
+        // out_b = -H_b Psi_mu
+        EpiParams e2{};
+        e2.out_mode = OUT_C128;
+        e2.out = out + (r0 - row_begin) * ld_out;
+        e2.ldo = ld_out;
+        e2.sa = x->sc + 1;
+        e2.sb = x->sc + 2;
+        e2.alpha = -1.f;
+        e2.err = x->err;
+        e2.ksplit = 1;
+        ISDF_TRY(run_gemm(x->m_hh, x->m_hl, x->m_qh, x->m_ql, (2 * nm) / TK, rows, 2 * x->n_psi, e2, st));
+    }
+    return ISDF_OK;
+}
+
+int mixed_exchange_error(MixedExchange *x)
+{
+    int h = 0;
+    if (cudaMemcpy(&h, x->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return ISDF_ERR_CUDA;
+    return h == 1 ? ISDF_ERR_TIMEOUT : (h == 2 ? ISDF_ERR_NONFINITE : 0);
+}
+
+void mixed_exchange_release(MixedExchange *x)
+{
+    if (!x) return;
+    void *bufs[] = {x->ah, x->al, x->bh, x->bl, x->hh, x->hl, x->qh, x->ql, x->mx, x->sc, x->err};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    free(x);
 }

@@ -3,9 +3,10 @@ against the oracle on the same seeded inputs.
 
 Tolerances, from the arithmetic: the FP64 FFT carries ~log2(N_r) eps of
 relative error per column, so V agrees to 1e-12 of max |V|; the FP32 FFT of the
-mixed mode to 1e-5. The products of the application are FP64-grade in both
-modes (exact integer slicing), so the applied exchange agrees to 1e-11 of its
-Frobenius norm on identical inputs."""
+mixed mode to 1e-5. The products of the application are FP64-grade (exact
+integer slicing) in FP64 mode and for shapes the split kernels do not take, so
+the applied exchange agrees to 1e-11 of its Frobenius norm on identical inputs;
+the mixed mode's split-FP16 x3 products (2^-22 per product, FP32 sums) to 1e-5."""
 import numpy as np
 import pytest
 import torch
@@ -115,9 +116,26 @@ def test_apply_fp64_row_range(isdf):
     assert np.linalg.norm(got - ref) < 1e-11 * np.linalg.norm(ref)
 
 
-def test_apply_mixed_c64_inputs(isdf):
+def test_apply_mixed_split_products_c64(isdf):
+    # split-FP16 x3 tensor-core products (N % 32 == 0, N_mu % 64 == 0): ~2^-22 per product
     w = W.small_workload(n=24, L=10.0, n_orb=32, n_mu=256, iters=4, ecut=10.0, seed=7, dtype="c64")
-    got, phi, psi, idx, V = _apply_case(isdf, w, "mixed", 4096, 0, w.n_r, 7)
+    got, phi, psi, idx, V = _apply_case(isdf, w, "mixed", 4096, 0, w.n_r, 7)   # 4 blocks, ragged tail
+    ref = O.exchange_apply(phi, psi, idx, V)
+    assert np.linalg.norm(got - ref) < 1e-5 * np.linalg.norm(ref)
+
+
+def test_apply_mixed_split_products_row_range_c128_orbitals(isdf):
+    w = W.WORKLOADS["tiny"]
+    w = W.Workload(w.name, w.n, w.L, 32, 128, "c128", w.iters, w.ecut, w.kfrac, w.centres, 11)
+    got, phi, psi, idx, V = _apply_case(isdf, w, "mixed", 65536, 1000, 7777, 11)
+    ref = O.exchange_apply(phi, psi, idx, V, rows=np.arange(1000, 8777))
+    assert np.linalg.norm(got - ref) < 1e-5 * np.linalg.norm(ref)
+
+
+def test_apply_mixed_sliced_products_for_other_sizes(isdf):
+    # N = 20 is outside the split kernels' shapes: exact slicing, FP64-grade products
+    w = W.small_workload(n=16, L=8.0, n_orb=20, n_mu=100, iters=4, ecut=8.0, seed=12, dtype="c64")
+    got, phi, psi, idx, V = _apply_case(isdf, w, "mixed", 1500, 0, w.n_r, 12)
     ref = O.exchange_apply(phi, psi, idx, V)
     assert np.linalg.norm(got - ref) < 1e-11 * np.linalg.norm(ref)
 
