@@ -70,11 +70,14 @@ template <typename T> __device__ __forceinline__ T rot(T a, bool inv)
 
 // one Stockham stage of radix R over TM columns: input index j + r n/R, output
 // (j / Ns) Ns R + j % Ns + r Ns, twiddle exp(-+2 pi i r (j % Ns) / (Ns R))
-template <typename T, int TM, int R>
-__device__ __forceinline__ void fft_stage(const T *__restrict__ in, T *__restrict__ out, const T *tw, int n, int Ns,
-                                          bool inv)
+// (NC, NSC > 0: the length and Ns as compile-time constants, so that every index division is by a constant)
+template <typename T, int TM, int R, int NC = 0, int NSC = 0>
+__device__ __forceinline__ void fft_stage(const T *__restrict__ in, T *__restrict__ out, const T *tw, int n_rt,
+                                          int Ns_rt, bool inv)
 {
     typedef typename Real<T>::type RT;
+    const int n = NC > 0 ? NC : n_rt;
+    const int Ns = NC > 0 ? NSC : Ns_rt;
     const int nb = n / R;
     const int step = n / (Ns * R);
     for (int it = threadIdx.x; it < nb * TM; it += FFT_THREADS) {
@@ -154,6 +157,36 @@ __device__ T *fft_line(T *b0, T *b1, const T *tw, int n, const Radices &rd, bool
     return in;
 }
 
+// radix sequence of a length (4s first, then 2, 3, 5), usable in constant expressions
+struct RadPlan {
+    int count;
+    int r[FFT_MAXSTAGE];
+};
+constexpr RadPlan rad_plan(int n)
+{
+    RadPlan p{0, {}};
+    while (n % 4 == 0 && p.count < FFT_MAXSTAGE) { p.r[p.count++] = 4; n /= 4; }
+    while (n % 2 == 0 && p.count < FFT_MAXSTAGE) { p.r[p.count++] = 2; n /= 2; }
+    while (n % 3 == 0 && p.count < FFT_MAXSTAGE) { p.r[p.count++] = 3; n /= 3; }
+    while (n % 5 == 0 && p.count < FFT_MAXSTAGE) { p.r[p.count++] = 5; n /= 5; }
+    return p;
+}
+
+// all stages for a compile-time length NC, from stage S with Ns = NS; returns the result buffer
+template <typename T, int TM, int NC, int S, int NS>
+__device__ __forceinline__ T *fft_line_ct(T *in, T *out, const T *tw, bool inv)
+{
+    constexpr RadPlan P = rad_plan(NC);
+    if constexpr (S == P.count) {
+        return in;
+    } else {
+        constexpr int R = P.r[S];
+        fft_stage<T, TM, R, NC, NS>(in, out, tw, NC, NS, inv);
+        __syncthreads();
+        return fft_line_ct<T, TM, NC, S + 1, NS * R>(out, in, tw, inv);
+    }
+}
+
 // signed FFT frequency of index k on an axis of n points (the Nyquist index n/2 reads as -n/2)
 __device__ __forceinline__ int freq(int k, int n) { return k <= (n - 1) / 2 ? k : k - n; }
 
@@ -177,12 +210,14 @@ __device__ double kernel_value(const KernelParams &kp, int kx, int ky, int kz)
 // One launch: lines along one axis (points p at rows base + p * pstride, base =
 // (l / d) S1 + (l % d) S2) x tiles of TM columns. FUSED (the last axis): forward
 // FFT, multiplication by the kernel, inverse FFT.
-template <typename T, int TM, bool FUSED>
+// NC > 0: the axis length as a compile-time constant (n is then ignored).
+template <typename T, int TM, bool FUSED, int NC>
 __global__ void __launch_bounds__(FFT_THREADS) fft_lines(const T *in, int64_t ld_in, T *out, int64_t ld_out, int ncol,
-                                                         int n, int64_t pstride, int64_t lines, int64_t d, int64_t S1,
-                                                         int64_t S2, const T *tw_g, Radices rd, int inverse,
-                                                         KernelParams kp)
+                                                         int n_arg, int64_t pstride, int64_t lines, int64_t d,
+                                                         int64_t S1, int64_t S2, const T *tw_g, Radices rd,
+                                                         int inverse, KernelParams kp)
 {
+    const int n = NC > 0 ? NC : n_arg;
     typedef typename Real<T>::type RT;
     extern __shared__ __align__(16) unsigned char fft_smem[];
     T *b0 = reinterpret_cast<T *>(fft_smem);
@@ -208,7 +243,9 @@ __global__ void __launch_bounds__(FFT_THREADS) fft_lines(const T *in, int64_t ld
         b0[it] = x;
     }
     __syncthreads();
-    T *res = fft_line<T, TM>(b0, b1, tw, n, rd, FUSED ? false : inverse != 0);
+    T *res;
+    if constexpr (NC > 0) res = fft_line_ct<T, TM, NC, 0, 1>(b0, b1, tw, FUSED ? false : inverse != 0);
+    else res = fft_line<T, TM>(b0, b1, tw, n, rd, FUSED ? false : inverse != 0);
     if (FUSED) {
         for (int it = threadIdx.x; it < n * TM; it += FFT_THREADS) {
             const RT s = kv[it / TM];
@@ -217,7 +254,8 @@ __global__ void __launch_bounds__(FFT_THREADS) fft_lines(const T *in, int64_t ld
         }
         __syncthreads();
         T *other = res == b0 ? b1 : b0;
-        res = fft_line<T, TM>(res, other, tw, n, rd, true);
+        if constexpr (NC > 0) res = fft_line_ct<T, TM, NC, 0, 1>(res, other, tw, true);
+        else res = fft_line<T, TM>(res, other, tw, n, rd, true);
     }
     for (int it = threadIdx.x; it < n * TM; it += FFT_THREADS) {
         const int c = it % TM, p = it / TM;
@@ -312,27 +350,55 @@ struct isdf_exchange {
 
 namespace {
 
-template <typename T>
-isdf_status fft_attr()
+// one pass: the kernel specialised for the axis length when it is one of the common grid sizes
+template <typename T, bool FUSED, int NC>
+isdf_status launch_pass(dim3 grid, size_t smem, cudaStream_t st, const T *src, int64_t lds, T *dst, int64_t ldd,
+                        int ncol, int n, int64_t pstride, int64_t lines, int64_t d, int64_t S1, int64_t S2,
+                        const T *tw, const Radices &rd, int inverse, const KernelParams &kp)
 {
-    static bool done[64] = {false};
+    constexpr int TM = tile_cols<T>();
+    static bool attr_set[64] = {false};
     int dev = 0;
     ISDF_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 64 && done[dev]) return ISDF_OK;
-    const int bytes = (int)fft_smem_bytes<T>(FFT_NMAX);
-    ISDF_CUDA_TRY(cudaFuncSetAttribute(fft_lines<T, tile_cols<T>(), false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    ISDF_CUDA_TRY(cudaFuncSetAttribute(fft_lines<T, tile_cols<T>(), true>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    if (dev < 64) done[dev] = true;
+    if (dev >= 64 || !attr_set[dev]) {
+        ISDF_CUDA_TRY(cudaFuncSetAttribute(fft_lines<T, TM, FUSED, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)fft_smem_bytes<T>(FFT_NMAX)));
+        if (dev < 64) attr_set[dev] = true;
+    }
+    fft_lines<T, TM, FUSED, NC><<<grid, FFT_THREADS, smem, st>>>(src, lds, dst, ldd, ncol, n, pstride, lines, d, S1, S2,
+                                                                tw, rd, inverse, kp);
+    isdf_note_launch();
+    ISDF_LAUNCH_CHECK();
     return ISDF_OK;
+}
+
+template <typename T, bool FUSED>
+isdf_status dispatch_pass(dim3 grid, size_t smem, cudaStream_t st, const T *src, int64_t lds, T *dst, int64_t ldd,
+                          int ncol, int n, int64_t pstride, int64_t lines, int64_t d, int64_t S1, int64_t S2,
+                          const T *tw, const Radices &rd, int inverse, const KernelParams &kp)
+{
+#define FFT_CASE(NV)                                                                                            \
+    case NV:                                                                                                    \
+        return launch_pass<T, FUSED, NV>(grid, smem, st, src, lds, dst, ldd, ncol, n, pstride, lines, d, S1, S2, \
+                                         tw, rd, inverse, kp);
+    switch (n) {
+        FFT_CASE(24)
+        FFT_CASE(48)
+        FFT_CASE(64)
+        FFT_CASE(72)
+        FFT_CASE(96)
+        FFT_CASE(128)
+        default:
+            return launch_pass<T, FUSED, 0>(grid, smem, st, src, lds, dst, ldd, ncol, n, pstride, lines, d, S1, S2, tw,
+                                            rd, inverse, kp);
+    }
+#undef FFT_CASE
 }
 
 template <typename T>
 isdf_status potential(isdf_exchange *ex, const T *theta, int64_t ldt, T *v, int64_t ldv, cudaStream_t st)
 {
     constexpr int TM = tile_cols<T>();
-    ISDF_TRY(fft_attr<T>());
     const int nx = ex->n[0], ny = ex->n[1], nz = ex->n[2];
     KernelParams kp;
     kp.kind = ex->kind;
@@ -368,14 +434,11 @@ isdf_status potential(isdf_exchange *ex, const T *theta, int64_t ldt, T *v, int6
         const int64_t lds = s == 0 ? ldt : ldv;
         const T *tw = static_cast<const T *>(ex->tw[P.axis]);
         if (P.fused)
-            fft_lines<T, TM, true><<<grid, FFT_THREADS, smem, st>>>(src, lds, v, ldv, ex->n_mu, n, P.pstride, P.lines,
-                                                                    P.d, P.S1, P.S2, tw, ex->rd[P.axis], 0, kp);
+            ISDF_TRY((dispatch_pass<T, true>(grid, smem, st, src, lds, v, ldv, ex->n_mu, n, P.pstride, P.lines, P.d, P.S1,
+                                             P.S2, tw, ex->rd[P.axis], 0, kp)));
         else
-            fft_lines<T, TM, false><<<grid, FFT_THREADS, smem, st>>>(src, lds, v, ldv, ex->n_mu, n, P.pstride,
-                                                                     P.lines, P.d, P.S1, P.S2, tw, ex->rd[P.axis],
-                                                                     P.inverse, kp);
-        isdf_note_launch();
-        ISDF_LAUNCH_CHECK();
+            ISDF_TRY((dispatch_pass<T, false>(grid, smem, st, src, lds, v, ldv, ex->n_mu, n, P.pstride, P.lines, P.d,
+                                              P.S1, P.S2, tw, ex->rd[P.axis], P.inverse, kp)));
     }
     return ISDF_OK;
 }
