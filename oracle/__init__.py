@@ -18,5 +18,5 @@ from .oracle import (  # noqa: F401
     load, weights, kmeans, fixed_point_scale, gather, form_M, cholesky, gram_hadamard,
     theta_rows, fit_theta, surrogate_loss, surrogate_grad_theta, theta_backward,
     grid_coords, explicit_Z, isdf_error, cluster_residual,
-    kernel_hat, poisson, exchange_apply, exchange_direct,
+    kernel_hat, poisson, exchange_apply, exchange_direct, qrcp_sketch, qrcp_points,
 )

@@ -336,3 +336,35 @@ def exchange_direct(phi, psi, shape, cell, kind: str = "coulomb", omega: float =
         pair = phi[:, i].conj()[:, None] * psi                  # phi_i*(r') psi_j(r'), all j
         out -= phi[:, i][:, None] * poisson(pair, shape, cell, kind, omega, q)
     return out
+
+
+# --------------------------------------------------------------------------
+# Interpolation points by QR with column pivoting (Sec. 2.1, Eq. QRCP), the
+# accuracy comparator of the K-means selection, on a randomized sketch of Z^T.
+# --------------------------------------------------------------------------
+def qrcp_sketch(phi, psi, A, B) -> np.ndarray:
+    """S = Z G for the random matrix G whose column k is a_k (x) conj(b_k) (A: N_phi x p, B: N_psi x p):
+    S(r, k) = sum_ij phi_i(r) conj(psi_j(r)) A_ik conj(B_jk) = (Phi A)(r, k) conj((Psi B)(r, k))."""
+    phi, psi, A, B = _c128(phi), _c128(psi), _c128(A), _c128(B)
+    return (phi @ A) * np.conj(psi @ B)
+
+
+def qrcp_points(S, n_mu: int) -> dict:
+    """The first n_mu pivots of QR with column pivoting of S^T (Eq. QRCP: the columns of S^T are the grid
+    points), by greedy pivoted Gram-Schmidt: at step k the column with the largest residual norm (the first
+    one on ties) is the pivot r_k, |R_kk| its residual norm, and every residual column loses its component
+    along the normalised pivot column. Residual norms are recomputed from the residuals at every step."""
+    R = _c128(S).copy()
+    norms = np.sum(np.abs(R) ** 2, axis=1)
+    piv, rdiag = [], []
+    for _ in range(int(n_mu)):
+        j = int(np.argmax(norms))
+        nrm = float(np.sqrt(norms[j]))
+        q = R[j] / nrm
+        piv.append(j)
+        rdiag.append(nrm)
+        coef = R @ q.conj()                     # q^H s_r for every column r of S^T
+        R -= np.outer(coef, q)
+        norms = np.sum(np.abs(R) ** 2, axis=1)
+        norms[piv] = -1.0
+    return {"idx": np.array(piv, dtype=np.int64), "rdiag": np.array(rdiag)}
