@@ -245,8 +245,8 @@ def run_adjoint(args):
 
 
 def run_study(args):
-    """Weight-function study (Sec. 2.2, Appendix A): for SSM with alpha = 1..4, PSM and uniformly
-    random points, the K-means interpolation points' fit error ||Z - Theta C||_F / ||Z||_F (FP64
+    """Weight-function study (Sec. 2.2, Appendix A): for SSM with alpha = 1..4, PSM, uniformly random
+    points and randomized-QRCP points (Eq. QRCP), the interpolation points' fit error ||Z - Theta C||_F / ||Z||_F (FP64
     plan), the cluster residual R of Eq. errorISDF relative to ||Z||_F^2, and how delocalised the
     points are (mean density at the points over the grid's mean density). All on the GPU path."""
     import numpy as np
@@ -288,6 +288,22 @@ def run_study(args):
         torch.cuda.synchronize()
         row["seconds"] = time.perf_counter() - t0
         rows.append(row)
+    # the comparator of Sec. 2.1: randomized QRCP points (Eq. QRCP) on a sketch with p = N_mu + 16 columns;
+    # one FP64 pass over the sketch per point, so only where the sketch stays below ~5 GB
+    p = w.n_mu + 16
+    if w.n_r * p * 16 < 5e9:
+        t0 = time.perf_counter()
+        rng = np.random.default_rng(5000 + w.seed)
+        cr = lambda *sh: torch.from_numpy((rng.standard_normal(sh) + 1j * rng.standard_normal(sh)) / np.sqrt(2))
+        q = isdf.qrcp_points(phi, psi, cr(w.n_orb, p), cr(w.n_orb, p), w.n_mu)
+        plan = isdf.Plan(phi, psi, q["idx"], mode="fp64", max_rows=min(w.n_r, 131072))
+        fe = plan.fit_error()
+        plan.check()
+        plan.close()
+        torch.cuda.synchronize()
+        rows.append({"points": "qrcp_randomized", "fit_error_rel": fe["error"],
+                     "rho_at_points_rel": float(rho[q["idx"]].mean()) / rho_mean,
+                     "seconds": time.perf_counter() - t0})
     print(json.dumps({"study": "weights", "workload": w.name, "grid": f"{w.n}^3", "n_orb": w.n_orb,
                       "n_mu": w.n_mu, "kmeans_iters": w.iters, "theta": "FP64 plan", "rows": rows}), flush=True)
     return 0

@@ -309,6 +309,32 @@ ISDF_API isdf_status isdf_fit_error(isdf_plan *plan, int64_t row_begin, int64_t 
  * [0, n_r) (ISDF_ERR_INVALID_ARG; those rows of Phi_mu, Psi_mu were zero),
  * or a non-finite operand bound in the split products (ISDF_ERR_NONFINITE).
  * ------------------------------------------------------------------------- */
+/* ---------------------------------------------------------------------------
+ * Interpolation points by QR with column pivoting (Sec. 2.1, Eq. QRCP): the
+ * comparator of the K-means selection. Z^T (N_phi N_psi x N_r) is replaced by
+ * the randomized sketch S^T with S = Z G, column k of G = a_k (x) conj(b_k):
+ *     S(r, k) = (Phi A)(r, k) conj((Psi B)(r, k))      (FP64 products)
+ * and idx receives the first n_mu pivots of S^T's column-pivoted QR, found by
+ * greedy pivoted Gram-Schmidt in FP64 (at each step the grid point with the
+ * largest residual norm; norms compared on their top 30 mantissa bits, ties
+ * and near ties within ~1e-9 relative to the lowest grid index; residual norms
+ * recomputed, not downdated), and rdiag the |R_kk| (non-increasing).
+ * phi, psi: n_r x n_phi / n_r x n_psi (dtype, leading dims ld >= n);
+ * A: n_phi x p, B: n_psi x p, complex128 row-major (the caller's random
+ * numbers, e.g. complex Gaussian; p >= n_mu, a few more than n_mu);
+ * idx: device int64[n_mu], rdiag: device double[n_mu].
+ * Allocates n_r * p * 16 bytes (+ a row block when n_phi != n_psi) for the
+ * sketch, frees it before returning, and synchronises the stream. Cost: one
+ * pass over the sketch per point (FP64-bound). Limits: n_r < 2^22, p <= 8192.
+ * Returns ISDF_ERR_NOT_HPD when every remaining column is exactly zero before
+ * n_mu points are found (idx[k] = -1 from that step on); a numerically
+ * rank-deficient sketch shows as tiny trailing rdiag instead.
+ * ------------------------------------------------------------------------- */
+ISDF_API isdf_status isdf_qrcp_points(const void *phi, int64_t ld_phi, int32_t n_phi, const void *psi,
+                                      int64_t ld_psi, int32_t n_psi, int64_t n_r, int32_t dtype, const void *A,
+                                      const void *B, int32_t p, int32_t n_mu, int64_t *idx, double *rdiag,
+                                      void *stream);
+
 typedef enum { ISDF_KERNEL_COULOMB = 0, ISDF_KERNEL_ERFC = 1 } isdf_kernel;
 typedef struct isdf_exchange isdf_exchange;
 

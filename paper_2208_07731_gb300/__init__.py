@@ -63,6 +63,8 @@ def lib():
         L.isdf_plan_update.argtypes = [P, P, P]
         L.isdf_fit_error.argtypes = [P, I64, I64, P, P]
         L.isdf_cluster_residual.argtypes = [P, I64, I32, P, I64, I32, I64, I32, P, P, I32, P, P, P]
+        L.isdf_qrcp_points.argtypes = [P, I64, I32, P, I64, I32, I64, I32, P, P, I32, I32, P, P, P]
+        L.isdf_qrcp_points.restype = ctypes.c_int32
         L.isdf_exchange_create.argtypes = [P, I32, I32, I32, P, I32, I32, I32, I32, I32, I32, D, P, I64, P]
         L.isdf_exchange_potential.argtypes = [P, P, I64, P, I64, P]
         L.isdf_exchange_apply.argtypes = [P, P, I64, P, I64, P, P, I64, I64, I64, P, I64, P]
@@ -299,6 +301,26 @@ def cluster_residual(phi: torch.Tensor, psi: torch.Tensor, labels: torch.Tensor,
         raise ValueError("labels or idx out of range")
     z2, R = (float(v) for v in sums.cpu())
     return {"R": R, "z2": z2}
+
+
+def qrcp_points(phi: torch.Tensor, psi: torch.Tensor, A: torch.Tensor, B: torch.Tensor, n_mu: int,
+                stream=None) -> dict:
+    """Interpolation points by column-pivoted QR of the randomized sketch S^T, S = (Phi A) o conj(Psi B)
+    (Sec. 2.1, Eq. QRCP): device tensors idx (n_mu) and rdiag = |R_kk|. A: N_phi x p, B: N_psi x p."""
+    a, lda, na, ca = _orbitals(phi)
+    b, ldb, nb, cb = _orbitals(psi)
+    if ca != cb or a.shape[0] != b.shape[0]:
+        raise ValueError("phi and psi must share dtype and row count")
+    Ad = A.to(device=a.device, dtype=torch.complex128).contiguous()
+    Bd = B.to(device=a.device, dtype=torch.complex128).contiguous()
+    p = Ad.shape[1]
+    if Ad.shape[0] != na or tuple(Bd.shape) != (nb, p):
+        raise ValueError("A must be N_phi x p and B N_psi x p")
+    idx = torch.empty(int(n_mu), dtype=torch.int64, device=a.device)
+    rdiag = torch.empty(int(n_mu), dtype=torch.float64, device=a.device)
+    _check(lib().isdf_qrcp_points(_ptr(a), lda, na, _ptr(b), ldb, nb, a.shape[0], ca, _ptr(Ad), _ptr(Bd), int(p),
+                                  int(n_mu), _ptr(idx), _ptr(rdiag), _stream(stream)), "isdf_qrcp_points")
+    return {"idx": idx, "rdiag": rdiag}
 
 
 class Exchange:

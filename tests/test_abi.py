@@ -100,6 +100,11 @@ def test_host_side_validation(lib):
     assert lib.isdf_exchange_potential(None, dummy, 4, dummy, 4, None) == 1
     assert lib.isdf_exchange_apply(None, dummy, 4, dummy, 4, dummy, dummy, 4, 0, 1, dummy, 4, None) == 1
     assert lib.isdf_exchange_status(None) == 1
+    # QRCP: n_mu > p, null A, bad dtype, too many grid rows
+    assert lib.isdf_qrcp_points(dummy, 4, 4, dummy, 4, 4, 100, 0, dummy, dummy, 8, 9, ix, ix, None) == 1
+    assert lib.isdf_qrcp_points(dummy, 4, 4, dummy, 4, 4, 100, 0, None, dummy, 8, 4, ix, ix, None) == 1
+    assert lib.isdf_qrcp_points(dummy, 4, 4, dummy, 4, 4, 100, 3, dummy, dummy, 8, 4, ix, ix, None) == 1
+    assert lib.isdf_qrcp_points(dummy, 4, 4, dummy, 4, 4, 1 << 23, 0, dummy, dummy, 8, 4, ix, ix, None) == 8
     # empty grid is a no-op
     assert lib.isdf_cluster_residual(dummy, 4, 4, dummy, 4, 4, ctypes.c_int64(0), 0, lab, ix, 2, dummy, lab,
                                      None) == 0
