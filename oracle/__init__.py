@@ -19,4 +19,5 @@ from .oracle import (  # noqa: F401
     theta_rows, fit_theta, surrogate_loss, surrogate_grad_theta, theta_backward,
     grid_coords, explicit_Z, isdf_error, cluster_residual,
     kernel_hat, poisson, exchange_apply, exchange_direct, qrcp_sketch, qrcp_points,
+    shared_weights,
 )

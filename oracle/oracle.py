@@ -368,3 +368,17 @@ def qrcp_points(S, n_mu: int) -> dict:
         norms = np.sum(np.abs(R) ** 2, axis=1)
         norms[piv] = -1.0
     return {"idx": np.array(piv, dtype=np.int64), "rdiag": np.array(rdiag)}
+
+
+# --------------------------------------------------------------------------
+# Several orbital pairs on one grid (k-points or spin channels of complex
+# Bloch orbitals, Sec. 2.1): one weight shared by all pairs.
+# --------------------------------------------------------------------------
+def shared_weights(pairs, kind: str = "ssm", alpha: float = 2.0) -> np.ndarray:
+    """w(r) = sum_b w_b(r) over the pairs (phi_b, psi_b) in order b = 0, 1, ..., each w_b the weight
+    function of Sec. 2.2, summed left to right in FP64."""
+    w = None
+    for phi, psi in pairs:
+        wb = weights(phi, psi, kind, alpha)
+        w = wb.copy() if w is None else w + wb
+    return w
