@@ -60,6 +60,8 @@ typedef enum {
 
 typedef enum { ISDF_C128 = 0, ISDF_C64 = 1 } isdf_dtype;   /* interleaved complex double / float */
 typedef enum { ISDF_W_SSM = 0, ISDF_W_PSM = 1 } isdf_wkind;
+#define ISDF_W_ACCUMULATE 0x100   /* kind flag: w(r) += the pair's weight (one FP64 rounding), for a weight
+                                     shared by several orbital pairs, e.g. k-points or spin channels */
 
 /* Precision of the Theta fit.
  *  ISDF_FP64:  every step in FP64; Theta is complex128.
@@ -89,8 +91,11 @@ typedef enum { ISDF_FP64 = 0, ISDF_MIXED = 1 } isdf_mode;
  * Each sum runs over the columns in ascending order with IEEE FP64 operations,
  * |z|^2 = re*re + im*im; alpha = 1, 3, 4 use sqrt and products, other alpha pow.
  * phi, psi: dtype (ISDF_C128 or ISDF_C64) arrays of n_r rows; ld >= n.
- * w: n_r doubles (output). Requires n_r >= 0, n_phi, n_psi >= 1, alpha > 0,
- * 16-byte aligned phi, psi and 8-byte aligned w.
+ * w: n_r doubles (output; with ISDF_W_ACCUMULATE OR-ed into kind, w(r) is
+ * replaced by fl(w(r) + the pair's weight), so B calls in order b = 0..B-1
+ * after one plain call give the shared weight sum_b w_b(r) summed left to
+ * right). Requires n_r >= 0, n_phi, n_psi >= 1, alpha > 0, 16-byte aligned
+ * phi, psi and 8-byte aligned w.
  * ------------------------------------------------------------------------- */
 ISDF_API isdf_status isdf_weights(const void *phi, int64_t ld_phi, int32_t n_phi,
                          const void *psi, int64_t ld_psi, int32_t n_psi,
@@ -230,6 +235,37 @@ ISDF_API isdf_status isdf_fit_theta_backward_finalize(isdf_plan *plan, void *gra
  * of an MD loop where the orbitals and the K-means points change but the
  * sizes do not. */
 ISDF_API isdf_status isdf_plan_update(isdf_plan *plan, const int64_t *idx, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Batched decompositions: B orbital pairs on one grid (k-points or spin
+ * channels of complex Bloch orbitals, Sec. 2.1) sharing one set of
+ * interpolation points, e.g. from one isdf_kmeans on the shared weight
+ * (isdf_weights with ISDF_W_ACCUMULATE). Each pair gets its own plan (as
+ * isdf_plan_create, all with the same sizes, dtype, mode and max_rows);
+ * isdf_batch_update and isdf_batch_fit_theta run the pairs' plan updates /
+ * fits on one internal stream per pair, ordered after the work already on
+ * `stream` and before anything later on it (event fork and join, so the
+ * batch can be captured into a CUDA graph from `stream`). The pairs' results
+ * are bit-identical to B separate plans run one after another.
+ * phi, psi, ld_phi, ld_psi, theta: HOST arrays of count entries (device
+ * pointers / leading dimensions); idx: device int64[n_mu]. Each plan keeps
+ * its phi/psi pointers (they must stay valid and unchanged).
+ * isdf_batch_plan returns pair i's plan (owned by the batch) for the other
+ * plan entry points; isdf_batch_status reports the first failing pair's
+ * isdf_plan_status (which = its index, or -1) and synchronises.
+ * ------------------------------------------------------------------------- */
+typedef struct isdf_batch isdf_batch;
+
+ISDF_API isdf_status isdf_batch_create(isdf_batch **batch, int32_t count, const void *const *phi,
+                                       const int64_t *ld_phi, const void *const *psi, const int64_t *ld_psi,
+                                       int64_t n_r, int32_t n_phi, int32_t n_psi, int32_t dtype, const int64_t *idx,
+                                       int32_t n_mu, int32_t mode, int64_t max_rows, void *stream);
+ISDF_API isdf_status isdf_batch_update(isdf_batch *batch, const int64_t *idx, void *stream);
+ISDF_API isdf_status isdf_batch_fit_theta(isdf_batch *batch, int64_t row_begin, int64_t row_count,
+                                          void *const *theta, int64_t ld_theta, void *stream);
+ISDF_API isdf_plan *isdf_batch_plan(isdf_batch *batch, int32_t i);
+ISDF_API isdf_status isdf_batch_status(isdf_batch *batch, int32_t *which, int32_t *detail);
+ISDF_API void isdf_batch_destroy(isdf_batch *batch);
 
 /* ---------------------------------------------------------------------------
  * Decomposition diagnostics (Appendix A).

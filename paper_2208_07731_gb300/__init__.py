@@ -24,6 +24,7 @@ _lib = None
 
 C128, C64 = 0, 1
 SSM, PSM = 0, 1
+W_ACCUMULATE = 0x100
 FP64, MIXED = 0, 1
 PLAN_FP64_SIMT = 0x100   # mode flag: plan-update products on the FP64 pipe only
 EARLY_STOP = 1
@@ -63,6 +64,16 @@ def lib():
         L.isdf_plan_update.argtypes = [P, P, P]
         L.isdf_fit_error.argtypes = [P, I64, I64, P, P]
         L.isdf_cluster_residual.argtypes = [P, I64, I32, P, I64, I32, I64, I32, P, P, I32, P, P, P]
+        L.isdf_batch_create.argtypes = [P, I32, P, P, P, P, I64, I32, I32, I32, P, I32, I32, I64, P]
+        L.isdf_batch_update.argtypes = [P, P, P]
+        L.isdf_batch_fit_theta.argtypes = [P, I64, I64, P, I64, P]
+        L.isdf_batch_plan.argtypes = [P, I32]
+        L.isdf_batch_plan.restype = ctypes.c_void_p
+        L.isdf_batch_status.argtypes = [P, P, P]
+        L.isdf_batch_destroy.argtypes = [P]
+        L.isdf_batch_destroy.restype = None
+        for f in ("isdf_batch_create", "isdf_batch_update", "isdf_batch_fit_theta", "isdf_batch_status"):
+            getattr(L, f).restype = ctypes.c_int32
         L.isdf_qrcp_points.argtypes = [P, I64, I32, P, I64, I32, I64, I32, P, P, I32, I32, P, P, P]
         L.isdf_qrcp_points.restype = ctypes.c_int32
         L.isdf_exchange_create.argtypes = [P, I32, I32, I32, P, I32, I32, I32, I32, I32, I32, D, P, I64, P]
@@ -115,16 +126,21 @@ def _orbitals(x: torch.Tensor):
     return x, x.stride(0), x.shape[1], code
 
 
-def weights(phi: torch.Tensor, psi: torch.Tensor, kind: str = "ssm", alpha: float = 2.0, out=None, stream=None):
-    """w(r) = sum_i |phi_i|^alpha + sum_j |psi_j|^alpha (kind "ssm") or the PSM product (kind "psm")."""
+def weights(phi: torch.Tensor, psi: torch.Tensor, kind: str = "ssm", alpha: float = 2.0, out=None, stream=None,
+            accumulate: bool = False):
+    """w(r) = sum_i |phi_i|^alpha + sum_j |psi_j|^alpha (kind "ssm") or the PSM product (kind "psm");
+    accumulate=True adds the pair's weight into out (a weight shared by several pairs)."""
     a, lda, na, ca = _orbitals(phi)
     b, ldb, nb, cb = _orbitals(psi)
     if ca != cb or a.shape[0] != b.shape[0]:
         raise ValueError("phi and psi must share dtype and row count")
     n_r = a.shape[0]
+    if accumulate and out is None:
+        raise ValueError("accumulate needs the running weight as out")
     w = out if out is not None else torch.empty(n_r, dtype=torch.float64, device=a.device)
-    _check(lib().isdf_weights(_ptr(a), lda, na, _ptr(b), ldb, nb, n_r, ca, PSM if kind == "psm" else SSM,
-                              float(alpha), _ptr(w), _stream(stream)), "isdf_weights")
+    code = (PSM if kind == "psm" else SSM) | (W_ACCUMULATE if accumulate else 0)
+    _check(lib().isdf_weights(_ptr(a), lda, na, _ptr(b), ldb, nb, n_r, ca, code, float(alpha), _ptr(w),
+                              _stream(stream)), "isdf_weights")
     return w
 
 
@@ -321,6 +337,69 @@ def qrcp_points(phi: torch.Tensor, psi: torch.Tensor, A: torch.Tensor, B: torch.
     _check(lib().isdf_qrcp_points(_ptr(a), lda, na, _ptr(b), ldb, nb, a.shape[0], ca, _ptr(Ad), _ptr(Bd), int(p),
                                   int(n_mu), _ptr(idx), _ptr(rdiag), _stream(stream)), "isdf_qrcp_points")
     return {"idx": idx, "rdiag": rdiag}
+
+
+class Batch:
+    """Batched decompositions (isdf_batch_*): one plan per orbital pair on a shared grid and shared
+    interpolation points; update() and fit_theta() run the pairs on concurrent streams."""
+
+    def __init__(self, pairs, idx: torch.Tensor, mode: str = "fp64", max_rows: int = 65536, stream=None):
+        ops = [(_orbitals(p), _orbitals(q)) for p, q in pairs]
+        (a0, _, na, ca), (_, _, nb, cb) = ops[0]
+        for (a, _, n1, c1), (b, _, n2, c2) in ops:
+            if (n1, n2, c1, c2) != (na, nb, ca, cb) or a.shape[0] != a0.shape[0] or b.shape[0] != a0.shape[0]:
+                raise ValueError("every pair must share sizes and dtype")
+        self.pairs = [(a, b) for (a, _, _, _), (b, _, _, _) in ops]
+        self.count, self.n_r, self.n_mu = len(ops), a0.shape[0], idx.numel()
+        self.idx = idx.to(device=a0.device, dtype=torch.int64).contiguous()
+        self.mode = MIXED if mode == "mixed" else FP64
+        self.theta_dtype = torch.complex64 if self.mode == MIXED else torch.complex128
+        n = self.count
+        P = ctypes.c_void_p
+        self._phi = (P * n)(*[a.data_ptr() for (a, _, _, _), _ in ops])
+        self._psi = (P * n)(*[b.data_ptr() for _, (b, _, _, _) in ops])
+        self._ldp = (ctypes.c_int64 * n)(*[lda for (_, lda, _, _), _ in ops])
+        self._ldq = (ctypes.c_int64 * n)(*[ldb for _, (_, ldb, _, _) in ops])
+        self._h = P(0)
+        _check(lib().isdf_batch_create(ctypes.byref(self._h), n, self._phi, self._ldp, self._psi, self._ldq,
+                                       self.n_r, na, nb, ca, _ptr(self.idx), self.n_mu, self.mode, int(max_rows),
+                                       _stream(stream)), "isdf_batch_create")
+
+    def close(self):
+        if self._h and self._h.value:
+            lib().isdf_batch_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self):
+        which, d = ctypes.c_int32(-1), ctypes.c_int32(0)
+        rc = lib().isdf_batch_status(self._h, ctypes.byref(which), ctypes.byref(d))
+        if rc != 0:
+            raise ISDFError(rc, f"isdf_batch_status (pair {which.value})", d.value)
+
+    def update(self, idx: torch.Tensor, stream=None):
+        self.idx = idx.to(device=self.idx.device, dtype=torch.int64).contiguous()
+        _check(lib().isdf_batch_update(self._h, _ptr(self.idx), _stream(stream)), "isdf_batch_update")
+
+    def fit_theta(self, row_begin: int = 0, row_count: int | None = None, out=None, stream=None):
+        """Theta of every pair (a list of row_count x n_mu tensors)."""
+        if row_count is None:
+            row_count = self.n_r - row_begin
+        th = out if out is not None else [torch.empty((row_count, self.n_mu), dtype=self.theta_dtype,
+                                                      device=self.idx.device) for _ in range(self.count)]
+        ld = th[0].stride(0)
+        for t in th:
+            if t.dtype != self.theta_dtype or t.stride(1) != 1 or t.stride(0) != ld:
+                raise ValueError("theta outputs need the mode's dtype and one common layout")
+        ptrs = (ctypes.c_void_p * self.count)(*[t.data_ptr() for t in th])
+        _check(lib().isdf_batch_fit_theta(self._h, int(row_begin), int(row_count), ptrs, ld, _stream(stream)),
+               "isdf_batch_fit_theta")
+        return th
 
 
 class Exchange:

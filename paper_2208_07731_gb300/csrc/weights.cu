@@ -95,34 +95,37 @@ template <typename T, int AK>
 __global__ void __launch_bounds__(kRows) weights_kernel(const T *__restrict__ phi, int64_t ld_phi, int n_phi,
                                                        const T *__restrict__ psi, int64_t ld_psi, int n_psi,
                                                        int64_t n_r, int psm, double half_alpha,
-                                                       double *__restrict__ w)
+                                                       double *__restrict__ w, int acc)
 {
     __shared__ uint4 tile[kRows][kStride];
     const int64_t row0 = (int64_t)blockIdx.x * kRows;
     const double sa = row_sum<T, AK>(phi, ld_phi, n_phi, row0, n_r, half_alpha, tile);
     const double sb = row_sum<T, AK>(psi, ld_psi, n_psi, row0, n_r, half_alpha, tile);
     const int64_t row = row0 + threadIdx.x;
-    if (row < n_r) w[row] = psm ? __dmul_rn(sa, sb) : __dadd_rn(sa, sb);
+    if (row < n_r) {
+        const double v = psm ? __dmul_rn(sa, sb) : __dadd_rn(sa, sb);
+        w[row] = acc ? __dadd_rn(w[row], v) : v;   // shared weight of several pairs: one rounding per pair
+    }
 }
 
 template <typename T>
 isdf_status launch_weights(const void *phi, int64_t ld_phi, int n_phi, const void *psi, int64_t ld_psi,
-                           int n_psi, int64_t n_r, int psm, double alpha, double *w, cudaStream_t st)
+                           int n_psi, int64_t n_r, int psm, double alpha, double *w, int acc, cudaStream_t st)
 {
     const unsigned grid = (unsigned)((n_r + kRows - 1) / kRows);
     const T *a = static_cast<const T *>(phi);
     const T *b = static_cast<const T *>(psi);
     const double ha = 0.5 * alpha;
     if (psm || alpha == 2.0)
-        weights_kernel<T, 2><<<grid, kRows, 0, st>>>(a, ld_phi, n_phi, b, ld_psi, n_psi, n_r, psm, ha, w);
+        weights_kernel<T, 2><<<grid, kRows, 0, st>>>(a, ld_phi, n_phi, b, ld_psi, n_psi, n_r, psm, ha, w, acc);
     else if (alpha == 1.0)
-        weights_kernel<T, 1><<<grid, kRows, 0, st>>>(a, ld_phi, n_phi, b, ld_psi, n_psi, n_r, 0, ha, w);
+        weights_kernel<T, 1><<<grid, kRows, 0, st>>>(a, ld_phi, n_phi, b, ld_psi, n_psi, n_r, 0, ha, w, acc);
     else if (alpha == 3.0)
-        weights_kernel<T, 3><<<grid, kRows, 0, st>>>(a, ld_phi, n_phi, b, ld_psi, n_psi, n_r, 0, ha, w);
+        weights_kernel<T, 3><<<grid, kRows, 0, st>>>(a, ld_phi, n_phi, b, ld_psi, n_psi, n_r, 0, ha, w, acc);
     else if (alpha == 4.0)
-        weights_kernel<T, 4><<<grid, kRows, 0, st>>>(a, ld_phi, n_phi, b, ld_psi, n_psi, n_r, 0, ha, w);
+        weights_kernel<T, 4><<<grid, kRows, 0, st>>>(a, ld_phi, n_phi, b, ld_psi, n_psi, n_r, 0, ha, w, acc);
     else
-        weights_kernel<T, 0><<<grid, kRows, 0, st>>>(a, ld_phi, n_phi, b, ld_psi, n_psi, n_r, 0, ha, w);
+        weights_kernel<T, 0><<<grid, kRows, 0, st>>>(a, ld_phi, n_phi, b, ld_psi, n_psi, n_r, 0, ha, w, acc);
     isdf_note_launch();
     ISDF_LAUNCH_CHECK();
     return ISDF_OK;
@@ -136,6 +139,8 @@ extern "C" isdf_status isdf_weights(const void *phi, int64_t ld_phi, int32_t n_p
 {
     if (n_r < 0 || n_phi < 1 || n_psi < 1 || ld_phi < n_phi || ld_psi < n_psi) return ISDF_ERR_INVALID_ARG;
     if (dtype != ISDF_C128 && dtype != ISDF_C64) return ISDF_ERR_INVALID_ARG;
+    const int acc = (kind & ISDF_W_ACCUMULATE) ? 1 : 0;
+    kind &= ~ISDF_W_ACCUMULATE;
     if (kind != ISDF_W_SSM && kind != ISDF_W_PSM) return ISDF_ERR_INVALID_ARG;
     if (!(alpha > 0.0) || alpha > 1e6) return ISDF_ERR_INVALID_ARG;
     if (n_r == 0) return ISDF_OK;
@@ -144,8 +149,9 @@ extern "C" isdf_status isdf_weights(const void *phi, int64_t ld_phi, int32_t n_p
     if (!aligned(phi, el) || !aligned(psi, el) || !aligned(w, 8)) return ISDF_ERR_INVALID_ARG;
     cudaStream_t st = as_stream(stream);
     if (dtype == ISDF_C128)
-        return launch_weights<double2>(phi, ld_phi, n_phi, psi, ld_psi, n_psi, n_r, kind == ISDF_W_PSM, alpha, w, st);
-    return launch_weights<float2>(phi, ld_phi, n_phi, psi, ld_psi, n_psi, n_r, kind == ISDF_W_PSM, alpha, w, st);
+        return launch_weights<double2>(phi, ld_phi, n_phi, psi, ld_psi, n_psi, n_r, kind == ISDF_W_PSM, alpha, w, acc,
+                                       st);
+    return launch_weights<float2>(phi, ld_phi, n_phi, psi, ld_psi, n_psi, n_r, kind == ISDF_W_PSM, alpha, w, acc, st);
 }
 
 static unsigned long long g_launches = 0;

@@ -67,7 +67,19 @@ WORKLOADS = {
     "adjoint": Workload("adjoint", 72, 17.625, 192, 1536, "c64", 100, 20.0, (0.25, 0.25, 0.0), "none", 3),
     # large: 128^3 grid, 1024 complex64 orbitals, 4096 points, silica-like lattice of centres
     "silica": Workload("silica", 128, 30.0, 1024, 4096, "c64", 100, 20.0, (0.25, 0.25, 0.0), "lattice6", 4),
+    # 8 pairs (k-points) on one 48^3 grid with small N: the batched decompositions
+    "kpoints": Workload("kpoints", 48, 18.0, 32, 256, "c128", 100, 20.0, (0.0, 0.0, 0.0), "none", 5),
 }
+
+
+def kpoint_pairs(w: Workload, count: int, device="cpu"):
+    """`count` orbital pairs on one grid, like the k-points of one cell: pair b uses the Bloch vector
+    k_b = (b % 4, b // 4, 0) / 8 (units of 2 pi / L) and seed w.seed + 100 b; (Phi_b, Psi_b) complex128."""
+    out = []
+    for b in range(count):
+        wb = dataclasses.replace(w, kfrac=(0.125 * (b % 4), 0.125 * (b // 4), 0.0), seed=w.seed + 100 * b)
+        out.append(make_pair(wb, device))
+    return out
 
 
 def small_workload(n=8, L=6.0, n_orb=4, n_mu=16, iters=10, ecut=6.0, seed=7,

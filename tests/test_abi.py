@@ -100,6 +100,16 @@ def test_host_side_validation(lib):
     assert lib.isdf_exchange_potential(None, dummy, 4, dummy, 4, None) == 1
     assert lib.isdf_exchange_apply(None, dummy, 4, dummy, 4, dummy, dummy, 4, 0, 1, dummy, 4, None) == 1
     assert lib.isdf_exchange_status(None) == 1
+    # batch: null arrays, zero count, a null pair pointer
+    arr = (P * 2)(256, 0)
+    lds = (ctypes.c_int64 * 2)(4, 4)
+    bt = P(0)
+    assert lib.isdf_batch_create(ctypes.byref(bt), 2, None, lds, arr, lds, 100, 4, 4, 0, dummy, 8, 0, 64,
+                                 None) == 1
+    assert lib.isdf_batch_create(ctypes.byref(bt), 0, arr, lds, arr, lds, 100, 4, 4, 0, dummy, 8, 0, 64, None) == 1
+    assert lib.isdf_batch_create(ctypes.byref(bt), 2, arr, lds, arr, lds, 100, 4, 4, 0, dummy, 8, 0, 64, None) == 1
+    assert lib.isdf_batch_update(None, dummy, None) == 1
+    assert lib.isdf_batch_plan(None, 0) is None
     # QRCP: n_mu > p, null A, bad dtype, too many grid rows
     assert lib.isdf_qrcp_points(dummy, 4, 4, dummy, 4, 4, 100, 0, dummy, dummy, 8, 9, ix, ix, None) == 1
     assert lib.isdf_qrcp_points(dummy, 4, 4, dummy, 4, 4, 100, 0, None, dummy, 8, 4, ix, ix, None) == 1
