@@ -504,25 +504,18 @@ def run_ours(args):
     import paper_2208_07731_gb300 as isdf
     from paper_2208_07731_gb300 import workload as W
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2208_07731_gb300 import ranks as R
+    rank, world, local = R.env()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
 
     def barrier_max(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return R.max_over_ranks(x, device=dev)
 
-    base = W.WORKLOADS[args.workload]
     # independent problems per rank (like separate k-points): the seed differs by rank
-    w = W.Workload(base.name, base.n, base.L, base.n_orb, base.n_mu, base.dtype, base.iters, base.ecut,
-                   base.kfrac, base.centres, base.seed + 1000 * rank)
+    w = R.rank_workload(W.WORKLOADS[args.workload], rank)
     phi, psi = W.make_pair(w, device=dev)
     phi, psi = W.storage(phi, w).contiguous(), W.storage(psi, w).contiguous()
     shape, cell = (w.n,) * 3, (w.L,) * 3
@@ -675,7 +668,7 @@ def run_ours(args):
 
     mixed = res["mixed"]
     rf = roof(mixed, "mixed")
-    line = {"metric": METRIC, "value": world * 1e3 / mixed["ms"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+    line = {"metric": METRIC, "value": R.job_throughput(1, world, mixed["ms"] * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": mixed["ms"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
             "dtype": "f16 hi+lo split x3 on tcgen05 (f32 accumulate) for the Gram and M^-1 GEMMs; f64 for weights, "
@@ -703,7 +696,7 @@ def run_ours(args):
         err = (torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)).item()
         same_idx = bool(torch.equal(mixed["idx"], f["idx"]))
         rf64 = roof(f, "fp64")
-        line["fp64"] = {"value": world * 1e3 / f["ms"], "unit": UNIT, "ms_per_step": f["ms"],
+        line["fp64"] = {"value": R.job_throughput(1, world, f["ms"] * 1e-3), "unit": UNIT, "ms_per_step": f["ms"],
                         "rooflines": rf64, "stages_ms": f["stages"],
                         "gpu_launches": f["launches"], "clocks": f["clocks"]}
         line["theta_rel_err"] = {"mixed_vs_fp64_gpu": err, "same_idx": same_idx}
@@ -746,7 +739,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_ms = barrier_max(e0.elapsed_time(e1)) / args.steps
     plan.fit_theta(out=theta_dev)   # untimed: the full Theta again for the error check below
-    line["e2e"] = {"value": world * 1e3 / e2e_ms, "unit": UNIT, "ms_per_step": e2e_ms,
+    line["e2e"] = {"value": R.job_throughput(1, world, e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
                    "h2d_bytes_per_step": 2 * phi.numel() * phi.element_size(),
                    "d2h_bytes_per_step": w.n_r * w.n_mu * th_h.element_size() + idx_h.numel() * 8,
                    "theta_block_rows": blk}
