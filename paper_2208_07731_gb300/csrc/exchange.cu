@@ -363,6 +363,10 @@ isdf_status launch_pass(dim3 grid, size_t smem, cudaStream_t st, const T *src, i
     if (dev >= 64 || !attr_set[dev]) {
         ISDF_CUDA_TRY(cudaFuncSetAttribute(fft_lines<T, TM, FUSED, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)fft_smem_bytes<T>(FFT_NMAX)));
+        // the whole unified L1/shared array as shared memory: several line tiles resident per SM
+        ISDF_CUDA_TRY(cudaFuncSetAttribute(fft_lines<T, TM, FUSED, NC>,
+                                           cudaFuncAttributePreferredSharedMemoryCarveout,
+                                           (int)cudaSharedmemCarveoutMaxShared));
         if (dev < 64) attr_set[dev] = true;
     }
     fft_lines<T, TM, FUSED, NC><<<grid, FFT_THREADS, smem, st>>>(src, lds, dst, ldd, ncol, n, pstride, lines, d, S1, S2,
