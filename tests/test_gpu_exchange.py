@@ -63,6 +63,24 @@ def test_potential_ragged_columns_strided_radix5_in_place(isdf):
     assert np.array_equal(got[:, n_mu:], buf[:, n_mu:])     # padding untouched
 
 
+@pytest.mark.parametrize("ld", [102, 101])
+def test_potential_ragged_tile_c64_padded_rows(isdf, ld):
+    # 24^3 takes the compile-time FFT; n_mu = 100 leaves a 4-column last tile; rows padded to an
+    # even (ld = 102) and an odd (ld = 101) number of complex64 entries
+    shape, cell, n_mu = (24, 24, 24), (9.0, 9.0, 9.0), 100
+    buf = _crandn(np.random.default_rng(21), 24 ** 3, ld).astype(np.complex64)
+    ref = O.poisson(buf[:, :n_mu], shape, cell, "coulomb")
+    ex = isdf.Exchange(shape, cell, n_mu, 4, 4, orb_dtype=torch.complex64, mode="mixed")
+    d = torch.from_numpy(buf).to(DEV)
+    out = torch.zeros((24 ** 3, ld), dtype=torch.complex64, device=DEV)
+    ex.potential(d[:, :n_mu], out=out[:, :n_mu])
+    ex.check()
+    got = out.cpu().numpy()
+    assert _maxrel(got[:, :n_mu], ref) < 1e-5
+    assert not np.any(got[:, n_mu:])                          # padding columns untouched
+    assert np.array_equal(d.cpu().numpy(), buf)               # out of place: the input is only read
+
+
 def test_potential_mixed_fp32(isdf):
     shape, cell, n_mu = (24, 24, 24), (10.0, 10.0, 10.0), 96
     theta = _crandn(np.random.default_rng(3), 24 ** 3, n_mu).astype(np.complex64)
