@@ -63,8 +63,11 @@ def algorithmic_flops(w):
 
 # DRAM bytes (read + write) per launch of the two tensor-core kernels from one ncu capture
 # (profiles/tc_gemm_medium.md); only valid for the workload and kernel version profiled there
-NCU_TRAFFIC = {("medium", "apply"): 932.196864e6 + 875.742976e6,
-               ("medium", "gram"): 258.377216e6 + 864.972544e6}
+NCU_TRAFFIC = {("medium", "apply"): 927.113472e6 + 872.801280e6,
+               ("medium", "gram"): 251.076608e6 + 860.567808e6,
+               # the five passes of one exchange potential (profiles/fft_lines_medium.md): 2 x, 2 y, fused z
+               ("medium", "fft_potential"): 2 * (906.020608e6 + 858.783232e6) + 2 * (906.043392e6 + 845.432320e6)
+               + 906.016768e6 + 845.357056e6}
 
 
 def peaks():
@@ -390,7 +393,10 @@ def run_exchange(args):
             "gpu_launches": a["launches"], "clocks": a["clocks"],
             "roofline": {"kernel": "fft_lines (5 passes)", "bound": "hbm", "achieved": achieved, "peak": hbm,
                          "unit": "GB/s", "frac": achieved / hbm if hbm else None,
-                         "peak_source": "measured" if hbm else None, "traffic": None,
+                         "peak_source": "measured" if hbm else None,
+                         "traffic": NCU_TRAFFIC.get((w.name, "fft_potential")),
+                         "traffic_note": "DRAM bytes of the 5 passes of one potential (ncu), vs the algorithmic "
+                                         "bytes below",
                          "algorithmic_bytes_per_step": fft_bytes},
             "fp64": ({"value": 1e3 / b["ms"], "ms_per_step": b["ms"], "potential_ms": b["potential_ms"],
                       "apply_ms": b["apply_ms"], "steps": b["steps"],
