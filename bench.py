@@ -61,11 +61,11 @@ def algorithmic_flops(w):
     return {"gram": 16.0 * w.n_orb * w.n_mu, "apply": 8.0 * w.n_mu * w.n_mu}
 
 
-# DRAM bytes (read + write) per launch of the two tensor-core kernels from one ncu capture
-# (profiles/tc_gemm_medium.md); only valid for the workload and kernel version profiled there
+# DRAM bytes (read + write) per launch of the two tensor-core kernels from one ncu capture of the
+# same command on GB300; only valid for the workload and kernel version profiled
 NCU_TRAFFIC = {("medium", "apply"): 927.113472e6 + 872.801280e6,
                ("medium", "gram"): 251.076608e6 + 860.567808e6,
-               # the five passes of one exchange potential (profiles/fft_lines_medium.md): 2 x, 2 y, fused z
+               # the five passes of one exchange potential (ncu on the x, y and fused z passes: 2 x, 2 y, z)
                ("medium", "fft_potential"): 2 * (906.020608e6 + 858.783232e6) + 2 * (906.043392e6 + 845.432320e6)
                + 906.016768e6 + 845.357056e6}
 
