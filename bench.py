@@ -635,17 +635,23 @@ def run_ours(args):
                 continue
             per_launch_flops = flops[name] * rows_k / n_k
             achieved = per_launch_flops / (ms_k / n_k * 1e-3) / 1e12
+            extra = {}
             if mode == "mixed":
                 peak = pk.get("bf16_tflops_sustained", 1700.0)
                 bound, src = "tensor", "measured cuBLAS bf16 sustained (fp16 dense = bf16 dense)"
             else:
-                peak = 1.25
-                bound, src = "alu", "FP64 pipe, nominal 1.25 TFLOP/s (no FP64 tensor-core MMA on GB300)"
+                # FP64 mode: the products run on tcgen05 by exact slicing, 28 FP16 digit-pair products
+                # per FP64 product; the roofline counts that tensor work, the FP64-equivalent rate is info
+                extra = {"fp64_equivalent_tflops": achieved, "slice_products_per_fp64_product": 28}
+                achieved *= 28.0
+                peak = pk.get("bf16_tflops_sustained", 1700.0)
+                bound, src = "tensor", ("measured cuBLAS bf16 sustained (fp16 dense = bf16 dense); achieved = 28 "
+                                        "digit-pair FP16 products per FP64 product")
             traffic = NCU_TRAFFIC.get((w.name, name)) if mode == "mixed" else None
             out[name] = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_source": src,
                          "launches": n_k, "ms_per_launch": ms_k / n_k,
-                         "algorithmic_flops_per_launch": per_launch_flops}
+                         "algorithmic_flops_per_launch": per_launch_flops, **extra}
         # the FP64 Cholesky factorisation (a9): zgemm_kernel, potrf_diag and split-K reductions on two
         # streams, timed as one stage; algorithmic work = the complex LAPACK count (4/3) n^3 real flops
         nt = r["kt"]["cholesky"][1]
