@@ -451,8 +451,8 @@ class Exchange:
         if theta.dtype != self.v_dtype or theta.stride(1) != 1 or tuple(theta.shape) != (self.n_r, self.n_mu):
             raise ValueError("theta must be n_r x n_mu with contiguous rows in the mode's dtype")
         v = out if out is not None else torch.empty_like(theta)
-        if v.dtype != self.v_dtype or v.stride(1) != 1:
-            raise ValueError("output has the wrong dtype or layout")
+        if v.dtype != self.v_dtype or v.stride(1) != 1 or tuple(v.shape) != (self.n_r, self.n_mu):
+            raise ValueError("output has the wrong dtype, shape or layout")
         _check(lib().isdf_exchange_potential(self._h, _ptr(theta), theta.stride(0), _ptr(v), v.stride(0),
                                              _stream(stream)), "isdf_exchange_potential")
         return v
@@ -460,8 +460,12 @@ class Exchange:
     def apply(self, phi: torch.Tensor, psi: torch.Tensor, idx: torch.Tensor, v: torch.Tensor,
               row_begin: int = 0, row_count: int | None = None, out=None, stream=None) -> torch.Tensor:
         """(V_X psi_j)(r) for rows [row_begin, row_begin + row_count), complex128."""
-        a, lda, _, ca = _orbitals(phi)
-        b, ldb, _, cb = _orbitals(psi)
+        a, lda, na, ca = _orbitals(phi)
+        b, ldb, nb, cb = _orbitals(psi)
+        if (a.shape[0], na, b.shape[0], nb) != (self.n_r, self.n_phi, self.n_r, self.n_psi):
+            raise ValueError("phi and psi must be n_r x n_phi and n_r x n_psi as created")
+        if v.dim() != 2 or v.shape[0] != self.n_r or v.shape[1] < self.n_mu:
+            raise ValueError("v must hold n_r rows of n_mu potentials")
         if row_count is None:
             row_count = self.n_r - row_begin
         if a.dtype != self.orb_dtype or b.dtype != self.orb_dtype:
@@ -470,6 +474,8 @@ class Exchange:
         o = out if out is not None else torch.empty((row_count, self.n_psi), dtype=torch.complex128, device=a.device)
         if v.dtype != self.v_dtype or v.stride(1) != 1 or o.dtype != torch.complex128 or o.stride(1) != 1:
             raise ValueError("v or out has the wrong dtype or layout")
+        if o.dim() != 2 or o.shape[0] < row_count or o.shape[1] < self.n_psi:
+            raise ValueError("out must hold row_count rows of n_psi entries")
         _check(lib().isdf_exchange_apply(self._h, _ptr(a), lda, _ptr(b), ldb, _ptr(ix), _ptr(v), v.stride(0),
                                          int(row_begin), int(row_count), _ptr(o), o.stride(0), _stream(stream)),
                "isdf_exchange_apply")

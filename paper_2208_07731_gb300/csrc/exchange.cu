@@ -567,6 +567,10 @@ extern "C" isdf_status isdf_exchange_create(isdf_exchange **out, int32_t nx, int
             twiddles<float2><<<(n + 127) / 128, 128, 0, st>>>(t, n);
         }
         isdf_note_launch();
+        if (cudaGetLastError() != cudaSuccess) {
+            release(ex);
+            return ISDF_ERR_CUDA;
+        }
     }
     EX_TRY(alloc(&ex->phi_mu, (size_t)n_mu * n_phi));
     EX_TRY(alloc(&ex->psi_mu, (size_t)n_mu * n_psi));

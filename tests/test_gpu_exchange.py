@@ -197,3 +197,20 @@ def test_apply_reports_bad_index(isdf):
     ex.apply(phi.to(DEV), psi.to(DEV), torch.from_numpy(idx), V)
     with pytest.raises(isdf.ISDFError):
         ex.check()
+
+
+def test_binding_rejects_mismatched_shapes(isdf):
+    w = W.small_workload(n=8, L=6.0, n_orb=4, n_mu=16, iters=1, ecut=6.0, seed=3)
+    phi, psi = (x.to(DEV) for x in W.make_pair(w))
+    ex = isdf.Exchange((w.n,) * 3, (w.L,) * 3, 16, 4, 4)
+    V = torch.zeros((w.n_r, 16), dtype=torch.complex128, device=DEV)
+    idx = torch.arange(16, dtype=torch.int64) * 7
+    wide = torch.zeros((w.n_r, 8), dtype=torch.complex128, device=DEV)
+    with pytest.raises(ValueError):
+        ex.apply(wide[:, :6], psi, idx, V)                  # n_phi 6 != 4
+    with pytest.raises(ValueError):
+        ex.apply(phi, psi, idx, V[:, :8])                   # fewer than n_mu potentials
+    with pytest.raises(ValueError):
+        ex.potential(V, out=torch.zeros((w.n_r, 15), dtype=torch.complex128, device=DEV))
+    out = ex.apply(phi, psi, idx, V)                        # the valid call still works
+    assert out.shape == (w.n_r, 4) and not torch.any(out)
