@@ -248,9 +248,12 @@ __device__ __forceinline__ void warp_accumulate(int key, const U128 (&v)[4], uns
     }
 }
 
-template <bool FINAL>
-__global__ void __launch_bounds__(kThreads, 1) km_assign(KmArgs a, int t)
+// NW = 8: an 8 x 8 x 8 tile per CTA (warps = its eight 4 x 4 x 4 sub-cubes); NW = 4: a 4 x 8 x 8 half
+// tile (the four sub-cubes of one x half), which doubles the CTAs on grids with few tiles per SM
+template <bool FINAL, int NW>
+__global__ void __launch_bounds__(32 * NW, 1) km_assign(KmArgs a, int t)
 {
+    constexpr int NT = 32 * NW, TXE = NW == 8 ? TX : TX / 2;
     if (a.ctl->error) return;
     if (!FINAL && a.ctl->converged) return;
     if (!FINAL && a.early_stop && t >= 2 && a.ctl->moved[(t - 1) & 1] == 0u) {
@@ -269,19 +272,19 @@ __global__ void __launch_bounds__(kThreads, 1) km_assign(KmArgs a, int t)
 
     extern __shared__ float4 cand[];  // n_mu entries: (qx, qy, qz, mu bits), tile-local FP32 coordinates
     __shared__ unsigned long long slot[kSlots][8];
-    __shared__ unsigned short wlist[kThreads / 32][kWarpCap];
-    __shared__ int wcount[kThreads / 32];
+    __shared__ unsigned short wlist[NW][kWarpCap];
+    __shared__ int wcount[NW];
     __shared__ unsigned int n_cand;
-    __shared__ float minub_sh[kThreads / 32];
-    __shared__ double red[kThreads / 32];
-    __shared__ unsigned long long redu[kThreads / 32];
-    __shared__ unsigned long long redu2[kThreads / 32];
+    __shared__ float minub_sh[NW];
+    __shared__ double red[NW];
+    __shared__ unsigned long long redu[NW];
+    __shared__ unsigned long long redu2[NW];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int b = blockIdx.x;
     const int tz = b % a.ntz, ty = (b / a.ntz) % a.nty, tx = b / (a.ntz * a.nty);
-    const int ix0 = tx * TX, iy0 = ty * TY, iz0 = tz * TZ;
-    const int ex = min(TX, a.nx - ix0), ey = min(TY, a.ny - iy0), ez = min(TZ, a.nz - iz0);
+    const int ix0 = tx * TXE, iy0 = ty * TY, iz0 = tz * TZ;
+    const int ex = min(TXE, a.nx - ix0), ey = min(TY, a.ny - iy0), ez = min(TZ, a.nz - iz0);
     const double ox = __dmul_rn((double)ix0, a.hx), oy = __dmul_rn((double)iy0, a.hy), oz = __dmul_rn((double)iz0, a.hz);
     const float hx = (float)a.hx, hy = (float)a.hy, hz = (float)a.hz;
     const float Px = (float)((ex - 1) * a.hx), Py = (float)((ey - 1) * a.hy), Pz = (float)((ez - 1) * a.hz);
@@ -291,7 +294,7 @@ __global__ void __launch_bounds__(kThreads, 1) km_assign(KmArgs a, int t)
     const float ox32 = (float)ox, oy32 = (float)oy, oz32 = (float)oz;
     const float dq = a.scan_err;
     float mub = INFINITY;
-    for (int m = tid; m < a.n_mu; m += kThreads) {
+    for (int m = tid; m < a.n_mu; m += NT) {
         const float4 c = a.c32[m];
         const float qx = c.x - ox32, qy = c.y - oy32, qz = c.z - oz32;
         const float ux = fmaxf(fabsf(qx), fabsf(Px - qx));
@@ -303,11 +306,11 @@ __global__ void __launch_bounds__(kThreads, 1) km_assign(KmArgs a, int t)
     if (lane == 0) minub_sh[warp] = mub;
     __syncthreads();
     float minub = minub_sh[0];
-    for (int i = 1; i < kThreads / 32; ++i) minub = fminf(minub, minub_sh[i]);
+    for (int i = 1; i < NW; ++i) minub = fminf(minub, minub_sh[i]);
     const float sminub = sqrtf(minub);
     // keep every centroid whose smallest squared distance to the tile can reach min UB: each
     // coordinate carries an error <= dq, so LB and UB move by <= dq (2 sqrt(3) sqrt(.) + 3 dq)
-    for (int m = tid; m < a.n_mu; m += kThreads) {
+    for (int m = tid; m < a.n_mu; m += NT) {
         const float4 c = a.c32[m];
         const float qx = c.x - ox32, qy = c.y - oy32, qz = c.z - oz32;
         const float lx = fmaxf(0.f, fmaxf(-qx, qx - Px));
@@ -326,7 +329,7 @@ __global__ void __launch_bounds__(kThreads, 1) km_assign(KmArgs a, int t)
     const int nc = (int)n_cand;
     const int ns = min(nc, kSlots);
     if (!FINAL)
-        for (int i = tid; i < ns * 8; i += kThreads) slot[i >> 3][i & 7] = 0ull;
+        for (int i = tid; i < ns * 8; i += NT) slot[i >> 3][i & 7] = 0ull;
 
     // ---- this warp's 4 x 4 x 4 sub-cube and its candidate list
     const int sx = (warp >> 2) & 1, sy = (warp >> 1) & 1, sz = warp & 1;
@@ -499,7 +502,7 @@ __global__ void __launch_bounds__(kThreads, 1) km_assign(KmArgs a, int t)
     if (tid == 0) {
         double jt = 0.0;
         unsigned long long tt = 0ull, rr = 0ull;
-        for (int i = 0; i < kThreads / 32; ++i) {
+        for (int i = 0; i < NW; ++i) {
             jt = __dadd_rn(jt, red[i]);
             tt += redu[i];
             rr += redu2[i];
@@ -509,7 +512,7 @@ __global__ void __launch_bounds__(kThreads, 1) km_assign(KmArgs a, int t)
         if (rr) atomicAdd(&a.ctl->refined, rr);
     }
     if (!FINAL) {
-        for (int j = tid; j < ns; j += kThreads) {
+        for (int j = tid; j < ns; j += NT) {
             unsigned long long *src = &slot[j][0];
             if ((src[0] | src[1]) == 0ull) continue;
             const int m = __float_as_int(cand[j].w);
@@ -655,12 +658,35 @@ isdf_status set_kernel_attributes()
     if (dev < 0 || dev >= 64) return ISDF_ERR_UNSUPPORTED;
     std::lock_guard<std::mutex> guard(lock);
     if (done[dev]) return ISDF_OK;
-    ISDF_CUDA_TRY(cudaFuncSetAttribute(km_assign<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    ISDF_CUDA_TRY(cudaFuncSetAttribute(km_assign<false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)(sizeof(float4) * kMaxMu)));
-    ISDF_CUDA_TRY(cudaFuncSetAttribute(km_assign<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    ISDF_CUDA_TRY(cudaFuncSetAttribute(km_assign<true, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(sizeof(float4) * kMaxMu)));
+    ISDF_CUDA_TRY(cudaFuncSetAttribute(km_assign<false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(sizeof(float4) * kMaxMu)));
+    ISDF_CUDA_TRY(cudaFuncSetAttribute(km_assign<true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)(sizeof(float4) * kMaxMu)));
     done[dev] = true;
     return ISDF_OK;
+}
+
+// CTA tiles of the assignment: 8 x 8 x 8, or 4 x 8 x 8 halves when the grid has fewer than two full
+// tiles per SM of the 152 (the halves' own candidate scans cost less than the idle SMs)
+struct TilePlan {
+    int half, ntx, nty, ntz, n_tiles;
+};
+
+TilePlan tile_plan(int nx, int ny, int nz)
+{
+    TilePlan p;
+    p.nty = (ny + TY - 1) / TY;
+    p.ntz = (nz + TZ - 1) / TZ;
+    const int full = ((nx + TX - 1) / TX) * p.nty * p.ntz;
+    p.half = full < 2 * 152 ? 1 : 0;
+    const int tx = p.half ? TX / 2 : TX;
+    p.ntx = (nx + tx - 1) / tx;
+    p.n_tiles = p.ntx * p.nty * p.ntz;
+    return p;
 }
 
 }  // namespace
@@ -669,8 +695,7 @@ extern "C" isdf_status isdf_kmeans_workspace(int32_t nx, int32_t ny, int32_t nz,
 {
     if (nx < 1 || ny < 1 || nz < 1 || n_mu < 1 || !ws_bytes) return ISDF_ERR_INVALID_ARG;
     const int64_t n_r = (int64_t)nx * ny * nz;
-    const int n_tiles = ((nx + TX - 1) / TX) * ((ny + TY - 1) / TY) * ((nz + TZ - 1) / TZ);
-    *ws_bytes = ws_layout(n_r, n_mu, n_tiles).total;
+    *ws_bytes = ws_layout(n_r, n_mu, tile_plan(nx, ny, nz).n_tiles).total;
     return ISDF_OK;
 }
 
@@ -686,8 +711,9 @@ extern "C" isdf_status isdf_kmeans(const double *w, int32_t nx, int32_t ny, int3
     if (n_mu > kMaxMu) return ISDF_ERR_UNSUPPORTED;
     for (int k = 0; k < 3; ++k)
         if (!(cell[k] > 0.0) || cell[k] > 1e300) return ISDF_ERR_INVALID_ARG;
-    const int ntx = (nx + TX - 1) / TX, nty = (ny + TY - 1) / TY, ntz = (nz + TZ - 1) / TZ;
-    const int n_tiles = ntx * nty * ntz;
+    const TilePlan tp = tile_plan(nx, ny, nz);
+    const int ntx = tp.ntx, nty = tp.nty, ntz = tp.ntz;
+    const int n_tiles = tp.n_tiles;
     const WsLayout L = ws_layout(n_r, n_mu, n_tiles);
     if (!ws || ws_bytes < L.total || !aligned(ws, 256)) return ISDF_ERR_WORKSPACE;
     char *base = static_cast<char *>(ws);
@@ -739,10 +765,14 @@ extern "C" isdf_status isdf_kmeans(const double *w, int32_t nx, int32_t ny, int3
     // small blocks spread the FP64 divisions of the update over many SMs
     const unsigned gmu = (unsigned)((n_mu + 63) / 64);
     for (int t = 0; t < max_iter; ++t) {
-        km_assign<false><<<n_tiles, kThreads, smem, st>>>(a, t); isdf_note_launch();
+        if (tp.half) km_assign<false, 4><<<n_tiles, 128, smem, st>>>(a, t);
+        else km_assign<false, 8><<<n_tiles, kThreads, smem, st>>>(a, t);
+        isdf_note_launch();
         km_update<<<gmu, 64, 0, st>>>(a, t, n_tiles, objective); isdf_note_launch();
     }
-    km_assign<true><<<n_tiles, kThreads, smem, st>>>(a, max_iter); isdf_note_launch();
+    if (tp.half) km_assign<true, 4><<<n_tiles, 128, smem, st>>>(a, max_iter);
+    else km_assign<true, 8><<<n_tiles, kThreads, smem, st>>>(a, max_iter);
+    isdf_note_launch();
     km_snap<<<(unsigned)((n_r + 255) / 256 < 4096 ? (n_r + 255) / 256 : 4096), 256, 0, st>>>(a, n_r); isdf_note_launch();
     km_finish<<<1, 256, 0, st>>>(a, max_iter, n_tiles, idx, centroids, objective, stats); isdf_note_launch();
     ISDF_LAUNCH_CHECK();
