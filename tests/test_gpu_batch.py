@@ -107,3 +107,13 @@ def test_batch_update_and_graph_replay(isdf, kp):
     for b, (p, q) in enumerate(dev_pairs):
         single = isdf.Plan(p, q, idx1, "mixed", max_rows=w.n_r)
         assert torch.equal(out[b], single.fit_theta())
+
+
+def test_batch_of_one_is_a_plan(isdf, kp):
+    w, pairs = kp
+    idx = torch.from_numpy(_idx(w, pairs[:1], 10))
+    p, q = pairs[0][0].to(DEV), pairs[0][1].to(DEV)
+    batch = isdf.Batch([(p, q)], idx, mode="fp64")
+    got = batch.fit_theta()[0]
+    batch.check()
+    assert torch.equal(got, isdf.Plan(p, q, idx, "fp64").fit_theta())

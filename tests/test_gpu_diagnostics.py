@@ -124,3 +124,12 @@ def test_cluster_residual_out_of_range_label_reported(isdf, tiny):
     lab[100] = w.n_mu                         # the kernel checks and skips this row
     with pytest.raises(ValueError):
         isdf.cluster_residual(phi.to(DEV), psi.to(DEV), torch.from_numpy(lab), torch.from_numpy(km["idx"]))
+
+
+def test_cluster_residual_every_point_its_own_cluster_is_zero(isdf):
+    # each row projected on itself (Eq. proj with r_mu = r): R = 0 up to rounding
+    w = W.small_workload(n=8, L=6.0, n_orb=6, n_mu=512, iters=1, ecut=6.0, seed=13)
+    phi, psi = (x.to(DEV) for x in W.make_pair(w))
+    lab = torch.arange(w.n_r, dtype=torch.int32)
+    got = isdf.cluster_residual(phi, psi, lab, torch.arange(w.n_r, dtype=torch.int64))
+    assert abs(got["R"]) <= 1e-13 * got["z2"]

@@ -214,3 +214,13 @@ def test_binding_rejects_mismatched_shapes(isdf):
         ex.potential(V, out=torch.zeros((w.n_r, 15), dtype=torch.complex128, device=DEV))
     out = ex.apply(phi, psi, idx, V)                        # the valid call still works
     assert out.shape == (w.n_r, 4) and not torch.any(out)
+
+
+@pytest.mark.parametrize("shape,n_mu", [((1, 12, 10), 1), ((9, 1, 15), 33)])
+def test_potential_length_one_axis_and_single_column(isdf, shape, n_mu):
+    cell = (3.0, 4.5, 5.0)
+    theta = _crandn(np.random.default_rng(41), int(np.prod(shape)), n_mu)
+    ref = O.poisson(theta, shape, cell, "erfc", 0.5)
+    ex = isdf.Exchange(shape, cell, n_mu, 2, 2, kernel="erfc", omega=0.5)
+    got = ex.potential(torch.from_numpy(theta).to(DEV)).cpu().numpy()
+    assert _maxrel(got, ref) < 1e-12

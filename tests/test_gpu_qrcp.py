@@ -67,3 +67,15 @@ def test_qrcp_medium_properties(isdf):
     n2 = np.sum(np.abs(S) ** 2, axis=1)
     assert idx[0] == int(np.argmax(n2))
     assert rd[0] == pytest.approx(np.sqrt(n2.max()), rel=1e-12)
+
+
+def test_qrcp_as_many_points_as_sketch_columns(isdf):
+    rng = np.random.default_rng(34)
+    n_r, n, p = 700, 6, 30
+    a, b = _crandn(rng, n_r, n), _crandn(rng, n_r, n)
+    A, B = _crandn(rng, n, p), _crandn(rng, n, p)
+    ref = O.qrcp_points(O.qrcp_sketch(a, b, A, B), p)
+    got = isdf.qrcp_points(torch.from_numpy(a).to(DEV), torch.from_numpy(b).to(DEV), torch.from_numpy(A),
+                           torch.from_numpy(B), p)
+    assert np.array_equal(got["idx"].cpu().numpy(), ref["idx"])
+    np.testing.assert_allclose(got["rdiag"].cpu().numpy(), ref["rdiag"], rtol=1e-9)
