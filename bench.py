@@ -245,7 +245,8 @@ def run_adjoint(args):
             "gpu_launches": a["launches"],
             "fp64": {"value": 1e3 / b["ms"], "ms_per_step": b["ms"], "steps": b["steps"]},
             "grad_rel_diff_mixed_vs_fp64": rel, "loss": {"mixed": a["loss"], "fp64": b["loss"]}}
-    print(json.dumps(line), flush=True)
+    if int(os.environ.get("RANK", "0")) == 0:
+        print(json.dumps(line), flush=True)
     return 0
 
 
@@ -402,7 +403,8 @@ def run_exchange(args):
                       "apply_ms": b["apply_ms"], "steps": b["steps"],
                       "fft_bound": "fp64 alu (complex128 FFT)"} if b else None),
             "out_rel_diff_mixed_vs_fp64": rel}
-    print(json.dumps(line), flush=True)
+    if int(os.environ.get("RANK", "0")) == 0:
+        print(json.dumps(line), flush=True)
     return 0
 
 
@@ -497,7 +499,8 @@ def run_batch(args):
             "gpu_launches": a["launches"], "clocks": a["clocks"],
             "sequential": {"value": B * 1e3 / b["ms"], "ms_per_step": b["ms"]},
             "speedup_vs_sequential": b["ms"] / a["ms"]}
-    print(json.dumps(line), flush=True)
+    if int(os.environ.get("RANK", "0")) == 0:
+        print(json.dumps(line), flush=True)
     return 0
 
 
