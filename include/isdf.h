@@ -301,7 +301,7 @@ ISDF_API isdf_status isdf_fit_error(isdf_plan *plan, int64_t row_begin, int64_t 
                                     void *stream);
 
 /* ---------------------------------------------------------------------------
- * ISDF exchange application (Sec. 2.4, Eq. v2 and Eq. V_mu).
+ * ISDF exchange application (Sec. 2.3, Eq. v2 and Eq. V_mu).
  *
  * Step A, isdf_exchange_potential: V_mu(r) = int zeta_mu(r') v(r - r') dr' for
  * every column mu of Theta (the interpolation vectors), on the periodic grid

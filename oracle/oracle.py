@@ -271,7 +271,7 @@ def cluster_residual(phi, psi, labels, idx) -> dict:
 
 
 # --------------------------------------------------------------------------
-# ISDF exchange application, Sec. 2.4 (Eq. v, Eq. v2, Eq. V_mu).
+# ISDF exchange application, Sec. 2.3 (Eq. v, Eq. v2, Eq. V_mu).
 # Periodic cell [0, L_x) x [0, L_y) x [0, L_z). A column f of grid samples is
 # read as the band-limited periodic function sum_G c(G) exp(i G.r) with
 # c = fftn(f) / N_r. A pair product that carries a Bloch phase exp(i q.r)

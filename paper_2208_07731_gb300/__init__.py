@@ -403,7 +403,7 @@ class Batch:
 
 
 class Exchange:
-    """ISDF exchange application (Sec. 2.4, isdf_exchange_*): potential() solves the periodic
+    """ISDF exchange application (Sec. 2.3, isdf_exchange_*): potential() solves the periodic
     Poisson problems V_mu = v * zeta_mu (Eq. V_mu) for all columns of Theta by FFT, apply()
     forms (V_X psi_j)(r) = -[(V o (Phi Phi_mu^H)) Psi_mu](r, j) (Eq. v2). kernel is "coulomb"
     (1/r) or "erfc" (erfc(omega r)/r). Theta must interpolate phi_i* psi_j, i.e. come from a

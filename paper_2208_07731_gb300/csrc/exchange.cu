@@ -1,4 +1,4 @@
-// ISDF exchange application (Sec. 2.4): the projected exchange integrals
+// ISDF exchange application (Sec. 2.3): the projected exchange integrals
 // V_mu = v * zeta_mu of Eq. V_mu for every interpolation vector, solved in
 // reciprocal space on the periodic FFT grid, and the application of Eq. v2,
 //     (V_X psi_j)(r) = -sum_mu V_mu(r) sum_i phi_i(r) phi_i*(r_mu) psi_j(r_mu)

@@ -1,4 +1,4 @@
-"""GPU parity of the ISDF exchange application (Sec. 2.4; isdf_exchange_*)
+"""GPU parity of the ISDF exchange application (Sec. 2.3; isdf_exchange_*)
 against the oracle on the same seeded inputs.
 
 Tolerances, from the arithmetic: the FP64 FFT carries ~log2(N_r) eps of

@@ -1,4 +1,4 @@
-"""Pins of the exchange-application oracle (Sec. 2.4: Eq. v, Eq. v2, Eq. V_mu)
+"""Pins of the exchange-application oracle (Sec. 2.3: Eq. v, Eq. v2, Eq. V_mu)
 against facts fixed outside it: plane waves are eigenfunctions of the periodic
 interaction, the screened (erfc) potential of a Gaussian charge has a closed
 form, the bare Coulomb potential satisfies Poisson's equation (checked with an
