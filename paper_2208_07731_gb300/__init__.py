@@ -344,7 +344,11 @@ class Batch:
     interpolation points; update() and fit_theta() run the pairs on concurrent streams."""
 
     def __init__(self, pairs, idx: torch.Tensor, mode: str = "fp64", max_rows: int = 65536, stream=None):
+        if len(pairs) == 0:
+            raise ValueError("a batch needs at least one orbital pair")
         ops = [(_orbitals(p), _orbitals(q)) for p, q in pairs]
+        if len({a.device for (a, _, _, _), _ in ops} | {b.device for _, (b, _, _, _) in ops}) != 1:
+            raise ValueError("every pair must live on the same device")
         (a0, _, na, ca), (_, _, nb, cb) = ops[0]
         for (a, _, n1, c1), (b, _, n2, c2) in ops:
             if (n1, n2, c1, c2) != (na, nb, ca, cb) or a.shape[0] != a0.shape[0] or b.shape[0] != a0.shape[0]:
