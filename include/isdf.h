@@ -136,9 +136,23 @@ ISDF_API isdf_status isdf_weights(const void *phi, int64_t ld_phi, int32_t n_phi
  *             256-byte aligned. Its contents need no initialisation.
  * Limits: 1 <= n_mu <= min(n_r, 8192), n_r < 2^31. Weights with
  * n_r * max(w) * max(L, 1) >= 2^126 are rejected on the device
- * (ISDF_ERR_NONFINITE recorded in stats[2] = -1).
+ * (ISDF_ERR_NONFINITE recorded in stats[2] = -1); an init_idx entry outside
+ * [0, n_r) gives stats[2] = -2. isdf_kmeans_status turns stats into a status.
  * ------------------------------------------------------------------------- */
 ISDF_API isdf_status isdf_kmeans_workspace(int32_t nx, int32_t ny, int32_t nz, int32_t n_mu, size_t *ws_bytes);
+
+/* The outcome of an isdf_kmeans call as a status code. stats is that call's
+ * device stats array (4 int64); the call synchronises `stream` (the stream the
+ * K-means ran on) and reads stats[2]:
+ *   0  -> ISDF_OK;
+ *   >0 -> ISDF_ERR_EMPTY_CLUSTER (that many clusters had no member after the
+ *         last assignment: their idx entries are -1, Algorithm 1 leaves the
+ *         case open);
+ *   -1 -> ISDF_ERR_NONFINITE (a weight negative, infinite or NaN, or too large
+ *         for the 128-bit fixed-point sums: every idx is -1);
+ *   -2 -> ISDF_ERR_INVALID_ARG (an init_idx entry outside [0, n_r): every idx
+ *         is -1). */
+ISDF_API isdf_status isdf_kmeans_status(const int64_t *stats, void *stream);
 ISDF_API isdf_status isdf_kmeans(const double *w, int32_t nx, int32_t ny, int32_t nz, const double *cell,
                         int32_t n_mu, const int64_t *init_idx, int32_t max_iter, int32_t flags,
                         int64_t *idx, double *centroids, double *objective, int32_t *labels,
@@ -158,9 +172,14 @@ ISDF_API isdf_status isdf_kmeans(const double *w, int32_t nx, int32_t ny, int32_
  *  - Problems whose isdf_kmeans_workspace() exceeds the array size return
  *    ISDF_ERR_UNSUPPORTED before anything is launched (32 MiB covers a
  *    128^3 grid with 4096 points).
- *  - The first call on a device looks up the array's device address with that
- *    device current (cudaGetSymbolAddress) and keeps it; make that first call
- *    before any stream capture on the device.
+ *  - The first call in a CUDA context looks up the array's device address in
+ *    that context (cudaGetSymbolAddress, with the context current) and keeps
+ *    it; a later call under a different current context on the same device
+ *    (after cudaDeviceReset, or a driver-API caller's own context) looks it up
+ *    again. Make the first call of each context before any stream capture on
+ *    the device. The lookup is not repeated for a context that is destroyed
+ *    and re-created at the same handle value. Arguments are checked like
+ *    isdf_kmeans's (ISDF_ERR_INVALID_ARG) before the size check.
  *  - Every call, on every stream, uses the same array, and the array keeps the
  *    last call's contents (each call re-initialises what it reads). Calls that
  *    overlap on the GPU (different streams, or different host threads without
@@ -393,8 +412,35 @@ ISDF_API isdf_status isdf_cluster_residual(const void *phi, int64_t ld_phi, int3
 
 /* Synchronises the plan's last stream and returns the first device-side
  * failure (ISDF_OK, ISDF_ERR_NOT_HPD with *detail = failing pivot index,
- * ISDF_ERR_NONFINITE, ISDF_ERR_TIMEOUT). detail may be NULL. */
+ * ISDF_ERR_NONFINITE, ISDF_ERR_TIMEOUT). detail may be NULL.
+ * ISDF_ERR_NONFINITE is also what a NaN or infinity anywhere in the orbitals
+ * gives: in ISDF_MIXED mode every row is scanned when the plan is created or
+ * updated, in ISDF_FP64 mode every row of a block when it is fitted (the
+ * tensor-core FP64 products cannot slice a non-finite entry); the affected
+ * Theta rows are then not valid. With ISDF_PLAN_FP64_SIMT the FP64-pipe
+ * products propagate a NaN into Theta instead. isdf_plan_update clears the
+ * status. */
 ISDF_API isdf_status isdf_plan_status(isdf_plan *plan, int32_t *detail);
+
+/* Failure-path control, for tests of the bounded waits (Sec. 2.1 names no
+ * such mechanism: it belongs to this implementation). Every wait of the
+ * plan's tensor-core kernels (the split products of ISDF_MIXED, the
+ * exact-slicing FP64 products) gives up after a budget of SM clock cycles,
+ * about 0.1 s by default; the kernel then records ISDF_ERR_TIMEOUT, lets its
+ * own copies and MMAs finish, frees its tensor memory and returns, and the
+ * grid's remaining CTAs exit at once. For later launches of this plan:
+ *   cycles > 0  replaces that budget for the pipeline waits (a wait may still
+ *               succeed: one try of an mbarrier wait can itself suspend the
+ *               thread for a while);
+ *   cycles < 0  test hook: the MMA-issuing thread of each CTA first waits on
+ *               a barrier that nothing signals, gives up after -cycles cycles
+ *               and takes the timeout path, so the launch reliably reports
+ *               ISDF_ERR_TIMEOUT (the other waits keep the default budget);
+ *   cycles == 0 restores the default.
+ * The waits that drain a kernel's own copies and MMAs before it exits always
+ * keep the default budget. isdf_plan_update clears a recorded timeout.
+ * Host-side setting only: nothing is launched. */
+ISDF_API isdf_status isdf_plan_set_wait_budget(isdf_plan *plan, int64_t cycles);
 
 /* Copies a plan-owned matrix into the caller's device buffer dst
  * (stream-ordered): which = 0 M, 1 L, 2 M^-1 (each n_mu x n_mu complex128,

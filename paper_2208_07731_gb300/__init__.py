@@ -62,6 +62,8 @@ def lib():
         L.isdf_plan_status.argtypes = [P, P]
         L.isdf_plan_copy_matrix.argtypes = [P, I32, P, P]
         L.isdf_plan_update.argtypes = [P, P, P]
+        L.isdf_plan_set_wait_budget.argtypes = [P, I64]
+        L.isdf_kmeans_status.argtypes = [P, P]
         L.isdf_fit_error.argtypes = [P, I64, I64, P, P]
         L.isdf_cluster_residual.argtypes = [P, I64, I32, P, I64, I32, I64, I32, P, P, I32, P, P, P]
         L.isdf_batch_create.argtypes = [P, I32, P, P, P, P, I64, I32, I32, I32, P, I32, I32, I64, P]
@@ -93,7 +95,8 @@ def lib():
                   "isdf_fit_theta_backward", "isdf_fit_theta_backward_finalize", "isdf_plan_status",
                   "isdf_plan_copy_matrix", "isdf_plan_update", "isdf_plan_enable_timing", "isdf_plan_kernel_time",
                   "isdf_fit_error", "isdf_cluster_residual", "isdf_exchange_create", "isdf_exchange_potential",
-                  "isdf_exchange_apply", "isdf_exchange_status"):
+                  "isdf_exchange_apply", "isdf_exchange_status", "isdf_plan_set_wait_budget",
+                  "isdf_kmeans_status"):
             getattr(L, f).restype = ctypes.c_int32
         _lib = L
     return _lib
@@ -179,6 +182,17 @@ def kmeans(w: torch.Tensor, shape, cell, n_mu: int, init_idx: torch.Tensor, max_
     return {"idx": idx, "centroids": cen, "objective": obj, "labels": lab, "stats": stats}
 
 
+def kmeans_status(km: dict, stream=None) -> int:
+    """Status code of a finished kmeans() call (isdf_kmeans_status; synchronises the stream):
+    0, or ISDF_ERR_EMPTY_CLUSTER / ISDF_ERR_NONFINITE / ISDF_ERR_INVALID_ARG."""
+    return int(lib().isdf_kmeans_status(_ptr(km["stats"]), _stream(stream)))
+
+
+def kmeans_check(km: dict, stream=None):
+    """Raise ISDFError unless the kmeans() call ended without an empty cluster or bad input."""
+    _check(kmeans_status(km, stream), "isdf_kmeans")
+
+
 class Plan:
     """Theta fit at fixed interpolation points (isdf_plan_*): gathers Phi_mu,
     Psi_mu, forms M = C C^H in FP64, factors it and forms M^-1 on creation.
@@ -240,6 +254,10 @@ class Plan:
         if self.idx.numel() != self.n_mu:
             raise ValueError("update needs the plan's n_mu points")
         _check(lib().isdf_plan_update(self._h, _ptr(self.idx), _stream(stream)), "isdf_plan_update")
+
+    def set_wait_budget(self, cycles: int):
+        """Cycle budget of the tensor-core kernels' pipeline waits for later launches (<= 0: default)."""
+        _check(lib().isdf_plan_set_wait_budget(self._h, int(cycles)), "isdf_plan_set_wait_budget")
 
     def enable_timing(self, capacity: int = 4096):
         _check(lib().isdf_plan_enable_timing(self._h, int(capacity)), "isdf_plan_enable_timing")

@@ -344,9 +344,11 @@ isdf_status cholesky_inverse(const double2 *M0, double2 *L, double2 *Linv, doubl
         const int k1 = k + NB, rest = n - k1;              // next block at k1, rows below block k
         const int nb1 = rest < NB ? rest : NB, rest1 = rest - nb1;
         cudaStream_t s2 = side ? side : stream;
+        StreamJoin fork;   // joins the side stream back on any early return below
         if (side) {
             ISDF_CUDA_TRY(cudaEventRecord(tp->ev_fork, stream));
             ISDF_CUDA_TRY(cudaStreamWaitEvent(side, tp->ev_fork, 0));
+            fork.arm(stream, side, tp->ev_join);
         }
         // side: A[k1:, k1:k1+nb1] -= L21 L21[0:nb1]^H, then factor block k1 and its panel
         ZGemm a = single(rest, nb1, NB, op(L + (int64_t)k1 * ld + k, ld, 1, 0), op(L + (int64_t)k1 * ld + k, 1, ld, 1),
@@ -368,10 +370,7 @@ isdf_status cholesky_inverse(const double2 *M0, double2 *L, double2 *Linv, doubl
             u.lower_only = 1;
             ISDF_TRY(zgemm_auto(u, pmain, nmain, stream));
         }
-        if (side) {
-            ISDF_CUDA_TRY(cudaEventRecord(tp->ev_join, side));
-            ISDF_CUDA_TRY(cudaStreamWaitEvent(stream, tp->ev_join, 0));
-        }
+        ISDF_CUDA_TRY(fork.join());
     }
     {
         const int64_t total = (int64_t)n * n;

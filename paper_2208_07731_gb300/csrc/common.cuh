@@ -28,6 +28,35 @@
 // host-side count of the kernels this library has launched (for benchmarks)
 void isdf_note_launch();
 
+// Joins a forked stream back into the caller's stream on every return path.
+// After `side` was made to wait on the caller's stream, arm() the guard; the
+// normal path calls join() where the work is meant to merge. If the function
+// returns early (an error after the fork), the destructor records `ev` on
+// the side stream and makes the caller's stream wait on it, so no work of the
+// side stream stays unjoined (a stream capture stays valid, and the caller's
+// stream does not run ahead of kernels that still use the plan's buffers).
+struct StreamJoin {
+    cudaStream_t main = nullptr, side = nullptr;
+    cudaEvent_t ev = nullptr;
+    bool armed = false;
+    void arm(cudaStream_t m, cudaStream_t s, cudaEvent_t e)
+    {
+        main = m;
+        side = s;
+        ev = e;
+        armed = true;
+    }
+    cudaError_t join()
+    {
+        if (!armed) return cudaSuccess;
+        armed = false;
+        cudaError_t e = cudaEventRecord(ev, side);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(main, ev, 0);
+        return e;
+    }
+    ~StreamJoin() { join(); }
+};
+
 static inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
 static inline bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }

@@ -678,7 +678,7 @@ extern "C" isdf_status isdf_exchange_status(isdf_exchange *ex)
     if (!ex) return ISDF_ERR_INVALID_ARG;
     int h[2] = {0, 0};
     ISDF_CUDA_TRY(cudaMemcpy(h, ex->flags, sizeof(h), cudaMemcpyDeviceToHost));
-    if (h[0]) return ISDF_ERR_TIMEOUT;
+    if (h[0]) return h[0] == 2 ? ISDF_ERR_NONFINITE : ISDF_ERR_TIMEOUT;
     if (h[1]) return ISDF_ERR_INVALID_ARG;
     if (ex->mixed) return (isdf_status)mixed_exchange_error(ex->mixed);
     return ISDF_OK;

@@ -608,7 +608,7 @@ __global__ void km_finish(KmArgs a, int max_iter, int n_tiles, int64_t *idx, dou
         if (stats) {
             stats[0] = nit;
             stats[1] = (int64_t)a.ctl->ties;
-            stats[2] = err ? -1 : empty_sh;
+            stats[2] = err == 2 ? -2 : (err ? -1 : empty_sh);
             stats[3] = (int64_t)a.ctl->refined;
         }
     }
@@ -777,4 +777,15 @@ extern "C" isdf_status isdf_kmeans(const double *w, int32_t nx, int32_t ny, int3
     km_finish<<<1, 256, 0, st>>>(a, max_iter, n_tiles, idx, centroids, objective, stats); isdf_note_launch();
     ISDF_LAUNCH_CHECK();
     return ISDF_OK;
+}
+
+extern "C" isdf_status isdf_kmeans_status(const int64_t *stats, void *stream)
+{
+    if (!stats) return ISDF_ERR_INVALID_ARG;
+    ISDF_CUDA_TRY(cudaStreamSynchronize(as_stream(stream)));
+    int64_t h[4] = {0, 0, 0, 0};
+    ISDF_CUDA_TRY(cudaMemcpy(h, stats, sizeof(h), cudaMemcpyDeviceToHost));
+    if (h[2] == -2) return ISDF_ERR_INVALID_ARG;
+    if (h[2] < 0) return ISDF_ERR_NONFINITE;
+    return h[2] > 0 ? ISDF_ERR_EMPTY_CLUSTER : ISDF_OK;
 }

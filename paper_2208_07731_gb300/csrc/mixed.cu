@@ -23,6 +23,8 @@
 // in segments summed in registers.
 #include <cudaTypedefs.h>
 
+#include <cfloat>
+
 #include "mixed.cuh"
 #include "tc.cuh"
 
@@ -75,6 +77,7 @@ template <typename T>
 __global__ void absmax_rows(const T *x, int64_t ld, int n, int64_t n_r, unsigned int *maxabs, unsigned int *maxrho)
 {
     float ma = 0.f, mr = 0.f;
+    bool bad = false;   // an infinite or NaN entry
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -85,6 +88,8 @@ __global__ void absmax_rows(const T *x, int64_t ld, int n, int64_t n_r, unsigned
             float acc = 0.f;
             for (int i = lane; i < n; i += 32) {
                 const float2 v = xr[i];
+                // fmaxf drops a NaN operand: NaN entries are flagged separately
+                bad |= !(fabsf(v.x) <= FLT_MAX) || !(fabsf(v.y) <= FLT_MAX);
                 ma = fmaxf(ma, fmaxf(fabsf(v.x), fabsf(v.y)));
                 acc = fmaf(v.x, v.x, fmaf(v.y, v.y, acc));
             }
@@ -96,6 +101,7 @@ __global__ void absmax_rows(const T *x, int64_t ld, int n, int64_t n_r, unsigned
             for (int i = lane; i < n; i += 32) {
                 const double2 v = cload(x, r * ld + i);
                 const float a = d2f_int(v.x), b = d2f_int(v.y);
+                bad |= !(fabsf(a) <= FLT_MAX) || !(fabsf(b) <= FLT_MAX);
                 ma = fmaxf(ma, fmaxf(fabsf(a), fabsf(b)));
                 acc = fmaf(a, a, fmaf(b, b, acc));
             }
@@ -108,6 +114,8 @@ __global__ void absmax_rows(const T *x, int64_t ld, int n, int64_t n_r, unsigned
         ma = fmaxf(ma, __shfl_xor_sync(0xffffffffu, ma, o));
         mr = fmaxf(mr, __shfl_xor_sync(0xffffffffu, mr, o));
     }
+    // a non-finite entry makes the bound infinite, which compute_scales reports as ISDF_ERR_NONFINITE
+    if (__any_sync(0xffffffffu, bad)) ma = INFINITY;
     if (lane == 0) {
         atomic_max_pos(maxabs, ma * 1.0001f);
         if (maxrho) atomic_max_pos(maxrho, mr);
@@ -218,6 +226,8 @@ struct EpiParams {
     const float2 *vmat;   // complex64, leading dimension ldv (complex), row 0 = the block's first row
     int64_t ldv;
     const float *fvh;
+    long long budget;     // cycle budget of the pipeline waits; 0: WAIT_BUDGET (the drain waits keep it);
+                          // < 0: test hook, see isdf_plan_set_wait_budget
 };
 
 // One persistent CTA per SM walks the output tiles (row-block major, so
@@ -248,10 +258,12 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     __shared__ __align__(8) uint64_t tfull[2];
     __shared__ __align__(8) uint64_t tempty[2];
     __shared__ __align__(8) uint64_t drain_bar;
+    __shared__ __align__(8) uint64_t never_bar;   // signalled by nothing (the test hook waits on it)
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int failed;
 
     if (*(volatile int *)ep.err) return;
+    const long long budget = ep.budget > 0 ? ep.budget : WAIT_BUDGET;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t raw = tc::smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -273,6 +285,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             tc::mbar_init(&tempty[a], EPI_WARPS);
         }
         tc::mbar_init(&drain_bar, 1);
+        tc::mbar_init(&never_bar, 1);
         failed = 0;
         tc::fence_barrier_init();
     }
@@ -295,7 +308,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                     for (int part = 0; part < PARTS && !failed; ++part)
                         for (int kc = s0; kc < min(ke, s0 + seg); ++kc, ++c) {
                             const int s = c % STAGES, it = c / STAGES;
-                            if (!tc::mbar_wait(&empty_bar[s], (it & 1) ^ 1, WAIT_BUDGET)) {
+                            if (!tc::mbar_wait(&empty_bar[s], (it & 1) ^ 1, budget)) {
                                 atomicExch(ep.err, 1);
                                 failed = 1;
                                 break;
@@ -319,12 +332,19 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             constexpr uint32_t idesc = tc::idesc_f16(TM, TN);
             int c = 0, tl = 0;
             bool ok = true;
+            // test hook (negative budget): a wait on a barrier that nothing signals runs out after
+            // -budget cycles and takes the timeout path before any MMA is issued
+            if (ep.budget < 0 && !tc::mbar_wait(&never_bar, 0, -ep.budget)) {
+                atomicExch(ep.err, 1);
+                failed = 1;
+                ok = false;
+            }
             for (int t = blockIdx.x; t < n_work && !failed && ok; t += gridDim.x) {
                 const int ks = t % ksplit;
                 const int kb = ks * kper, ke = min(kchunks, kb + kper);
                 for (int s0 = kb; s0 < ke && ok; s0 += seg, ++tl) {
                     const int acc = tl & 1, use = tl >> 1;
-                    if (!tc::mbar_wait(&tempty[acc], (use & 1) ^ 1, WAIT_BUDGET)) {
+                    if (!tc::mbar_wait(&tempty[acc], (use & 1) ^ 1, budget)) {
                         atomicExch(ep.err, 1);
                         failed = 1;
                         ok = false;
@@ -336,7 +356,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                         const uint32_t d = tmem + (uint32_t)acc * ACC + (uint32_t)part * TN;
                         for (int kc = s0; kc < s1; ++kc, ++c) {
                             const int s = c % STAGES, it = c / STAGES;
-                            if (!tc::mbar_wait(&full_bar[s], it & 1, WAIT_BUDGET)) {
+                            if (!tc::mbar_wait(&full_bar[s], it & 1, budget)) {
                                 atomicExch(ep.err, 1);
                                 failed = 1;
                                 ok = false;
@@ -384,7 +404,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             bool ok = true;
             for (int s0 = kb; s0 < ke; s0 += seg, ++tl) {
                 const int acc = tl & 1, use = tl >> 1;
-                if (!tc::mbar_wait(&tfull[acc], use & 1, WAIT_BUDGET)) {
+                if (!tc::mbar_wait(&tfull[acc], use & 1, budget)) {
                     atomicExch(ep.err, 1);
                     failed = 1;
                     ok = false;
@@ -772,6 +792,7 @@ isdf_status mixed_fit(isdf_plan *p, int64_t row_begin, int64_t row_count, void *
         ep.ldy = 2 * nm;
         ep.sc = b->sc;
         ep.err = err;
+        ep.budget = p->wait_budget;
         ep.ksplit = 1;
         ep.ncols = 2 * nm;
         const int n_tiles_n = (2 * nm) / TN, m_tiles = (rows + TM - 1) / TM;
@@ -938,6 +959,7 @@ isdf_status mixed_backward(isdf_plan *p, int64_t row_begin, int64_t row_count, c
             ep.ldab = nm;
             ep.sc = b->sc;
             ep.err = err;
+            ep.budget = p->wait_budget;
             ep.ksplit = 1;
             ep.ncols = 2 * nm;
             const int n_tiles_n = (2 * nm) / TN, m_tiles = (rows + TM - 1) / TM;
@@ -952,6 +974,7 @@ isdf_status mixed_backward(isdf_plan *p, int64_t row_begin, int64_t row_count, c
         EpiParams e{};
         e.sc = b->sc;
         e.err = err;
+        e.budget = p->wait_budget;
         e.ksplit = 1;
         // 2. Theta = Y M^-1 (complex64)
         e.out_mode = OUT_C64;

@@ -57,7 +57,9 @@ struct OzArgs {
     int64_t ldc, bsc;
     const unsigned long long *ma, *mb;   // row maxima (batch-major: M and N per product)
     int *gsum;              // buffered epilogue: exact group sums [b][g - 2][M][2N] (int32), or NULL
-    int *err;
+    int *err;               // 1: a bounded wait gave up; 2: a non-finite operand entry
+    long long budget;       // cycle budget of the pipeline waits (the drain waits keep OWAIT)
+    long long never;        // > 0: test hook, the MMA issuer first waits this long on a barrier nothing signals
 };
 
 __device__ __forceinline__ int row_exp(unsigned long long maxbits) { return (int)(maxbits >> 52) - 1022; }
@@ -102,7 +104,8 @@ __device__ __forceinline__ double2 load_c(const float2 *p, int64_t i)
 // per-row max |Re|, |Im| (as double bits) of the operand rows r, entries X[r sr + k sk],
 // one 32 x 32 (r, k) tile per block of 32 x 8 threads, batch in blockIdx.z
 template <typename T>
-__global__ void oz_rowmax(const T *X, int64_t sr, int64_t sk, int64_t bsx, int R, int K, unsigned long long *maxbits)
+__global__ void oz_rowmax(const T *X, int64_t sr, int64_t sk, int64_t bsx, int R, int K, unsigned long long *maxbits,
+                          int *err)
 {
     __shared__ unsigned long long t[32][33];
     const int k0 = blockIdx.x * 32, r0 = blockIdx.y * 32, b = blockIdx.z;
@@ -126,6 +129,8 @@ __global__ void oz_rowmax(const T *X, int64_t sr, int64_t sk, int64_t bsx, int R
         for (int j = 0; j < 32; ++j) m = t[threadIdx.x][j] > m ? t[threadIdx.x][j] : m;
         const int r = r0 + (int)threadIdx.x;
         if (r < R && m) atomicMax(&maxbits[(int64_t)b * R + r], m);
+        // an infinity or NaN (exponent field all ones) cannot be sliced: recorded, not computed on
+        if (m >= 0x7FF0000000000000ull) atomicCAS(err, 0, 2);
     }
 }
 
@@ -206,6 +211,7 @@ __global__ void __launch_bounds__(OTHREADS, 1)
     __shared__ __align__(8) uint64_t tfull[2];
     __shared__ __align__(8) uint64_t tempty[2];
     __shared__ __align__(8) uint64_t drain_bar;
+    __shared__ __align__(8) uint64_t never_bar;   // signalled by nothing (the test hook waits on it)
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int failed;
 
@@ -226,6 +232,7 @@ __global__ void __launch_bounds__(OTHREADS, 1)
             tc::mbar_init(&tempty[i], OEPI);
         }
         tc::mbar_init(&drain_bar, 1);
+        tc::mbar_init(&never_bar, 1);
         failed = 0;
         tc::fence_barrier_init();
     }
@@ -249,7 +256,7 @@ __global__ void __launch_bounds__(OTHREADS, 1)
                         const int ya = (b * NSLICE + s - 1) * a.Ra + m0, yb = (b * NSLICE + g - s - 1) * a.Rb + n0;
                         for (int kc = kb; kc < ke; ++kc, ++c) {
                             const int st = c % OSTAGES, it = c / OSTAGES;
-                            if (!tc::mbar_wait(&empty_bar[st], (it & 1) ^ 1, OWAIT)) {
+                            if (!tc::mbar_wait(&empty_bar[st], (it & 1) ^ 1, a.budget)) {
                                 atomicExch(a.err, 1);
                                 failed = 1;
                                 break;
@@ -271,6 +278,11 @@ __global__ void __launch_bounds__(OTHREADS, 1)
             constexpr uint32_t idesc = tc::idesc_f16(OTM, OTN);
             int c = 0, tl = 0;
             bool ok = true;
+            if (a.never > 0 && !tc::mbar_wait(&never_bar, 0, a.never)) {
+                atomicExch(a.err, 1);
+                failed = 1;
+                ok = false;
+            }
             for (int t = blockIdx.x; t < n_work && ok && !failed; t += gridDim.x) {
                 int b, m0, n0, kb, ke;
                 if (!tile_of(a, t, b, m0, n0)) continue;
@@ -279,7 +291,7 @@ __global__ void __launch_bounds__(OTHREADS, 1)
                     for (int s = max(1, g - NSLICE); s <= min(NSLICE, g - 1) && ok; ++s)
                         for (int s0 = kb; s0 < ke && ok; s0 += SEG, ++tl) {
                             const int acc = tl & 1, use = tl >> 1;
-                            if (!tc::mbar_wait(&tempty[acc], (use & 1) ^ 1, OWAIT)) {
+                            if (!tc::mbar_wait(&tempty[acc], (use & 1) ^ 1, a.budget)) {
                                 atomicExch(a.err, 1);
                                 failed = 1;
                                 ok = false;
@@ -290,7 +302,7 @@ __global__ void __launch_bounds__(OTHREADS, 1)
                             const int s1 = min(ke, s0 + SEG);
                             for (int kc = s0; kc < s1; ++kc, ++c) {
                                 const int st = c % OSTAGES, it = c / OSTAGES;
-                                if (!tc::mbar_wait(&full_bar[st], it & 1, OWAIT)) {
+                                if (!tc::mbar_wait(&full_bar[st], it & 1, a.budget)) {
                                     atomicExch(a.err, 1);
                                     failed = 1;
                                     ok = false;
@@ -343,7 +355,7 @@ __global__ void __launch_bounds__(OTHREADS, 1)
                 for (int s = s_lo; s <= s_hi && ok; ++s)
                     for (int s0 = kb; s0 < ke; s0 += SEG, ++tl) {
                         const int accb = tl & 1, use = tl >> 1;
-                        if (!tc::mbar_wait(&tfull[accb], use & 1, OWAIT)) {
+                        if (!tc::mbar_wait(&tfull[accb], use & 1, a.budget)) {
                             atomicExch(a.err, 1);
                             failed = 1;
                             ok = false;
@@ -541,13 +553,13 @@ isdf_status oz_zgemm(const ZGemm &g, const OzWork &w, int *err, cudaStream_t st)
                      unsigned long long *mx, __half *out, int64_t Rp) {
         if (o.type == ZG_C64) {
             const float2 *X = static_cast<const float2 *>(o.p);
-            oz_rowmax<float2><<<grid, blk, 0, st>>>(X, sr, sk, bs, R, g.K, mx);
+            oz_rowmax<float2><<<grid, blk, 0, st>>>(X, sr, sk, bs, R, g.K, mx, err);
             isdf_note_launch();
             oz_slice<float2><<<grid, blk, 0, st>>>(X, sr, sk, bs, R, g.K, conj, rot, mx, out, Rp, Kp);
             isdf_note_launch();
         } else {
             const double2 *X = static_cast<const double2 *>(o.p);
-            oz_rowmax<double2><<<grid, blk, 0, st>>>(X, sr, sk, bs, R, g.K, mx);
+            oz_rowmax<double2><<<grid, blk, 0, st>>>(X, sr, sk, bs, R, g.K, mx, err);
             isdf_note_launch();
             oz_slice<double2><<<grid, blk, 0, st>>>(X, sr, sk, bs, R, g.K, conj, rot, mx, out, Rp, Kp);
             isdf_note_launch();
@@ -582,6 +594,8 @@ isdf_status oz_zgemm(const ZGemm &g, const OzWork &w, int *err, cudaStream_t st)
     a.ma = w.ma;
     a.mb = w.mb;
     a.err = err;
+    a.budget = w.wait_budget > 0 ? w.wait_budget : OWAIT;
+    a.never = w.wait_budget < 0 ? -w.wait_budget : 0;
     // buffered epilogue when the group sums fit the scratch and no group needs a partial flush
     const int64_t segs = (a.kchunks + SEG - 1) / SEG;
     const size_t gneed = (size_t)batch * NSLICE * g.M * 2 * (size_t)g.N;

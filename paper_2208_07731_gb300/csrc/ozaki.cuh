@@ -17,6 +17,7 @@ struct OzWork {
     size_t cap_ma, cap_mb;           // capacity in rows
     int *gsum;                       // exact int32 group sums of a buffered product (or NULL)
     size_t cap_g;                    // capacity in ints
+    long long wait_budget;           // cycle budget of the pipeline waits (0: the default; < 0: test hook)
 };
 
 // Halves and rows needed for an M x N x K product (batch products).
@@ -29,6 +30,6 @@ bool oz_fits(const ZGemm &g, const OzWork &w);
 // C = alpha op(A) op(B) + beta C with the ZGemm conventions (strides, conj,
 // lower_only, kmode, k_to_m_end, batch); the result carries an error of the
 // order of an FP64 GEMM's (slices of 8 bits, 56 bits per operand, products of
-// slice pairs with s + t <= 8). Device errors (a bounded wait that gave up) go
-// to *err.
+// slice pairs with s + t <= 8). Device errors go to *err: 1 for a bounded wait
+// that gave up, 2 for an infinite or NaN operand entry (first error wins).
 isdf_status oz_zgemm(const ZGemm &g, const OzWork &w, int *err, cudaStream_t st);

@@ -299,6 +299,7 @@ isdf_status plan_compute(isdf_plan *p, const int64_t *idx, cudaStream_t st)
     const int n_mu = p->n_mu, n_phi = p->n_phi, n_psi = p->n_psi;
     const size_t nn = (size_t)n_mu * n_mu;
     ISDF_CUDA_TRY(cudaMemsetAsync(p->status, 0, sizeof(DeviceStatus), st));
+    if (p->oz_err) ISDF_CUDA_TRY(cudaMemsetAsync(p->oz_err, 0, sizeof(int), st));
     ISDF_CUDA_TRY(cudaMemcpyAsync(p->idx, idx, sizeof(int64_t) * n_mu, cudaMemcpyDeviceToDevice, st));
     ISDF_CUDA_TRY(cudaMemsetAsync(p->Mbar, 0, sizeof(double2) * nn, st));
     ISDF_CUDA_TRY(cudaMemsetAsync(p->gphi_mu, 0, sizeof(double2) * n_mu * n_phi, st));
@@ -306,11 +307,12 @@ isdf_status plan_compute(isdf_plan *p, const int64_t *idx, cudaStream_t st)
     // the orbitals' FP16 operands (mixed mode) do not depend on the points: prepared on a
     // third stream while this one runs the FP64 update
     const bool fork_aux = p->mode == ISDF_MIXED && p->aux;
+    StreamJoin aux_join;   // joins the aux stream back on any early return below
     if (fork_aux) {
         ISDF_CUDA_TRY(cudaEventRecord(p->ev_aux_fork, st));
         ISDF_CUDA_TRY(cudaStreamWaitEvent(p->aux, p->ev_aux_fork, 0));
+        aux_join.arm(st, p->aux, p->ev_aux_join);
         ISDF_TRY(mixed_prepare_orbitals(p, p->aux));
-        ISDF_CUDA_TRY(cudaEventRecord(p->ev_aux_join, p->aux));
     }
     // a7: Phi_mu = Phi[idx], Psi_mu = Psi[idx]  (Eq. Cmu)
     timer_start(p, 2, st);
@@ -357,7 +359,7 @@ isdf_status plan_compute(isdf_plan *p, const int64_t *idx, cudaStream_t st)
                               p));
     if (p->mode == ISDF_MIXED) {
         if (fork_aux)
-            ISDF_CUDA_TRY(cudaStreamWaitEvent(st, p->ev_aux_join, 0));
+            ISDF_CUDA_TRY(aux_join.join());
         else
             ISDF_TRY(mixed_prepare_orbitals(p, st));
         timer_start(p, 6, st);
@@ -792,12 +794,20 @@ extern "C" isdf_status isdf_plan_status(isdf_plan *p, int32_t *detail)
         if (!m && p->oz_err) {
             int e = 0;
             ISDF_CUDA_TRY(cudaMemcpy(&e, p->oz_err, sizeof(int), cudaMemcpyDeviceToHost));
-            if (e) m = ISDF_ERR_TIMEOUT;
+            if (e) m = e == 2 ? ISDF_ERR_NONFINITE : ISDF_ERR_TIMEOUT;
         }
         if (m && detail) *detail = -1;
         return (isdf_status)m;
     }
     return (isdf_status)h.code;
+}
+
+extern "C" isdf_status isdf_plan_set_wait_budget(isdf_plan *p, int64_t cycles)
+{
+    if (!p) return ISDF_ERR_INVALID_ARG;
+    p->wait_budget = (long long)cycles;
+    p->oz.wait_budget = p->wait_budget;
+    return ISDF_OK;
 }
 
 extern "C" isdf_status isdf_plan_copy_matrix(const isdf_plan *p, int32_t which, void *dst, void *stream)

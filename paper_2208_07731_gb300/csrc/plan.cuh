@@ -27,7 +27,8 @@ struct isdf_plan {
     MixedBuffers *mixed;                      // tensor-core path (ISDF_MIXED)
     int use_oz;                               // plan-update products on the tensor cores (exact slicing)
     OzWork oz;                                // their slice scratch
-    int *oz_err;                              // device flag: a bounded wait of that kernel gave up
+    int *oz_err;                              // device flag of those kernels: 1 a wait gave up, 2 non-finite input
+    long long wait_budget;                    // cycle budget of the tensor-core kernels' waits (0: default)
     cudaStream_t side;                        // look-ahead stream of the Cholesky factorisation
     cudaEvent_t ev_fork, ev_join;             // its fork / join points
     cudaStream_t aux;                         // orbital operand preparation, concurrent with a8-a9

@@ -118,6 +118,24 @@ def test_host_side_validation(lib):
     # empty grid is a no-op
     assert lib.isdf_cluster_residual(dummy, 4, 4, dummy, 4, 4, ctypes.c_int64(0), 0, lab, ix, 2, dummy, lab,
                                      None) == 0
+    # status of a K-means call and the wait budget need their objects
+    lib.isdf_kmeans_status.argtypes = [P, P]
+    lib.isdf_plan_set_wait_budget.argtypes = [P, ctypes.c_int64]
+    assert lib.isdf_kmeans_status(None, None) == 1
+    assert lib.isdf_plan_set_wait_budget(None, 100) == 1
+    # the allocation-free K-means checks its arguments like isdf_kmeans before the scratch size:
+    # an invalid call on a large grid is INVALID_ARG, a valid one beyond the fixed array UNSUPPORTED
+    I32 = ctypes.c_int32
+    lib.isdf_kmeans_noalloc.argtypes = [P, I32, I32, I32, P, I32, P, I32, I32, P, P, P, P, P, P]
+    big = (256, 256, 256)
+    assert lib.isdf_kmeans_noalloc(None, *big, cell, 64, dummy, 1, 0, dummy, None, None, None, None, None) == 1
+    assert lib.isdf_kmeans_noalloc(dummy, *big, cell, 64, None, 1, 0, dummy, None, None, None, None, None) == 1
+    assert lib.isdf_kmeans_noalloc(dummy, *big, bad_cell, 64, dummy, 1, 0, dummy, None, None, None, None,
+                                   None) == 1
+    assert lib.isdf_kmeans_noalloc(dummy, *big, cell, 64, dummy, 1, 8, dummy, None, None, None, None, None) == 1
+    assert lib.isdf_kmeans_noalloc(dummy, 4, 4, 4, cell, 65, dummy, 1, 0, dummy, None, None, None, None,
+                                   None) == 1
+    assert lib.isdf_kmeans_noalloc(dummy, *big, cell, 64, dummy, 1, 0, dummy, None, None, None, None, None) == 8
 
 
 def test_oracle_builds_and_loads():
