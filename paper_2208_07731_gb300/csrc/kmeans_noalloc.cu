@@ -10,8 +10,16 @@
 // exits, and the library never allocates it, grows it or frees it.
 //
 // Host code cannot use the array's name as a device address (in host code it
-// is a host-side stand-in), so the first call on each device, with that device
-// current, asks the runtime for the array's device address once and keeps it.
+// is a host-side stand-in), so the first call in each CUDA context, with that
+// context current, asks the runtime for the array's device address and keeps
+// it. The address belongs to the context that loaded the module: after
+// cudaDeviceReset, or under another context on the same device (a driver-API
+// caller's own context instead of the primary one), the array has a new
+// address, so the cache is keyed on the current context and looked up again
+// whenever the context differs.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <mutex>
 
 #include "common.cuh"
@@ -22,21 +30,46 @@ static __device__ __align__(256) unsigned char g_kmeans_scratch[ISDF_KMEANS_NOAL
 
 constexpr int kMaxDevices = 256;
 std::mutex g_lock;
-void *g_addr[kMaxDevices] = {};
+struct ScratchEntry {
+    CUcontext ctx;
+    void *addr;
+};
+ScratchEntry g_entry[kMaxDevices] = {};
 
-// device address of g_kmeans_scratch on the current device (set up once per device)
+// cuCtxGetCurrent through the runtime's driver entry-point query (no link against libcuda)
+CUresult current_context(CUcontext *ctx)
+{
+    static PFN_cuCtxGetCurrent_v4000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !p)
+            return CUDA_ERROR_NOT_FOUND;
+        fn = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(p);
+    }
+    return fn(ctx);
+}
+
+// device address of g_kmeans_scratch in the current context (looked up once per context)
 isdf_status scratch_address(void **out)
 {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return ISDF_ERR_CUDA;
     if (dev < 0 || dev >= kMaxDevices) return ISDF_ERR_UNSUPPORTED;
     std::lock_guard<std::mutex> guard(g_lock);
-    if (!g_addr[dev]) {
+    CUcontext ctx = nullptr;
+    if (current_context(&ctx) != CUDA_SUCCESS) return ISDF_ERR_CUDA;
+    if (!ctx || !g_entry[dev].addr || g_entry[dev].ctx != ctx) {
+        // with no context current yet, this runtime call makes the device's primary context
+        // current, and the context is read again below
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_kmeans_scratch) != cudaSuccess || !p) return ISDF_ERR_CUDA;
-        g_addr[dev] = p;
+        if (!ctx && (current_context(&ctx) != CUDA_SUCCESS || !ctx)) return ISDF_ERR_CUDA;
+        g_entry[dev].ctx = ctx;
+        g_entry[dev].addr = p;
     }
-    *out = g_addr[dev];
+    *out = g_entry[dev].addr;
     return ISDF_OK;
 }
 
@@ -47,6 +80,14 @@ extern "C" isdf_status isdf_kmeans_noalloc(const double *w, int32_t nx, int32_t 
                                            int64_t *idx, double *centroids, double *objective, int32_t *labels,
                                            int64_t *stats, void *stream)
 {
+    // the argument checks of isdf_kmeans first, so that an invalid call on a large grid is
+    // reported as ISDF_ERR_INVALID_ARG rather than as too large for the scratch array
+    if (nx < 1 || ny < 1 || nz < 1 || !cell || !w || !init_idx || !idx) return ISDF_ERR_INVALID_ARG;
+    const int64_t n_r = (int64_t)nx * ny * nz;
+    if (n_r >= ((int64_t)1 << 31)) return ISDF_ERR_UNSUPPORTED;
+    if (n_mu < 1 || n_mu > n_r || max_iter < 0 || (flags & ~ISDF_KMEANS_EARLY_STOP)) return ISDF_ERR_INVALID_ARG;
+    for (int k = 0; k < 3; ++k)
+        if (!(cell[k] > 0.0) || cell[k] > 1e300) return ISDF_ERR_INVALID_ARG;
     size_t need = 0;
     isdf_status s = isdf_kmeans_workspace(nx, ny, nz, n_mu, &need);
     if (s != ISDF_OK) return s;

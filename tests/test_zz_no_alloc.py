@@ -34,12 +34,12 @@ def _p(t):
     return ctypes.c_void_p(0 if t is None else t.data_ptr())
 
 
-def noalloc(isdf, w, shape, cell, n_mu, init, iters, flags=0):
+def noalloc(isdf, w, shape, cell, n_mu, init, iters, flags=0, labels=True, objective=True):
     n_r = int(np.prod(shape))
     idx = torch.full((n_mu,), -7, dtype=torch.int64, device=DEV)
     cen = torch.full((n_mu, 3), -1.0, dtype=torch.float64, device=DEV)
-    obj = torch.full((iters + 1,), -1.0, dtype=torch.float64, device=DEV)
-    lab = torch.full((n_r,), -3, dtype=torch.int32, device=DEV)
+    obj = torch.full((iters + 1,), -1.0, dtype=torch.float64, device=DEV) if objective else None
+    lab = torch.full((n_r,), -3, dtype=torch.int32, device=DEV) if labels else None
     stats = torch.zeros(4, dtype=torch.int64, device=DEV)
     cellh = (ctypes.c_double * 3)(*cell)
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
@@ -79,8 +79,38 @@ def test_noalloc_repeated_identical_calls(isdf):
         assert torch.equal(a[k], b[k]), k
 
 
+def test_noalloc_after_a_failed_call_and_without_labels(isdf):
+    # a call that leaves an error flag in the shared array (an init index outside the grid: every
+    # idx -1, stats[2] = -2), then a good call that must equal isdf_kmeans exactly; then a call with
+    # labels and objective NULL, where the labels live in the shared array too
+    shape, cell, n_mu, iters = (16, 12, 10), (8.0, 6.0, 5.0), 48, 15
+    w, init = _case(21, shape, n_mu)
+    bad = init.clone()
+    bad[3] = int(np.prod(shape)) + 5
+    rc, got = noalloc(isdf, w, shape, cell, n_mu, bad, iters)
+    torch.cuda.synchronize()
+    assert rc == 0 and bool((got["idx"] == -1).all()) and got["stats"][2].item() == -2
+    ref = isdf.kmeans(w, shape, cell, n_mu, init, iters)
+    rc, got = noalloc(isdf, w, shape, cell, n_mu, init, iters)
+    torch.cuda.synchronize()
+    assert rc == 0
+    for k in ("idx", "centroids", "objective", "labels", "stats"):
+        assert torch.equal(got[k], ref[k]), k
+    rc, got = noalloc(isdf, w, shape, cell, n_mu, init, iters, labels=False, objective=False)
+    torch.cuda.synchronize()
+    assert rc == 0
+    for k in ("idx", "centroids", "stats"):
+        assert torch.equal(got[k], ref[k]), k
+
+
 def test_noalloc_rejects_problems_beyond_the_scratch_size(isdf):
-    # 256^3 points need far more than the fixed 32 MiB array: refused before any launch
-    rc, got = noalloc(isdf, None, (256, 256, 256), (10.0, 10.0, 10.0), 64, None, 1)
+    # 256^3 points need far more than the fixed 32 MiB array: refused before any launch. The
+    # pointers are valid, so the refusal is the size check and not an argument error
+    w = torch.zeros(8, dtype=torch.float64, device=DEV)
+    init = torch.arange(64, dtype=torch.int64, device=DEV)
+    rc, got = noalloc(isdf, w, (256, 256, 256), (10.0, 10.0, 10.0), 64, init, 1)
     assert rc == 8  # ISDF_ERR_UNSUPPORTED
     assert bool((got["idx"] == -7).all())
+    # an invalid call (no weights) is reported as such first
+    rc, _ = noalloc(isdf, None, (256, 256, 256), (10.0, 10.0, 10.0), 64, init, 1)
+    assert rc == 1  # ISDF_ERR_INVALID_ARG
