@@ -15,7 +15,7 @@ closed forms, brute force, explicit formation of Z, textbook least squares,
 invariances and finite differences. No function is parity-unpinned.
 """
 from .oracle import (  # noqa: F401
-    load, weights, kmeans, fixed_point_scale, gather, form_M, cholesky, gram_hadamard,
+    load, weights, kmeans, kmeans_update, kmeans_assign, kmeans_snap, fixed_point_scale, gather, form_M, cholesky, gram_hadamard,
     theta_rows, fit_theta, surrogate_loss, surrogate_grad_theta, theta_backward,
     grid_coords, explicit_Z, isdf_error, cluster_residual,
     kernel_hat, poisson, exchange_apply, exchange_direct, qrcp_sketch, qrcp_points,

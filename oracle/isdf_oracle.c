@@ -214,3 +214,121 @@ int oracle_fixed_point_scale(int64_t n_r, double wmax, const double *cell)
     frexp(lmax, &el);
     return 126 - (bits_of((uint64_t)n_r) + ew + el);
 }
+
+/*
+ * Single steps of Algorithm 1, for checking a long K-means run one step at a
+ * time (a lock-step check) without repeating all its passes on the CPU.
+ * They restate the same formulas as oracle_kmeans above.
+ */
+
+/* fixed-point exponent of the centroid sums for these weights (as in oracle_kmeans) */
+static int kmeans_scale(const double *w, int64_t n_r, const double *cell, int *s_out)
+{
+    double wmax = 0.0;
+    for (int64_t r = 0; r < n_r; ++r) {
+        if (!(w[r] >= 0.0) || isinf(w[r])) return -1;
+        if (w[r] > wmax) wmax = w[r];
+    }
+    *s_out = oracle_fixed_point_scale(n_r, wmax, cell);
+    return *s_out < 0 ? -1 : 0;
+}
+
+/*
+ * One centroid update, Eq. r_k: c_out[mu] = sum_{lab(r)=mu} w x_r / sum w, with
+ * each FP64 product w*x taken as floor(w*x*2^s) in 128 bits, the integer sums
+ * rounded to FP64, one IEEE division; a cluster without weight keeps
+ * c_in[mu]. labels: n_r entries in [0, n_mu). Returns 0, or -1 for invalid
+ * input.
+ */
+int oracle_kmeans_update(const double *w, int32_t nx, int32_t ny, int32_t nz, const double *cell, int32_t n_mu,
+                         const int32_t *labels, const double *c_in, double *c_out)
+{
+    const int64_t n_r = (int64_t)nx * ny * nz;
+    int s = 0;
+    if (n_mu <= 0 || kmeans_scale(w, n_r, cell, &s) < 0) return -1;
+    const double hx = cell[0] / nx, hy = cell[1] / ny, hz = cell[2] / nz;
+    u128 *S = (u128 *)calloc((size_t)4 * n_mu, sizeof(u128));
+    for (int64_t r = 0; r < n_r; ++r) {
+        const int32_t m = labels[r];
+        if (m < 0 || m >= n_mu) { free(S); return -1; }
+        int64_t ix = r / ((int64_t)ny * nz), iy = (r / nz) % ny, iz = r % nz;
+        double x = (double)ix * hx, y = (double)iy * hy, z = (double)iz * hz;
+        u128 *q = S + 4 * (int64_t)m;
+        q[0] += (u128)ldexp(w[r], s);
+        q[1] += (u128)ldexp(w[r] * x, s);
+        q[2] += (u128)ldexp(w[r] * y, s);
+        q[3] += (u128)ldexp(w[r] * z, s);
+    }
+    for (int32_t m = 0; m < n_mu; ++m) {
+        const u128 *q = S + 4 * (int64_t)m;
+        if (q[0] == 0) {
+            c_out[3 * m + 0] = c_in[3 * m + 0];
+            c_out[3 * m + 1] = c_in[3 * m + 1];
+            c_out[3 * m + 2] = c_in[3 * m + 2];
+            continue;
+        }
+        double sw = (double)q[0];
+        c_out[3 * m + 0] = (double)q[1] / sw;
+        c_out[3 * m + 1] = (double)q[2] / sw;
+        c_out[3 * m + 2] = (double)q[3] / sw;
+    }
+    free(S);
+    return 0;
+}
+
+/*
+ * Assignment, Eq. opt (second form), of the listed grid points only:
+ * labels[i] = argmin_mu |x_{points[i]} - c_mu|^2 (lowest mu on ties) and
+ * dist[i] its squared distance (nullable). Brute force over all centroids.
+ */
+int oracle_kmeans_assign(int32_t nx, int32_t ny, int32_t nz, const double *cell, int32_t n_mu,
+                         const double *centroids, const int64_t *points, int64_t count, int32_t *labels,
+                         double *dist)
+{
+    const int64_t n_r = (int64_t)nx * ny * nz;
+    if (n_mu <= 0) return -1;
+    const double hx = cell[0] / nx, hy = cell[1] / ny, hz = cell[2] / nz;
+    int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
+    for (int64_t i = 0; i < count; ++i) {
+        const int64_t r = points[i];
+        if (r < 0 || r >= n_r) { bad |= 1; continue; }
+        int64_t ix = r / ((int64_t)ny * nz), iy = (r / nz) % ny, iz = r % nz;
+        double x = (double)ix * hx, y = (double)iy * hy, z = (double)iz * hz;
+        double best = INFINITY;
+        int32_t arg = 0;
+        for (int32_t m = 0; m < n_mu; ++m) {
+            double d = dist2(x, y, z, centroids + 3 * m);
+            if (d < best) { best = d; arg = m; }
+        }
+        labels[i] = arg;
+        if (dist) dist[i] = best;
+    }
+    return bad ? -1 : 0;
+}
+
+/*
+ * Snap, the last step of Algorithm 1 (reading: each centroid's nearest member):
+ * idx[mu] = the grid point r with labels[r] = mu nearest to c_mu, ties to the
+ * lowest r, or -1 when the cluster has no member. Returns the number of empty
+ * clusters, or -1 for invalid labels.
+ */
+int oracle_kmeans_snap(int32_t nx, int32_t ny, int32_t nz, const double *cell, int32_t n_mu,
+                       const double *centroids, const int32_t *labels, int64_t *idx)
+{
+    const int64_t n_r = (int64_t)nx * ny * nz;
+    const double hx = cell[0] / nx, hy = cell[1] / ny, hz = cell[2] / nz;
+    double *best = (double *)malloc(sizeof(double) * n_mu);
+    for (int32_t m = 0; m < n_mu; ++m) { best[m] = INFINITY; idx[m] = -1; }
+    for (int64_t r = 0; r < n_r; ++r) {
+        const int32_t m = labels[r];
+        if (m < 0 || m >= n_mu) { free(best); return -1; }
+        int64_t ix = r / ((int64_t)ny * nz), iy = (r / nz) % ny, iz = r % nz;
+        double d = dist2((double)ix * hx, (double)iy * hy, (double)iz * hz, centroids + 3 * m);
+        if (d < best[m]) { best[m] = d; idx[m] = r; }
+    }
+    int empty = 0;
+    for (int32_t m = 0; m < n_mu; ++m) if (idx[m] < 0) ++empty;
+    free(best);
+    return empty;
+}

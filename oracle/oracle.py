@@ -39,6 +39,10 @@ def load():
         lib.oracle_kmeans.argtypes = [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, ctypes.c_int32, P,
                                       ctypes.c_int32, ctypes.c_int32, P, P, P, P, P, P]
         lib.oracle_fixed_point_scale.argtypes = [ctypes.c_int64, ctypes.c_double, P]
+        I32, I64 = ctypes.c_int32, ctypes.c_int64
+        lib.oracle_kmeans_update.argtypes = [P, I32, I32, I32, P, I32, P, P, P]
+        lib.oracle_kmeans_assign.argtypes = [I32, I32, I32, P, I32, P, P, I64, P, P]
+        lib.oracle_kmeans_snap.argtypes = [I32, I32, I32, P, I32, P, P, P]
         _lib = lib
     return _lib
 
@@ -94,6 +98,50 @@ def kmeans(w, shape, cell, n_mu: int, init_idx, max_iter: int, early_stop: bool 
         raise ValueError("oracle_kmeans: invalid arguments")
     return {"idx": idx, "centroids": cen, "objective": obj, "n_iter": int(nit[0]),
             "near_ties": int(ties[0]), "labels": lab, "empty": int(rc)}
+
+
+def kmeans_update(w, shape, cell, labels, centroids) -> np.ndarray:
+    """One centroid update of Algorithm 1 (Eq. r_k, exact 128-bit sums) from given
+    labels; clusters without weight keep their centroid. Returns n_mu x 3."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    nx, ny, nz = (int(v) for v in shape)
+    cell = np.ascontiguousarray(cell, dtype=np.float64)
+    lab = np.ascontiguousarray(labels, dtype=np.int32)
+    c_in = np.ascontiguousarray(centroids, dtype=np.float64)
+    n_mu = c_in.shape[0]
+    out = np.empty_like(c_in)
+    if load().oracle_kmeans_update(_ptr(w), nx, ny, nz, _ptr(cell), n_mu, _ptr(lab), _ptr(c_in), _ptr(out)) != 0:
+        raise ValueError("oracle_kmeans_update: invalid arguments")
+    return out
+
+
+def kmeans_assign(shape, cell, centroids, points) -> tuple:
+    """Assignment (Eq. opt, second form) of the listed grid points by brute force:
+    (labels, squared distances), lowest mu on ties."""
+    nx, ny, nz = (int(v) for v in shape)
+    cell = np.ascontiguousarray(cell, dtype=np.float64)
+    c = np.ascontiguousarray(centroids, dtype=np.float64)
+    pts = np.ascontiguousarray(points, dtype=np.int64)
+    lab = np.empty(pts.shape[0], np.int32)
+    dist = np.empty(pts.shape[0], np.float64)
+    if load().oracle_kmeans_assign(nx, ny, nz, _ptr(cell), c.shape[0], _ptr(c), _ptr(pts), pts.shape[0], _ptr(lab),
+                                   _ptr(dist)) != 0:
+        raise ValueError("oracle_kmeans_assign: invalid arguments")
+    return lab, dist
+
+
+def kmeans_snap(shape, cell, centroids, labels) -> tuple:
+    """Snap (last step of Algorithm 1): each centroid's nearest member, lowest r on
+    ties, -1 for an empty cluster. Returns (idx, empty count)."""
+    nx, ny, nz = (int(v) for v in shape)
+    cell = np.ascontiguousarray(cell, dtype=np.float64)
+    c = np.ascontiguousarray(centroids, dtype=np.float64)
+    lab = np.ascontiguousarray(labels, dtype=np.int32)
+    idx = np.empty(c.shape[0], np.int64)
+    rc = load().oracle_kmeans_snap(nx, ny, nz, _ptr(cell), c.shape[0], _ptr(c), _ptr(lab), _ptr(idx))
+    if rc < 0:
+        raise ValueError("oracle_kmeans_snap: invalid labels")
+    return idx, int(rc)
 
 
 def grid_coords(shape, cell) -> np.ndarray:

@@ -5,8 +5,11 @@ K-means bit-exact against the oracle, mixed Theta on sampled rows <= 1e-5.
 adjoint (72^3, 192 orbitals, 1536 points fixed from a prior K-means): the
 FP64 and tensor-core adjoints of the exchange-like surrogate against the
 oracle gradient, and the FP64 adjoint against central finite differences on
-32 seeded directions scaled to the orbital norms (h = 1e-5 within 1e-6).
-silica (128^3, 1024 orbitals, 4096 points): K-means checked through
+32 seeded directions scaled to the orbital norms (h = 1e-6 within 1e-6, the
+difference of the two losses formed without cancellation).
+silica (128^3, 1024 orbitals, 4096 points): K-means checked step by step
+against the oracle (lock-step: one exact update from the GPU's labels, the
+brute-force assignment of a 131,072-point sample, the final snap) and through
 properties that hold at any size (sampled labels are the nearest centroids
 under the FP64 formula, every cluster is non-empty, snapped points are
 distinct members nearest to their centroids), and
@@ -98,8 +101,10 @@ def test_adjoint_config_against_oracle_gradient(isdf):
 def test_adjoint_config_finite_differences(isdf):
     w, phi, psi, idx, _ = _adjoint_setup(isdf)
     # a Hermitian positive-definite K = c I + U U^H with U of rank 32 (passed to the adjoint as a
-    # dense matrix), so that each FD loss costs one Theta fit: with P = Theta conj(U),
-    # sum conj(Theta) o (Theta K^T) = c ||Theta||^2 + ||P||^2
+    # dense matrix): per grid row the loss is q(t) = c |t|^2 + |U^H t|^2, and the central difference
+    # q(t+) - q(t-) = c Re<t+ - t-, t+ + t-> + Re<U^H (t+ - t-), U^H (t+ + t-)> is formed block by block
+    # from the two FP64 fits, without subtracting two large sums (whose rounding would be ~3e-6 of the
+    # derivative at h = 1e-6 on 5.7e8 terms)
     rng = np.random.default_rng(3000 + w.seed)
     Qk, _ = np.linalg.qr(rng.standard_normal((w.n_mu, 32)) + 1j * rng.standard_normal((w.n_mu, 32)))
     U = Qk * np.sqrt(rng.uniform(1.0, 9.0, size=32))[None, :]
@@ -110,27 +115,47 @@ def test_adjoint_config_finite_differences(isdf):
     Ucd = torch.from_numpy(U.conj()).to(DEV)
     P = phi.to(torch.complex128)
     Q = psi.to(torch.complex128)
-    plan = isdf.Plan(P, Q, idx, mode="fp64", max_rows=131072)
-    loss, gphi, gpsi = isdf.surrogate_loss_and_grad(plan, Kd, w.dV, block=131072)
+    B = 131072
+    plan = isdf.Plan(P, Q, idx, mode="fp64", max_rows=B)
+    loss, gphi, gpsi = isdf.surrogate_loss_and_grad(plan, Kd, w.dV, block=B)
     plan.check()
-    theta = torch.empty((w.n_r, w.n_mu), dtype=torch.complex128, device=DEV)
-    Pp, Qp = torch.empty_like(P), torch.empty_like(Q)
-    fplan = isdf.Plan(Pp.copy_(P), Qp.copy_(Q), idx, mode="fp64", max_rows=131072)
+    plan.close()
+    bufs = [torch.empty_like(P), torch.empty_like(Q), torch.empty_like(P), torch.empty_like(Q)]
+    plus = isdf.Plan(bufs[0].copy_(P), bufs[1].copy_(Q), idx, mode="fp64", max_rows=B)
+    minus = isdf.Plan(bufs[2].copy_(P), bufs[3].copy_(Q), idx, mode="fp64", max_rows=B)
+    tp = torch.empty((B, w.n_mu), dtype=torch.complex128, device=DEV)
+    tm = torch.empty_like(tp)
 
-    def loss_at(sign, Dp, Dq, h):
-        Pp.copy_(P).add_(Dp, alpha=sign * h)
-        Qp.copy_(Q).add_(Dq, alpha=sign * h)
-        fplan.update(idx)
-        fplan.fit_theta(out=theta)
-        return w.dV * (c * torch.linalg.vector_norm(theta) ** 2 +
-                       torch.linalg.vector_norm(theta @ Ucd) ** 2).item()
+    # the loss at the plus plan's orbitals, from one fit
+    def loss_plus():
+        plus.update(idx)
+        tot = 0.0
+        for r0 in range(0, w.n_r, B):
+            n = min(B, w.n_r - r0)
+            plus.fit_theta(r0, n, out=tp[:n])
+            tot += (c * torch.linalg.vector_norm(tp[:n]) ** 2 + torch.linalg.vector_norm(tp[:n] @ Ucd) ** 2).item()
+        return w.dV * tot
 
-    assert abs(loss_at(0, P, Q, 0.0) - loss.item()) < 1e-10 * abs(loss.item())
-    # FP64 rounding of the loss divided by 2h is ~3e-6 of the directional derivative at
-    # h = 1e-6 on this size (5.7e8 terms): the 1e-6 check uses h = 1e-5, whose
-    # truncation error is ~1e-10 (h = 1e-6 is checked on the small workload)
+    def loss_difference(Dp, Dq, h):
+        bufs[0].copy_(P).add_(Dp, alpha=h)
+        bufs[1].copy_(Q).add_(Dq, alpha=h)
+        bufs[2].copy_(P).add_(Dp, alpha=-h)
+        bufs[3].copy_(Q).add_(Dq, alpha=-h)
+        plus.update(idx)
+        minus.update(idx)
+        tot = 0.0
+        for r0 in range(0, w.n_r, B):
+            n = min(B, w.n_r - r0)
+            plus.fit_theta(r0, n, out=tp[:n])
+            minus.fit_theta(r0, n, out=tm[:n])
+            d, s = tp[:n] - tm[:n], tp[:n] + tm[:n]
+            tot += (c * torch.real(torch.vdot(d.flatten(), s.flatten())) +
+                    torch.real(torch.vdot((d @ Ucd).flatten(), (s @ Ucd).flatten()))).item()
+        return w.dV * tot
+
+    assert abs(loss_plus() - loss.item()) < 1e-10 * abs(loss.item())
     gen = torch.Generator(device=DEV).manual_seed(4242)
-    h = 1e-5
+    h = 1e-6
     for d in range(32):
         Dp = torch.randn(P.shape, dtype=torch.complex128, device=DEV, generator=gen)
         Dq = torch.randn(Q.shape, dtype=torch.complex128, device=DEV, generator=gen)
@@ -138,9 +163,41 @@ def test_adjoint_config_finite_differences(isdf):
         Dp *= torch.linalg.vector_norm(P) / torch.linalg.vector_norm(Dp)
         Dq *= torch.linalg.vector_norm(Q) / torch.linalg.vector_norm(Dq)
         an = torch.real(torch.vdot(gphi.flatten(), Dp.flatten()) + torch.vdot(gpsi.flatten(), Dq.flatten())).item()
-        fd = (loss_at(+1, Dp, Dq, h) - loss_at(-1, Dp, Dq, h)) / (2 * h)
+        fd = loss_difference(Dp, Dq, h) / (2 * h)
         assert abs(fd - an) <= 1e-6 * abs(an), (d, fd, an)
-    fplan.check()
+    plus.check()
+    minus.check()
+
+
+def test_silica_kmeans_lock_step_against_oracle(isdf):
+    """The 128^3 x 4096 K-means checked step by step against the oracle's single steps of
+    Algorithm 1: for t in {0, 1, 50, T-1}, the GPU's centroids after t + 1 updates equal the
+    oracle's update (exact 128-bit sums, Eq. r_k) applied to the GPU's labels and centroids after t
+    updates, and those labels equal the oracle's brute-force assignment (Eq. opt) of a seeded
+    131,072-point sample; the final snap equals the oracle's nearest members."""
+    w = W.WORKLOADS["silica"]
+    phi, psi = _gpu_pair(w)
+    wt = isdf.weights(phi, psi)
+    shape, cell = (w.n,) * 3, (w.L,) * 3
+    wt_h = wt.cpu().numpy()
+    # the weights on a row sample (the full grid is checked bit for bit on the waterbox workload)
+    rs = torch.from_numpy(W.subsample_rows(w.n_r, 8192, 7)).to(DEV)
+    assert np.array_equal(wt_h[rs.cpu().numpy()], O.weights(phi[rs].cpu().numpy(), psi[rs].cpu().numpy()))
+    del phi, psi
+    init = torch.from_numpy(W.init_indices(wt_h, w.n_mu, 1000 + w.seed))
+    sample = W.subsample_rows(w.n_r, 131072, 2000 + w.seed)
+    for t in (0, 1, 50, w.iters - 1):
+        a = isdf.kmeans(wt, shape, cell, w.n_mu, init, t, objective=False)
+        b = isdf.kmeans(wt, shape, cell, w.n_mu, init, t + 1, labels=False, objective=False)
+        c_t = a["centroids"].cpu().numpy()
+        lab_t = a["labels"].cpu().numpy()
+        assert np.array_equal(b["centroids"].cpu().numpy(), O.kmeans_update(wt_h, shape, cell, lab_t, c_t)), t
+        lab_s, _ = O.kmeans_assign(shape, cell, c_t, sample)
+        assert np.array_equal(lab_t[sample], lab_s), t
+    km = isdf.kmeans(wt, shape, cell, w.n_mu, init, w.iters, objective=False)
+    idx_ref, empty = O.kmeans_snap(shape, cell, km["centroids"].cpu().numpy(), km["labels"].cpu().numpy())
+    assert empty == 0 and np.array_equal(km["idx"].cpu().numpy(), idx_ref)
+    assert isdf.kmeans_status(km) == 0
 
 
 def test_silica_kmeans_properties_and_blocked_mixed_theta(isdf):

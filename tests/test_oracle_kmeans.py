@@ -152,3 +152,61 @@ def test_invalid_arguments():
         O.kmeans(np.array([1.0, -1.0]), (2, 1, 1), [1.0, 1.0, 1.0], 1, np.array([0]), 1)
     with pytest.raises(ValueError):
         O.kmeans(np.array([1.0, 1.0]), (2, 1, 1), [1.0, 1.0, 1.0], 1, np.array([5]), 1)
+
+
+# ---------------------------------------------------------------- single steps (lock-step checks)
+def test_single_steps_against_rational_lloyd():
+    # the one-step functions restate Algorithm 1's steps: one update from the exact labels of pass t
+    # gives the exact rational centroids of pass t + 1 (dyadic inputs), the assignment of every point
+    # gives the rational labels, and the snap gives each cluster's nearest member
+    rng = np.random.default_rng(9)
+    shape = (4, 3, 5)
+    h = Fraction(1, 2)
+    cell = [2.0, 1.5, 2.5]
+    wts = rng.integers(1, 64, size=60) / 8.0
+    init = np.array([2, 19, 30, 47, 55], dtype=np.int64)
+    for t in range(4):
+        lab_t, cen_t = _rational_lloyd(wts, shape, h, init, t)
+        _, cen_t1 = _rational_lloyd(wts, shape, h, init, t + 1)
+        c_t = np.array([[float(c) for c in cc] for cc in cen_t])
+        c_t1 = np.array([[float(c) for c in cc] for cc in cen_t1])
+        got = O.kmeans_update(wts, shape, cell, np.array(lab_t), c_t)
+        assert np.array_equal(got, c_t1), t
+        lab, dist = O.kmeans_assign(shape, cell, c_t, np.arange(60))
+        assert list(lab) == lab_t
+        pts = O.grid_coords(shape, cell)
+        assert np.array_equal(dist, ((pts - c_t[lab]) ** 2).sum(1))
+
+
+def test_single_steps_reproduce_full_run():
+    w = W.small_workload(n=10, n_orb=3, n_mu=24, iters=8, seed=3)
+    phi, psi = W.make_pair(w)
+    wt = O.weights(phi.numpy(), psi.numpy())
+    shape, cell = (w.n,) * 3, (w.L,) * 3
+    init = W.init_indices(wt, w.n_mu, 11)
+    x = O.grid_coords(shape, cell)
+    c = x[init]
+    for t in range(6):
+        ref = O.kmeans(wt, shape, cell, w.n_mu, init, t)
+        assert np.array_equal(ref["centroids"], c), t
+        lab, _ = O.kmeans_assign(shape, cell, c, np.arange(w.n_r))
+        assert np.array_equal(lab, ref["labels"]), t
+        idx, empty = O.kmeans_snap(shape, cell, c, lab)
+        assert np.array_equal(idx, ref["idx"]) and empty == ref["empty"]
+        c = O.kmeans_update(wt, shape, cell, lab, c)
+
+
+def test_single_update_weighted_mean_and_empty_cluster():
+    # one cluster holding every point: the update is the weighted mean (closed form); a label that no
+    # point carries keeps its centroid, and the snap reports that cluster empty
+    rng = np.random.default_rng(4)
+    shape, cell = (5, 4, 6), [2.5, 2.0, 3.0]
+    w = rng.random(120)
+    x = O.grid_coords(shape, cell)
+    c_in = np.array([[0.1, 0.2, 0.3], [9.0, 9.0, 9.0]])
+    got = O.kmeans_update(w, shape, cell, np.zeros(120, np.int32), c_in)
+    exp = (w[:, None] * x).sum(0) / w.sum()
+    assert np.allclose(got[0], exp, rtol=1e-13, atol=0) and np.array_equal(got[1], c_in[1])
+    idx, empty = O.kmeans_snap(shape, cell, got, np.zeros(120, np.int32))
+    assert empty == 1 and idx[1] == -1
+    assert idx[0] == int(np.argmin(((x - got[0]) ** 2).sum(1)))
