@@ -10,6 +10,7 @@ import concurrent.futures as cf
 import glob
 import os
 import subprocess
+import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
@@ -37,11 +38,29 @@ def _deps_mtime() -> float:
     return max(os.path.getmtime(f) for f in files)
 
 
+STAMP = LIB + ".stamp"
+
+
+def _toolchain(nvcc: str) -> str:
+    """What the library was built with: nvcc's version line, the host machine and the flags. A library
+    built elsewhere (another toolchain or CPU architecture) is rebuilt, not reused."""
+    try:
+        ver = subprocess.run([nvcc, "--version"], capture_output=True, text=True).stdout.strip().splitlines()[-1]
+    except Exception:
+        ver = "unknown"
+    return "|".join([ver, os.uname().machine, " ".join(ARCH + FLAGS)])
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime():
+    """Compile libisdf.so unless an up-to-date one built by this toolchain on this machine type exists.
+    Reports on stderr which of the two happened."""
+    nvcc = _nvcc()
+    tool = _toolchain(nvcc)
+    stamp = open(STAMP).read() if os.path.exists(STAMP) else ""
+    if (not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime() and stamp == tool):
+        print(f"libisdf: reusing {LIB} (sources unchanged, same toolchain)", file=sys.stderr)
         return LIB
     os.makedirs(OBJDIR, exist_ok=True)
-    nvcc = _nvcc()
 
     def compile_one(src):
         obj = os.path.join(OBJDIR, os.path.basename(src) + ".o")
@@ -61,6 +80,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as f:
+        f.write(tool)
+    print(f"libisdf: compiled {len(objs)} sources into {LIB}", file=sys.stderr)
     return LIB
 
 
