@@ -88,8 +88,15 @@ typedef enum { ISDF_FP64 = 0, ISDF_MIXED = 1 } isdf_mode;
  *       alpha = 2 is SSM (the paper's choice); 1, 3, 4 are SM, SCM, SQM.
  *   kind ISDF_W_PSM (Eq. weight function):   w(r) = (sum_i |phi_i(r)|^2)(sum_j |psi_j(r)|^2)
  *       (alpha is ignored).
- * Each sum runs over the columns in ascending order with IEEE FP64 operations,
- * |z|^2 = re*re + im*im; alpha = 1, 3, 4 use sqrt and products, other alpha pow.
+ * Each sum is the exact sum of its terms, rounded once to FP64 (so it does not
+ * depend on summation order): for alpha = 2 the terms are the exact squares of
+ * the real components x = Re z, Im z, truncated 2^-110 below 2^(2E) with E the
+ * largest floor(log2|x|) of the sum's components (the result is the correctly
+ * rounded sum unless it lies within ~2^-96 of a rounding boundary); for
+ * alpha != 2 the terms are |z|^alpha formed in FP64 (m = re*re + im*im, each
+ * operation rounded; sqrt and products for alpha = 1, 3, 4, pow otherwise),
+ * truncated 2^-110 below the largest term. PSM rounds each of its two sums
+ * and multiplies once. Results in FP64's subnormal range are rounded twice.
  * phi, psi: dtype (ISDF_C128 or ISDF_C64) arrays of n_r rows; ld >= n.
  * w: n_r doubles (output; with ISDF_W_ACCUMULATE OR-ed into kind, w(r) is
  * replaced by fl(w(r) + the pair's weight), so B calls in order b = 0..B-1

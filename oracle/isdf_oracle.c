@@ -19,39 +19,116 @@
 typedef unsigned __int128 u128;
 
 /* |z|^alpha for z = re + i im, via m = |z|^2 = re*re + im*im (Eq. weight
- * function 2). The four values of alpha the paper studies (SM, SSM, SCM, SQM:
- * alpha = 1, 2, 3, 4) use sqrt and products only; any other alpha uses pow. */
+ * function 2), for alpha != 2. The values of alpha the paper studies besides
+ * 2 (SM, SCM, SQM: alpha = 1, 3, 4) use sqrt and products only; any other
+ * alpha uses pow. */
 static double modpow(double re, double im, double alpha)
 {
     double m = re * re;
     m = m + im * im;
-    if (alpha == 2.0) return m;
     if (alpha == 1.0) return sqrt(m);
     if (alpha == 3.0) return m * sqrt(m);
     if (alpha == 4.0) return m * m;
     return pow(m, 0.5 * alpha);
 }
 
+/* floor(log2|x|) for x != 0 */
+static int log2_floor(double x)
+{
+    int e = 0;
+    frexp(x, &e);
+    return e - 1;
+}
+
+/* round-to-nearest-even of an unsigned 128-bit integer, times 2^scale */
+static double u128_scaled(u128 acc, int scale)
+{
+    return ldexp((double)acc, scale);
+}
+
+/*
+ * Exact sum of the squared real components x = Re z, Im z of the n columns of
+ * one or two rows (a, na) and (b, nb): every x^2 is exact as a rational, the
+ * row's window top is E = max floor(log2|x|) over its non-zero components, and
+ *     sum = RN( sum_x floor(x^2 2^(110 - 2E)) ) * 2^(2E - 110),
+ * i.e. the squares are truncated 2^-110 below 2^(2E) (at most 2^14 of them,
+ * so the integer sum stays below 2^127), summed exactly, and rounded once.
+ * Each x = m 2^(e - 53) with an integer m < 2^53 (frexp), so x^2 = m^2 2^(2e-106)
+ * and the term is floor(m^2 2^(2e + 4 - 2E)). Returns 0 for an all-zero row.
+ */
+static double exact_square_sum(const double *a, int32_t na, const double *b, int32_t nb)
+{
+    int E = -100000;
+    for (int32_t i = 0; i < 2 * na; ++i) if (a[i] != 0.0 && log2_floor(a[i]) > E) E = log2_floor(a[i]);
+    for (int32_t j = 0; j < 2 * nb; ++j) if (b[j] != 0.0 && log2_floor(b[j]) > E) E = log2_floor(b[j]);
+    if (E == -100000) return 0.0;
+    u128 acc = 0;
+    for (int32_t k = 0; k < 2 * (na + nb); ++k) {
+        const double x = k < 2 * na ? a[k] : b[k - 2 * na];
+        if (x == 0.0) continue;
+        int e = 0;
+        const double f = frexp(fabs(x), &e);
+        const u128 m = (u128)(uint64_t)ldexp(f, 53);      /* |x| = m 2^(e - 53), m < 2^53 exact */
+        const int sh = 2 * e + 4 - 2 * E;                   /* <= 6 */
+        const u128 sq = m * m;
+        if (sh >= 0) acc += sq << sh;
+        else if (sh > -128) acc += sq >> (-sh);
+    }
+    return u128_scaled(acc, 2 * E - 110);
+}
+
+/*
+ * Exact sum of non-negative FP64 terms t_k: window top E = max floor(log2 t),
+ *     sum = RN( sum_k floor(t_k 2^(110 - E)) ) * 2^(E - 110)
+ * (at most 2^13 terms, each below 2^111, so the integer sum stays below 2^127).
+ */
+static double exact_term_sum(const double *t, int64_t n)
+{
+    int E = -100000;
+    for (int64_t k = 0; k < n; ++k) if (t[k] != 0.0 && log2_floor(t[k]) > E) E = log2_floor(t[k]);
+    if (E == -100000) return 0.0;
+    u128 acc = 0;
+    for (int64_t k = 0; k < n; ++k) acc += (u128)ldexp(t[k], 110 - E);
+    return u128_scaled(acc, E - 110);
+}
+
 /*
  * Weight function, Sec. 2.2.
  *   kind 0 (SSM family, Eq. weight function 2): w(r) = sum_i |phi_i(r)|^a + sum_j |psi_j(r)|^a
  *   kind 1 (PSM, Eq. weight function):          w(r) = (sum_i |phi_i(r)|^2)(sum_j |psi_j(r)|^2)
- * Each sum runs over all columns of its orbital set in ascending order,
- * left to right. phi, psi: interleaved complex128, row r at phi + 2*r*ld.
+ * Each sum runs over all columns of its orbital set(s) and is the exact sum of
+ * its terms rounded once (the reading of these sums used on both sides; any
+ * summation order gives the same bits):
+ *   alpha = 2: the terms are the exact squares of the real components
+ *              (exact_square_sum over both sets for SSM, over each set for PSM);
+ *   alpha != 2: the terms are |z|^alpha in FP64 (modpow), summed exactly over
+ *              both sets (exact_term_sum).
+ * PSM multiplies its two sums once. phi, psi: interleaved complex128, row r
+ * at phi + 2*r*ld.
  */
 int oracle_weights(const double *phi, int64_t ld_phi, int32_t n_phi,
                    const double *psi, int64_t ld_psi, int32_t n_psi,
                    int64_t n_r, int32_t kind, double alpha, double *w)
 {
     if (kind == 1) alpha = 2.0;
-#pragma omp parallel for schedule(static)
-    for (int64_t r = 0; r < n_r; ++r) {
-        const double *a = phi + 2 * r * ld_phi;
-        const double *b = psi + 2 * r * ld_psi;
-        double sa = 0.0, sb = 0.0;
-        for (int32_t i = 0; i < n_phi; ++i) sa = sa + modpow(a[2 * i], a[2 * i + 1], alpha);
-        for (int32_t j = 0; j < n_psi; ++j) sb = sb + modpow(b[2 * j], b[2 * j + 1], alpha);
-        w[r] = (kind == 1) ? sa * sb : sa + sb;
+#pragma omp parallel
+    {
+        double *t = (alpha == 2.0) ? NULL : (double *)malloc(sizeof(double) * (size_t)(n_phi + n_psi));
+#pragma omp for schedule(static)
+        for (int64_t r = 0; r < n_r; ++r) {
+            const double *a = phi + 2 * r * ld_phi;
+            const double *b = psi + 2 * r * ld_psi;
+            if (kind == 1) {
+                w[r] = exact_square_sum(a, n_phi, b, 0) * exact_square_sum(b, n_psi, a, 0);
+            } else if (alpha == 2.0) {
+                w[r] = exact_square_sum(a, n_phi, b, n_psi);
+            } else {
+                for (int32_t i = 0; i < n_phi; ++i) t[i] = modpow(a[2 * i], a[2 * i + 1], alpha);
+                for (int32_t j = 0; j < n_psi; ++j) t[n_phi + j] = modpow(b[2 * j], b[2 * j + 1], alpha);
+                w[r] = exact_term_sum(t, n_phi + n_psi);
+            }
+        }
+        free(t);
     }
     return 0;
 }

@@ -1,131 +1,316 @@
 // Step 1: the K-means weight function (Sec. 2.2, Eq. weight function 2 for
 // SSM and its alpha family, Eq. weight function for PSM).
 //
-// One thread owns one grid row and sums its moduli in ascending column order
-// with explicitly rounded FP64 operations, so the result is bit-identical to
-// the plain sequential definition. To keep HBM reads coalesced, a CTA stages
-// a 256-row x 128-byte tile through shared memory with 16-byte vector loads
-// (rows padded to 144 bytes so that the per-thread row reads are free of bank
-// conflicts), then each thread consumes its row of the tile.
+// Every sum of the weight is the exact sum of its terms rounded once, so the
+// result does not depend on summation order (and equals the oracle bit for
+// bit). For alpha = 2 the terms are the exact squares x^2 of the real
+// components x = Re z, Im z: with E = max floor(log2|x|) over the row's
+// non-zero components,
+//     sum = RN( sum_x floor(x^2 2^(110 - 2E)) ) 2^(2E - 110),
+// where x = m 2^p (integer mantissa m, exponent p of its format) makes each
+// term the integer m^2 shifted by 2p + 110 - 2E, accumulated in 128 bits with
+// integer instructions only. For alpha != 2 the terms are |z|^alpha in FP64
+// and the same exact summation runs on floor(t 2^(110 - E_t)).
+//
+// One warp owns one grid row: pass 1 reads the row and reduces the exponent
+// window E, pass 2 reads it again (from L1/L2: the row was just read) and
+// accumulates; the 128-bit lane sums are added across the warp with carries.
+// GB300 issues FP64 at about 2 operations per clock per SM, so the integer
+// formulation keeps the kernel on the memory system instead of the FP64 pipe.
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace {
 
-constexpr int kRows = 256;          // rows per CTA (one per thread)
-constexpr int kPieces = 8;          // 16-byte pieces per row per chunk (128 B)
-constexpr int kStride = kPieces + 1;
+constexpr int kThreads = 256;
+constexpr int kNoExp = -0x40000000;   // no non-zero component seen
 
-template <int AK>  // 2: alpha = 2; 1, 3, 4: sqrt/product forms; 0: pow
-__device__ __forceinline__ double modulus_pow(double m, double half_alpha)
+struct U128 {
+    unsigned long long lo, hi;
+};
+
+__device__ __forceinline__ void add_u128(U128 &a, unsigned long long lo, unsigned long long hi)
 {
-    if (AK == 2) return m;
+    const unsigned long long l = a.lo + lo;
+    a.hi += hi + (l < lo ? 1ull : 0ull);
+    a.lo = l;
+}
+
+// a += floor(v 2^sh) for a 64-bit v and sh <= 64
+__device__ __forceinline__ void add_shifted64(U128 &a, unsigned long long v, int sh)
+{
+    if (sh >= 0) {
+        if (sh == 0) add_u128(a, v, 0ull);
+        else if (sh < 64) add_u128(a, v << sh, v >> (64 - sh));
+        else add_u128(a, 0ull, v);
+    } else if (sh > -64) {
+        add_u128(a, v >> (-sh), 0ull);
+    }
+}
+
+// a += floor((vhi:vlo) 2^sh) for sh <= 63
+__device__ __forceinline__ void add_shifted128(U128 &a, unsigned long long vlo, unsigned long long vhi, int sh)
+{
+    if (sh >= 0) {
+        if (sh == 0) add_u128(a, vlo, vhi);
+        else add_u128(a, vlo << sh, (vhi << sh) | (vlo >> (64 - sh)));
+    } else {
+        const int t = -sh;
+        if (t < 64) add_u128(a, (vlo >> t) | (vhi << (64 - t)), vhi >> t);
+        else if (t < 128) add_u128(a, vhi >> (t - 64), 0ull);
+    }
+}
+
+// floor(log2|x|) and the integer form |x| = m 2^p of a float / a double (x != 0)
+__device__ __forceinline__ int exp_of(uint32_t u)
+{
+    const int b = (int)((u >> 23) & 0xFF);
+    const uint32_t f = u & 0x7FFFFFu;
+    if (b) return b - 127;
+    return f ? (31 - __clz((int)f)) - 149 : kNoExp;
+}
+__device__ __forceinline__ int exp_of(unsigned long long u)
+{
+    const int b = (int)((u >> 52) & 0x7FF);
+    const unsigned long long f = u & 0xFFFFFFFFFFFFFull;
+    if (b) return b - 1023;
+    return f ? (63 - __clzll((long long)f)) - 1074 : kNoExp;
+}
+
+// the term floor(x^2 2^(110 - 2E)) of one component, added to a
+__device__ __forceinline__ void add_square(U128 &a, uint32_t u, int E)
+{
+    const int b = (int)((u >> 23) & 0xFF);
+    const uint32_t f = u & 0x7FFFFFu;
+    if (!b && !f) return;
+    const uint32_t m = b ? (f | 0x800000u) : f;
+    const int p = b ? b - 150 : -149;
+    add_shifted64(a, (unsigned long long)m * m, 2 * p + 110 - 2 * E);   // m^2 < 2^48, shift <= 64
+}
+__device__ __forceinline__ void add_square(U128 &a, unsigned long long u, int E)
+{
+    const int b = (int)((u >> 52) & 0x7FF);
+    const unsigned long long f = u & 0xFFFFFFFFFFFFFull;
+    if (!b && !f) return;
+    const unsigned long long m = b ? (f | (1ull << 52)) : f;
+    const int p = b ? b - 1075 : -1074;
+    add_shifted128(a, m * m, __umul64hi(m, m), 2 * p + 110 - 2 * E);     // m^2 < 2^106, shift <= 6
+}
+
+// round-to-nearest-even of a 128-bit integer, times 2^scale
+__device__ __forceinline__ double u128_scaled(U128 a, int scale)
+{
+    double d;
+    if (a.hi == 0ull) {
+        d = __ull2double_rn(a.lo);
+    } else {
+        const int n = __clzll((long long)a.hi);
+        unsigned long long top = n ? ((a.hi << n) | (a.lo >> (64 - n))) : a.hi;
+        if (a.lo << n) top |= 1ull;   // sticky: the bits below top decide ties
+        d = ldexp(__ull2double_rn(top), 64 - n);
+    }
+    return ldexp(d, scale);
+}
+
+__device__ __forceinline__ U128 warp_sum(U128 a)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long lo = __shfl_xor_sync(0xffffffffu, a.lo, o);
+        const unsigned long long hi = __shfl_xor_sync(0xffffffffu, a.hi, o);
+        add_u128(a, lo, hi);
+    }
+    return a;
+}
+
+// The component bits of one orbital row, visited by the lanes of a warp: complex64 rows as 16-byte
+// pieces (two elements) when the row start is 16-byte aligned, else element by element.
+template <typename F>
+__device__ __forceinline__ void for_components(const float2 *row, int n, int lane, F &&fn)
+{
+    if ((reinterpret_cast<uintptr_t>(row) & 15) == 0) {
+        const uint4 *v = reinterpret_cast<const uint4 *>(row);
+        const int n2 = n >> 1;
+#pragma unroll 4
+        for (int i = lane; i < n2; i += 32) {
+            const uint4 q = __ldg(v + i);
+            fn(q.x);
+            fn(q.y);
+            fn(q.z);
+            fn(q.w);
+        }
+        if ((n & 1) && lane == 0) {
+            const uint2 q = __ldg(reinterpret_cast<const uint2 *>(row) + (n - 1));
+            fn(q.x);
+            fn(q.y);
+        }
+    } else {
+        for (int i = lane; i < n; i += 32) {
+            const uint2 q = __ldg(reinterpret_cast<const uint2 *>(row) + i);
+            fn(q.x);
+            fn(q.y);
+        }
+    }
+}
+template <typename F>
+__device__ __forceinline__ void for_components(const double2 *row, int n, int lane, F &&fn)
+{
+    const ulonglong2 *v = reinterpret_cast<const ulonglong2 *>(row);
+#pragma unroll 4
+    for (int i = lane; i < n; i += 32) {
+        const ulonglong2 q = __ldg(v + i);
+        fn(q.x);
+        fn(q.y);
+    }
+}
+
+// floor(log2 max |x|) over a row's components from the largest magnitude bit pattern (the bit
+// patterns of non-negative floats / doubles order like their values), kNoExp for an all-zero row
+__device__ __forceinline__ int exp_of_max(uint32_t m) { return m ? exp_of(m) : kNoExp; }
+__device__ __forceinline__ int exp_of_max(unsigned long long m) { return m ? exp_of(m) : kNoExp; }
+
+template <typename T>
+__device__ __forceinline__ int row_exp(const T *row, int n, int lane)
+{
+    using B = typename std::conditional<sizeof(T) == 8, uint32_t, unsigned long long>::type;
+    constexpr B mag = sizeof(T) == 8 ? (B)0x7FFFFFFFu : (B)0x7FFFFFFFFFFFFFFFull;
+    B m = 0;
+    for_components(row, n, lane, [&](B u) { m = max(m, (B)(u & mag)); });
+    return __reduce_max_sync(0xffffffffu, exp_of_max(m));
+}
+
+template <typename T>
+__device__ __forceinline__ void row_squares(const T *row, int n, int lane, int E, U128 &a)
+{
+    for_components(row, n, lane, [&](auto u) { add_square(a, u, E); });
+}
+
+// alpha = 2: SSM (one window over both sets) or PSM (one per set, multiplied)
+template <typename T>
+__global__ void __launch_bounds__(kThreads) weights_squares(const T *__restrict__ phi, int64_t ld_phi, int n_phi,
+                                                            const T *__restrict__ psi, int64_t ld_psi, int n_psi,
+                                                            int64_t n_r, int psm, double *__restrict__ w, int acc)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n_r; r += nw) {
+        const T *a = phi + r * ld_phi, *b = psi + r * ld_psi;
+        const int ea = row_exp(a, n_phi, lane), eb = row_exp(b, n_psi, lane);
+        double v;
+        if (!psm) {
+            const int E = max(ea, eb);
+            U128 s{0ull, 0ull};
+            if (E != kNoExp) {
+                row_squares(a, n_phi, lane, E, s);
+                row_squares(b, n_psi, lane, E, s);
+            }
+            s = warp_sum(s);
+            v = E == kNoExp ? 0.0 : u128_scaled(s, 2 * E - 110);
+        } else {
+            U128 sa{0ull, 0ull}, sb{0ull, 0ull};
+            if (ea != kNoExp) row_squares(a, n_phi, lane, ea, sa);
+            if (eb != kNoExp) row_squares(b, n_psi, lane, eb, sb);
+            sa = warp_sum(sa);
+            sb = warp_sum(sb);
+            const double xa = ea == kNoExp ? 0.0 : u128_scaled(sa, 2 * ea - 110);
+            const double xb = eb == kNoExp ? 0.0 : u128_scaled(sb, 2 * eb - 110);
+            v = __dmul_rn(xa, xb);
+        }
+        if (lane == 0) w[r] = acc ? __dadd_rn(w[r], v) : v;   // shared weight of several pairs: one rounding per pair
+    }
+}
+
+// |z|^alpha in FP64 for alpha != 2: m = re*re + im*im with each operation rounded (for complex64
+// input the products are exact, so one fused multiply-add gives the same bits)
+template <int AK>  // 1, 3, 4: sqrt/product forms; 0: pow
+__device__ __forceinline__ double modulus_pow(double re, double im, bool exact_products, double half_alpha)
+{
+    const double m = exact_products ? __fma_rn(re, re, __dmul_rn(im, im))
+                                    : __dadd_rn(__dmul_rn(re, re), __dmul_rn(im, im));
     if (AK == 1) return __dsqrt_rn(m);
     if (AK == 3) return __dmul_rn(m, __dsqrt_rn(m));
     if (AK == 4) return __dmul_rn(m, m);
     return pow(m, half_alpha);
 }
 
-// |z|^2 = re*re + im*im with each operation rounded. For complex64 input the
-// products are exact in FP64, so one fused multiply-add gives the same bits.
-__device__ __forceinline__ double mod2(double re, double im, bool exact_products)
+template <typename T, int AK, typename F>
+__device__ __forceinline__ void for_terms(const T *row, int n, int lane, double half_alpha, F &&fn)
 {
-    if (exact_products) return __fma_rn(re, re, __dmul_rn(im, im));
-    return __dadd_rn(__dmul_rn(re, re), __dmul_rn(im, im));
+    for (int i = lane; i < n; i += 32) {
+        const double2 z = cload(row, i);
+        fn(modulus_pow<AK>(z.x, z.y, sizeof(T) == 8, half_alpha));
+    }
 }
 
-// Sum of |x_j|^alpha over the n columns of one orbital set for this CTA's rows.
-template <typename T, int AK>
-__device__ double row_sum(const T *__restrict__ x, int64_t ld, int n, int64_t row0, int64_t n_r,
-                          double half_alpha, uint4 (*tile)[kStride])
+// floor(t 2^s) of a non-negative double as a 128-bit integer (t 2^s < 2^127)
+__device__ __forceinline__ void add_fixed(U128 &a, double t, int s)
 {
-    constexpr int per_piece = 16 / (int)sizeof(T);   // complex elements per 16-byte piece
-    constexpr int chunk = kPieces * per_piece;        // columns per chunk
-    const int tid = threadIdx.x;
-    const bool vec_ok = ((ld * (int64_t)sizeof(T)) % 16 == 0) && ((reinterpret_cast<uintptr_t>(x) & 15) == 0);
-    double s = 0.0;
-    for (int c0 = 0; c0 < n; c0 += chunk) {
-        // cooperative coalesced load of kRows x chunk columns
-#pragma unroll
-        for (int it = 0; it < kPieces; ++it) {
-            const int e = it * kRows + tid;
-            const int r = e / kPieces, p = e % kPieces;
-            const int64_t row = row0 + r;
-            const int col = c0 + p * per_piece;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (row < n_r && col < n) {
-                const T *src = x + row * ld + col;
-                if (vec_ok && col + per_piece <= n) {
-                    v = *reinterpret_cast<const uint4 *>(src);
-                } else {
-                    T tmp[per_piece];
-#pragma unroll
-                    for (int q = 0; q < per_piece; ++q) {
-                        if (col + q < n) tmp[q] = src[q];
-                        else memset(&tmp[q], 0, sizeof(T));
-                    }
-                    memcpy(&v, tmp, 16);
-                }
-            }
-            tile[r][p] = v;
-        }
-        __syncthreads();
-        const int cols = min(chunk, n - c0);
-#pragma unroll 1
-        for (int p = 0; p < kPieces; ++p) {
-            if (p * per_piece >= cols) break;
-            uint4 v = tile[tid][p];
-            if (sizeof(T) == 16) {
-                double2 z;
-                memcpy(&z, &v, 16);
-                s = __dadd_rn(s, modulus_pow<AK>(mod2(z.x, z.y, false), half_alpha));
-            } else {
-                float4 z;
-                memcpy(&z, &v, 16);
-                s = __dadd_rn(s, modulus_pow<AK>(mod2((double)z.x, (double)z.y, true), half_alpha));
-                if (p * per_piece + 1 < cols)
-                    s = __dadd_rn(s, modulus_pow<AK>(mod2((double)z.z, (double)z.w, true), half_alpha));
-            }
-        }
-        __syncthreads();
-    }
-    return s;
+    const unsigned long long u = (unsigned long long)__double_as_longlong(t);
+    const int b = (int)((u >> 52) & 0x7FF);
+    const unsigned long long f = u & 0xFFFFFFFFFFFFFull;
+    if (!b && !f) return;
+    const unsigned long long m = b ? (f | (1ull << 52)) : f;
+    add_shifted128(a, m, 0ull, (b ? b - 1075 : -1074) + s);
 }
 
+// alpha != 2: the FP64 terms summed exactly over both sets (the terms are formed twice: once for
+// the window, once for the sum; this path serves the weight-function study)
 template <typename T, int AK>
-__global__ void __launch_bounds__(kRows) weights_kernel(const T *__restrict__ phi, int64_t ld_phi, int n_phi,
-                                                       const T *__restrict__ psi, int64_t ld_psi, int n_psi,
-                                                       int64_t n_r, int psm, double half_alpha,
-                                                       double *__restrict__ w, int acc)
+__global__ void __launch_bounds__(kThreads) weights_terms(const T *__restrict__ phi, int64_t ld_phi, int n_phi,
+                                                          const T *__restrict__ psi, int64_t ld_psi, int n_psi,
+                                                          int64_t n_r, double half_alpha, double *__restrict__ w,
+                                                          int acc)
 {
-    __shared__ uint4 tile[kRows][kStride];
-    const int64_t row0 = (int64_t)blockIdx.x * kRows;
-    const double sa = row_sum<T, AK>(phi, ld_phi, n_phi, row0, n_r, half_alpha, tile);
-    const double sb = row_sum<T, AK>(psi, ld_psi, n_psi, row0, n_r, half_alpha, tile);
-    const int64_t row = row0 + threadIdx.x;
-    if (row < n_r) {
-        const double v = psm ? __dmul_rn(sa, sb) : __dadd_rn(sa, sb);
-        w[row] = acc ? __dadd_rn(w[row], v) : v;   // shared weight of several pairs: one rounding per pair
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n_r; r += nw) {
+        const T *a = phi + r * ld_phi, *b = psi + r * ld_psi;
+        int e = kNoExp;
+        auto mx = [&](double t) {
+            if (t != 0.0) e = max(e, exp_of((unsigned long long)__double_as_longlong(t)));
+        };
+        for_terms<T, AK>(a, n_phi, lane, half_alpha, mx);
+        for_terms<T, AK>(b, n_psi, lane, half_alpha, mx);
+        const int E = __reduce_max_sync(0xffffffffu, e);
+        U128 s{0ull, 0ull};
+        if (E != kNoExp) {
+            auto add = [&](double t) { add_fixed(s, t, 110 - E); };
+            for_terms<T, AK>(a, n_phi, lane, half_alpha, add);
+            for_terms<T, AK>(b, n_psi, lane, half_alpha, add);
+        }
+        s = warp_sum(s);
+        const double v = E == kNoExp ? 0.0 : u128_scaled(s, E - 110);
+        if (lane == 0) w[r] = acc ? __dadd_rn(w[r], v) : v;
     }
+}
+
+unsigned grid_rows(int64_t n_r)
+{
+    // 4 blocks of 8 warps per SM: enough loads in flight, and the rows between a warp's two passes
+    // (about 32 warps x 152 SMs rows) stay in L2 for the second read
+    const int64_t g = (n_r + 7) / 8;
+    return (unsigned)(g < 152 * 4 ? (g < 1 ? 1 : g) : 152 * 4);
 }
 
 template <typename T>
 isdf_status launch_weights(const void *phi, int64_t ld_phi, int n_phi, const void *psi, int64_t ld_psi,
                            int n_psi, int64_t n_r, int psm, double alpha, double *w, int acc, cudaStream_t st)
 {
-    const unsigned grid = (unsigned)((n_r + kRows - 1) / kRows);
+    const unsigned grid = grid_rows(n_r);
     const T *a = static_cast<const T *>(phi);
     const T *b = static_cast<const T *>(psi);
     const double ha = 0.5 * alpha;
     if (psm || alpha == 2.0)
-        weights_kernel<T, 2><<<grid, kRows, 0, st>>>(a, ld_phi, n_phi, b, ld_psi, n_psi, n_r, psm, ha, w, acc);
+        weights_squares<T><<<grid, kThreads, 0, st>>>(a, ld_phi, n_phi, b, ld_psi, n_psi, n_r, psm, w, acc);
     else if (alpha == 1.0)
-        weights_kernel<T, 1><<<grid, kRows, 0, st>>>(a, ld_phi, n_phi, b, ld_psi, n_psi, n_r, 0, ha, w, acc);
+        weights_terms<T, 1><<<grid, kThreads, 0, st>>>(a, ld_phi, n_phi, b, ld_psi, n_psi, n_r, ha, w, acc);
     else if (alpha == 3.0)
-        weights_kernel<T, 3><<<grid, kRows, 0, st>>>(a, ld_phi, n_phi, b, ld_psi, n_psi, n_r, 0, ha, w, acc);
+        weights_terms<T, 3><<<grid, kThreads, 0, st>>>(a, ld_phi, n_phi, b, ld_psi, n_psi, n_r, ha, w, acc);
     else if (alpha == 4.0)
-        weights_kernel<T, 4><<<grid, kRows, 0, st>>>(a, ld_phi, n_phi, b, ld_psi, n_psi, n_r, 0, ha, w, acc);
+        weights_terms<T, 4><<<grid, kThreads, 0, st>>>(a, ld_phi, n_phi, b, ld_psi, n_psi, n_r, ha, w, acc);
     else
-        weights_kernel<T, 0><<<grid, kRows, 0, st>>>(a, ld_phi, n_phi, b, ld_psi, n_psi, n_r, 0, ha, w, acc);
+        weights_terms<T, 0><<<grid, kThreads, 0, st>>>(a, ld_phi, n_phi, b, ld_psi, n_psi, n_r, ha, w, acc);
     isdf_note_launch();
     ISDF_LAUNCH_CHECK();
     return ISDF_OK;
