@@ -8,6 +8,11 @@
 // updated by A22 -= L21 L21^H. The diagonal blocks are then inverted together,
 // and L^-1 is assembled bottom-up from them, one batched launch per level:
 // inv([[A, 0], [B, C]]) = [[A^-1, 0], [-C^-1 B A^-1, C^-1]].
+// Above 512 rows (with the tensor-core FP64 products enabled) the matrix is
+// split in halves recursively: the factor and the inverse of the leading half
+// give L21 = A21 L11^-H as one product, the Schur complement A22 - L21 L21^H is
+// one more, and the inverse's off-diagonal block two more, so that most flops
+// run as large exact-slicing products instead of 16-wide FP64 steps.
 #include "chol.cuh"
 #include "plan.cuh"
 #include "zgemm.cuh"
@@ -306,20 +311,17 @@ isdf_status tri_inv(const double2 *L, double2 *Linv, double2 *tmp, int64_t ld, i
     return ISDF_OK;
 }
 
-}  // namespace
-
-isdf_status cholesky_inverse(const double2 *M0, double2 *L, double2 *Linv, double2 *W, double2 *tmp, int n,
-                             double2 *part, size_t part_n, DeviceStatus *st, cudaStream_t stream,
-                             isdf_plan *tp)
+// Right-looking blocked factorisation of the diagonal block L[o:o+m, o:o+m] in place (its lower
+// triangle holds the matrix; earlier columns are already final). Look-ahead: after the panel of
+// block k, a side stream updates block column k+1, factors its diagonal block and forms its panel
+// while this stream updates the rest of the block's trailing matrix (disjoint columns). Each
+// stream has its own split-K scratch.
+isdf_status chol_blocked(const double2 *M0, double2 *L, int64_t ld, int o, int m, double2 *part, size_t part_n,
+                         DeviceStatus *st, cudaStream_t stream, isdf_plan *tp)
 {
-    const int64_t ld = n;
-    if (tp) timer_start(tp, 3, stream);
-    ISDF_CUDA_TRY(cudaMemsetAsync(Linv, 0, sizeof(double2) * (size_t)n * n, stream));
-    // Look-ahead: after the panel of block k, a side stream updates block column k+1,
-    // factors its diagonal block and forms its panel while this stream updates the rest
-    // of the trailing matrix (disjoint columns). Each stream has its own split-K scratch.
+    const int end = o + m;
     cudaStream_t side = (tp && tp->side) ? tp->side : nullptr;
-    const size_t side_need = (size_t)4 * n * NB;
+    const size_t side_need = (size_t)4 * m * NB;
     double2 *pside = nullptr, *pmain = part;
     size_t nmain = part_n;
     if (part && part_n >= 2 * side_need) {
@@ -335,13 +337,13 @@ isdf_status cholesky_inverse(const double2 *M0, double2 *L, double2 *Linv, doubl
         return ISDF_OK;
     };
     {
-        const int nb = n < NB ? n : NB;
-        potrf_diag<<<1, DT, 0, stream>>>(L, ld, M0, 0, nb, st); isdf_note_launch();
+        const int nb = m < NB ? m : NB;
+        potrf_diag<<<1, DT, 0, stream>>>(L, ld, M0, o, nb, st); isdf_note_launch();
         ISDF_LAUNCH_CHECK();
-        if (n - nb > 0) ISDF_TRY(panel(0, nb, n - nb, stream));
+        if (m - nb > 0) ISDF_TRY(panel(o, nb, m - nb, stream));
     }
-    for (int k = 0; k + NB < n; k += NB) {
-        const int k1 = k + NB, rest = n - k1;              // next block at k1, rows below block k
+    for (int k = o; k + NB < end; k += NB) {
+        const int k1 = k + NB, rest = end - k1;            // next block at k1, rows below block k
         const int nb1 = rest < NB ? rest : NB, rest1 = rest - nb1;
         cudaStream_t s2 = side ? side : stream;
         StreamJoin fork;   // joins the side stream back on any early return below
@@ -372,23 +374,97 @@ isdf_status cholesky_inverse(const double2 *M0, double2 *L, double2 *Linv, doubl
         }
         ISDF_CUDA_TRY(fork.join());
     }
-    {
+    return ISDF_OK;
+}
+
+// The inverse of the factored diagonal block L[o:o+m, o:o+m] into Linv[o:o+m, o:o+m]: its NB-wide
+// diagonal blocks inverted at once, then merged bottom-up (tri_inv).
+isdf_status inverse_blocked(const double2 *L, double2 *Linv, double2 *tmp, int64_t ld, int o, int m, double2 *part,
+                            size_t part_n, DeviceStatus *st, cudaStream_t stream, const isdf_plan *tp)
+{
+    const double2 *Lo = L + (int64_t)o * ld + o;
+    double2 *Io = Linv + (int64_t)o * ld + o;
+    inv_diag<<<(m + NB - 1) / NB, EW, 0, stream>>>(Lo, ld, Io, ld, m, st); isdf_note_launch();
+    ISDF_LAUNCH_CHECK();
+    return tri_inv(Lo, Io, tmp, ld, m, part, part_n, tp, stream);
+}
+
+// Recursive factorisation and inverse of the diagonal block [o, o+m) for large blocks, so that
+// most of the (4/3) m^3 flops of each are in large products (on the tensor cores by exact slicing
+// when the plan enables it): with the block split at m1,
+//   L11 = chol(A11), L11^-1                 (recursively)
+//   L21 = A21 L11^-H                        (product; L11^-1 is at hand)
+//   A22 <- A22 - L21 L21^H                  (lower tiles)
+//   L22 = chol(A22), L22^-1                 (recursively)
+//   (L^-1)21 = -L22^-1 (L21 L11^-1)
+// Blocks of at most kRecBase rows use the blocked factorisation and inverse above.
+constexpr int kRecBase = 512;
+
+isdf_status chol_rec(const double2 *M0, double2 *L, double2 *Linv, double2 *tmp, int64_t ld, int o, int m,
+                     double2 *part, size_t part_n, DeviceStatus *st, cudaStream_t stream, isdf_plan *tp)
+{
+    if (m <= kRecBase) {
+        ISDF_TRY(chol_blocked(M0, L, ld, o, m, part, part_n, st, stream, tp));
+        return inverse_blocked(L, Linv, tmp, ld, o, m, part, part_n, st, stream, tp);
+    }
+    const int m1 = ((m / 2 + NB - 1) / NB) * NB, m2 = m - m1;
+    ISDF_TRY(chol_rec(M0, L, Linv, tmp, ld, o, m1, part, part_n, st, stream, tp));
+    double2 *A21 = L + (int64_t)(o + m1) * ld + o;
+    const double2 *I11 = Linv + (int64_t)o * ld + o;
+    // L21 = A21 L11^-H into tmp (m2 x m1), then back in place
+    ZGemm g = single(m2, m1, m1, op(A21, ld, 1, 0), op(I11, 1, ld, 1), tmp, m1, 1.0, 0);
+    ISDF_TRY(product(g, part, part_n, tp, stream));
+    ISDF_CUDA_TRY(cudaMemcpy2DAsync(A21, sizeof(double2) * ld, tmp, sizeof(double2) * m1, sizeof(double2) * m1, m2,
+                                    cudaMemcpyDeviceToDevice, stream));
+    // A22 -= L21 L21^H (lower tiles)
+    ZGemm u = single(m2, m2, m1, op(A21, ld, 1, 0), op(A21, 1, ld, 1), L + (int64_t)(o + m1) * (ld + 1), ld, -1.0, 1);
+    u.lower_only = 1;
+    ISDF_TRY(product(u, part, part_n, tp, stream));
+    ISDF_TRY(chol_rec(M0, L, Linv, tmp, ld, o + m1, m2, part, part_n, st, stream, tp));
+    // (L^-1)21 = -L22^-1 (L21 L11^-1)
+    ZGemm g1 = single(m2, m1, m1, op(A21, ld, 1, 0), op(I11, ld, 1, 0), tmp, m1, 1.0, 0);
+    g1.kmode = ZG_K_FROM_N0;   // L11^-1 lower: k >= n
+    ISDF_TRY(product(g1, part, part_n, tp, stream));
+    ZGemm g2 = single(m2, m1, m2, op(Linv + (int64_t)(o + m1) * (ld + 1), ld, 1, 0), op(tmp, m1, 1, 0),
+                      Linv + (int64_t)(o + m1) * ld + o, ld, -1.0, 0);
+    g2.k_to_m_end = 1;         // L22^-1 lower: k <= m
+    return product(g2, part, part_n, tp, stream);
+}
+
+}  // namespace
+
+isdf_status cholesky_inverse(const double2 *M0, double2 *L, double2 *Linv, double2 *W, double2 *tmp, int n,
+                             double2 *part, size_t part_n, DeviceStatus *st, cudaStream_t stream,
+                             isdf_plan *tp)
+{
+    const int64_t ld = n;
+    if (tp) timer_start(tp, 3, stream);
+    ISDF_CUDA_TRY(cudaMemsetAsync(Linv, 0, sizeof(double2) * (size_t)n * n, stream));
+    const bool recursive = tp && tp->use_oz && n > kRecBase;
+    if (recursive) {
+        // factor and inverse together (timed as stage 3; stage 4 records nothing)
+        ISDF_TRY(chol_rec(M0, L, Linv, tmp, ld, 0, n, part, part_n, st, stream, tp));
+        const int64_t total = (int64_t)n * n;
+        const unsigned gr = (unsigned)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+        zero_strict_upper<<<gr, 256, 0, stream>>>(L, n, ld); isdf_note_launch();
+        ISDF_LAUNCH_CHECK();
+        timer_stop(tp, 3, stream, n);
+    } else {
+        ISDF_TRY(chol_blocked(M0, L, ld, 0, n, part, part_n, st, stream, tp));
         const int64_t total = (int64_t)n * n;
         const unsigned gr = (unsigned)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
         zero_strict_upper<<<gr, 256, 0, stream>>>(L, n, ld); isdf_note_launch();
         // the inverted diagonal blocks of L, all at once (the first level of L^-1)
         inv_diag<<<(n + NB - 1) / NB, EW, 0, stream>>>(L, ld, Linv, ld, n, st); isdf_note_launch();
         ISDF_LAUNCH_CHECK();
+        if (tp) {
+            timer_stop(tp, 3, stream, n);
+            timer_start(tp, 4, stream);
+        }
+        ISDF_TRY(tri_inv(L, Linv, tmp, ld, n, part, part_n, tp, stream));
+        if (tp) timer_stop(tp, 4, stream, n);
     }
-    if (tp) {
-        timer_stop(tp, 3, stream, n);
-        timer_start(tp, 4, stream);
-    }
-    ISDF_TRY(tri_inv(L, Linv, tmp, ld, n, part, part_n, tp, stream));
-    if (tp) {
-        timer_stop(tp, 4, stream, n);
-        timer_start(tp, 5, stream);
-    }
+    if (tp) timer_start(tp, 5, stream);
     // W = Linv^H Linv: W_ij = sum_{k >= max(i, j)} conj(Linv_ki) Linv_kj (lower tiles, then mirrored)
     ZGemm w = single(n, n, n, op(Linv, 1, ld, 1), op(Linv, ld, 1, 0), W, ld, 1.0, 0);
     w.kmode = ZG_K_FROM_MAX_MN;
