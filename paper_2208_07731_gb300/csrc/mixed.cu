@@ -30,15 +30,18 @@
 
 namespace {
 
+// K chunk of 64 FP16 (one 128-byte row per tile row, 128-byte swizzle) in a 3-stage ring of 64 KB
+// (a 6-stage ring of 32-element chunks with 64-byte swizzle was 13-17 % slower at N_mu = 4096)
 constexpr int TM = 128, TN = 128, TK = 64;
 constexpr int STAGES = 3;
 constexpr int TILE_A = TM * TK * 2;
 constexpr int TILE_B = TN * TK * 2;
 constexpr int STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
-constexpr long long WAIT_BUDGET = 200000000LL;
-constexpr int kApplySegment = 8;   // K chunks (of 64) per TMEM accumulation segment in the M^-1 GEMM
-constexpr int kGramSegment = 8;    // the same for each of the two Gram products  // SM cycles (~0.1 s); normal waits take microseconds
+constexpr long long WAIT_BUDGET = 200000000LL;   // SM cycles (~0.1 s); normal waits take microseconds
+constexpr int kSegmentK = 512;                   // K per TMEM accumulation segment (summed in FP32 registers)
+constexpr int kApplySegment = kSegmentK / TK;    // K chunks per segment in the M^-1 GEMM
+constexpr int kGramSegment = kSegmentK / TK;     // the same for each of the two Gram products
 
 struct MixScales {
     unsigned int maxabs_phi, maxrho_phi, maxabs_psi, maxrho_psi, maxabs_w;  // float bits
@@ -244,6 +247,23 @@ struct EpiParams {
 constexpr int EPI_WARPS = 8;
 constexpr int GEMM_THREADS = 64 + 32 * EPI_WARPS;
 
+// Output tile order: groups of kGroupM row tiles, all column tiles of a group before the next
+// group, row tile fastest within the group. The ~152 tiles in flight then cover ~kGroupM row tiles
+// x ~152/kGroupM column tiles, so both operands' panels are shared in L2 by several CTAs; with the
+// plain row-major order they span ~2 row tiles x every column tile, and a B operand larger than L2
+// (e.g. the 268 MB split M^-1 at N_mu = 4096) is re-read from HBM every ~2 row tiles.
+constexpr int kGroupM = 16;
+
+__device__ __forceinline__ void tile_coords(int mn, int n_tiles_n, int m_tiles, int &m0, int &n0)
+{
+    const int per_group = kGroupM * n_tiles_n;
+    const int g = mn / per_group, r = mn - g * per_group;
+    const int gm0 = g * kGroupM;
+    const int gm = min(kGroupM, m_tiles - gm0);
+    m0 = (gm0 + r % gm) * TM;
+    n0 = (r / gm) * TN;
+}
+
 template <bool DUAL>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
     tc_gemm_persist(const __grid_constant__ CUtensorMap a1h, const __grid_constant__ CUtensorMap a1l,
@@ -302,7 +322,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             int c = 0, issued = 0;
             for (int t = blockIdx.x; t < n_work && !failed; t += gridDim.x) {
                 const int mn = t / ksplit, ks = t % ksplit;
-                const int m0 = (mn / n_tiles_n) * TM, n0 = (mn % n_tiles_n) * TN;
+                int m0, n0;
+                tile_coords(mn, n_tiles_n, n_tiles / n_tiles_n, m0, n0);
                 const int kb = ks * kper, ke = min(kchunks, kb + kper);
                 for (int s0 = kb; s0 < ke && !failed; s0 += seg)
                     for (int part = 0; part < PARTS && !failed; ++part)
@@ -393,7 +414,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         int tl = 0;
         for (int t = blockIdx.x; t < n_work && !failed; t += gridDim.x) {
             const int mn = t / ksplit, ks = t % ksplit;
-            const int m0 = (mn / n_tiles_n) * TM, n0 = (mn % n_tiles_n) * TN;
+            int m0, n0;
+            tile_coords(mn, n_tiles_n, n_tiles / n_tiles_n, m0, n0);
             const int kb = ks * kper, ke = min(kchunks, kb + kper);
             const int row = m0 + quarter * 32 + lane;
             float sa[HC], sb[DUAL ? HC : 1];
@@ -648,7 +670,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 }
 
 // 2-D FP16 map: `inner` halves per row (row pitch `pitch` halves, default inner), `rows`
-// rows, box 64 x 128, 128-byte swizzle
+// rows, box TK x 128 (128 bytes x 128 rows), 128-byte swizzle
 bool make_map(CUtensorMap *m, const void *base, uint64_t inner, uint64_t rows, uint64_t pitch = 0)
 {
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
@@ -826,7 +848,7 @@ isdf_status mixed_fit(isdf_plan *p, int64_t row_begin, int64_t row_count, void *
 
 namespace {
 
-// one tensor-core GEMM launch: C (rows x ncols real) = A (rows x K) Bh^T over kchunks chunks of 64
+// one tensor-core GEMM launch: C (rows x ncols real) = A (rows x K) Bh^T over kchunks chunks of TK
 isdf_status run_gemm(const CUtensorMap &ah, const CUtensorMap &al, const CUtensorMap &bh, const CUtensorMap &bl,
                      int kchunks, int rows, int ncols, EpiParams ep, cudaStream_t st)
 {
@@ -843,12 +865,12 @@ isdf_status run_gemm(const CUtensorMap &ah, const CUtensorMap &al, const CUtenso
     return ISDF_OK;
 }
 
-// split-K factor for a long reduction with few output tiles: ~3 CTAs of work per SM, >= 16 chunks each
+// split-K factor for a long reduction with few output tiles: ~3 CTAs of work per SM, >= 1024 K each
 int ksplit_for(int rows, int ncols, int kchunks)
 {
     const int tiles = ((rows + TM - 1) / TM) * ((ncols + TN - 1) / TN);
     int k = (3 * num_sms() + tiles - 1) / tiles;
-    const int kmax = kchunks / 16 > 1 ? kchunks / 16 : 1;
+    const int kmax = kchunks / (1024 / TK) > 1 ? kchunks / (1024 / TK) : 1;
     return k < 1 ? 1 : (k > kmax ? kmax : k);
 }
 

@@ -15,6 +15,8 @@ under the FP64 formula, every cluster is non-empty, snapped points are
 distinct members nearest to their centroids), and
 Theta fitted in blocks of 131,072 rows, never fully resident, <= 1e-5 against
 the oracle on a 16,384-row sample."""
+import math
+
 import numpy as np
 import pytest
 import torch
@@ -243,3 +245,127 @@ def test_silica_kmeans_properties_and_blocked_mixed_theta(isdf):
     dT = got - T
     zerr = np.sqrt(np.real(np.sum((dT @ M) * dT.conj())) / np.real(np.sum((T @ M) * T.conj())))
     assert err < 1e-5 and zerr < 1e-5, (err, zerr)
+
+
+def test_silica_adjoint_mixed_vs_fp64_and_central_differences(isdf):
+    """Config 4 (128^3, 1024 complex64 orbitals, 4096 points, blocks of 131,072 rows, Theta never
+    stored): the tensor-core gradient of the exchange-like surrogate against the FP64 GPU gradient
+    (itself pinned to the oracle gradient at 72^3), and the FP64 gradient against central differences
+    at h = 1e-6 on four directions, each loss difference formed from the two fits' Theta difference
+    (the per-row loss is a Hermitian quadratic form): three directions supported on a row range
+    without interpolation points (only those Theta rows move; fitted through a plan on
+    [Phi[idx]; Phi[range]]) and one on 64 interpolation points (M moves; two full FP64 fits)."""
+    w = W.WORKLOADS["silica"]
+    phi, psi = _gpu_pair(w)
+    shape, cell = (w.n,) * 3, (w.L,) * 3
+    wt = isdf.weights(phi, psi)
+    init = torch.from_numpy(W.init_indices(wt.cpu().numpy(), w.n_mu, 1000 + w.seed))
+    idx = isdf.kmeans(wt, shape, cell, w.n_mu, init, w.iters, labels=False, objective=False)["idx"]
+    del wt
+    rng = np.random.default_rng(3000 + w.seed)
+    Qk, _ = np.linalg.qr(rng.standard_normal((w.n_mu, 32)) + 1j * rng.standard_normal((w.n_mu, 32)))
+    U = Qk * np.sqrt(rng.uniform(1.0, 9.0, size=32))[None, :]
+    c = 1.0
+    K = c * np.eye(w.n_mu) + U @ U.conj().T
+    Kd = torch.from_numpy(0.5 * (K + K.conj().T)).to(DEV)
+    Ucd = torch.from_numpy(U.conj()).to(DEV)
+    B = 131072
+
+    def q_diff(tp, tm):
+        # sum over rows of q(t+) - q(t-), q(t) = c |t|^2 + |U^H t|^2, without cancellation
+        d, s = tp - tm, tp + tm
+        return (c * torch.real(torch.vdot(d.flatten(), s.flatten())) +
+                torch.real(torch.vdot((d @ Ucd).flatten(), (s @ Ucd).flatten()))).item()
+
+    # the tensor-core gradient, kept in complex64 (its rounding is far below the 1e-4 comparison)
+    mplan = isdf.Plan(phi, psi, idx, mode="mixed", max_rows=B)
+    _, mphi, mpsi = isdf.surrogate_loss_and_grad(mplan, Kd, w.dV, block=B)
+    mplan.check()
+    mplan.close()
+    mphi, mpsi = mphi.to(torch.complex64), mpsi.to(torch.complex64)
+    torch.cuda.empty_cache()
+    # the FP64 gradient on the same (complex64-valued) orbitals
+    plan = isdf.Plan(phi, psi, idx, mode="fp64", max_rows=B)
+    loss, gphi, gpsi = isdf.surrogate_loss_and_grad(plan, Kd, w.dV, block=B)
+    plan.check()
+    plan.close()
+    num = den = 0.0
+    for x, y in ((mphi, gphi), (mpsi, gpsi)):
+        for r0 in range(0, w.n_r, B):
+            yb = y[r0:r0 + B]
+            num += (torch.linalg.vector_norm(x[r0:r0 + B].to(torch.complex128) - yb) ** 2).item()
+            den += (torch.linalg.vector_norm(yb) ** 2).item()
+    assert math.sqrt(num / den) < 1e-4, math.sqrt(num / den)
+    del mphi, mpsi, x, y, yb   # the loop variables would keep two gradients alive
+    torch.cuda.empty_cache()
+
+    h = 1e-6
+    gen = torch.Generator(device=DEV).manual_seed(777)
+    idx_h = idx.cpu().numpy()
+    is_point = np.zeros(w.n_r, bool)
+    is_point[idx_h] = True
+    # (1) three directions on row ranges of 8,192 rows (interpolation rows in the range left unperturbed)
+    R = 8192
+    for r0 in (123 * 512, w.n_r // 2 + 77, w.n_r - R):
+        keep = torch.from_numpy(~is_point[r0:r0 + R]).to(DEV)[:, None]
+        Dp = torch.randn((R, w.n_orb), dtype=torch.complex128, device=DEV, generator=gen) * keep
+        Dq = torch.randn((R, w.n_orb), dtype=torch.complex128, device=DEV, generator=gen) * keep
+        Pr, Qr = phi[r0:r0 + R].to(torch.complex128), psi[r0:r0 + R].to(torch.complex128)
+        Dp *= torch.linalg.vector_norm(Pr) / torch.linalg.vector_norm(Dp)
+        Dq *= torch.linalg.vector_norm(Qr) / torch.linalg.vector_norm(Dq)
+        an = torch.real(torch.vdot(gphi[r0:r0 + R].flatten(), Dp.flatten()) +
+                        torch.vdot(gpsi[r0:r0 + R].flatten(), Dq.flatten())).item()
+        th = []
+        for sgn in (1.0, -1.0):
+            sp = torch.cat([phi[idx].to(torch.complex128), Pr + sgn * h * Dp]).contiguous()
+            sq = torch.cat([psi[idx].to(torch.complex128), Qr + sgn * h * Dq]).contiguous()
+            pl = isdf.Plan(sp, sq, torch.arange(w.n_mu, device=DEV), mode="fp64", max_rows=R)
+            th.append(pl.fit_theta(w.n_mu, R))
+            pl.check()
+            pl.close()
+        fd = w.dV * q_diff(th[0], th[1]) / (2 * h)
+        assert abs(fd - an) <= 1e-6 * abs(an), (r0, fd, an)
+        del th
+    # (2) one direction on 64 interpolation points: M moves, so every Theta row moves
+    S = torch.from_numpy(np.sort(rng.choice(idx_h, 64, replace=False))).to(DEV)
+    Dp = torch.randn((64, w.n_orb), dtype=torch.complex128, device=DEV, generator=gen)
+    Dq = torch.randn((64, w.n_orb), dtype=torch.complex128, device=DEV, generator=gen)
+    an = torch.real(torch.vdot(gphi[S].flatten(), Dp.flatten()) + torch.vdot(gpsi[S].flatten(), Dq.flatten())).item()
+    del gphi, gpsi
+    torch.cuda.empty_cache()
+    P = phi.to(torch.complex128)
+    Q = psi.to(torch.complex128)
+    del phi, psi
+    torch.cuda.empty_cache()
+    P0, Q0 = P[S].clone(), Q[S].clone()
+    plans = []
+    B = 32768      # smaller blocks here: two FP64 plans and the complex128 orbitals share the GPU
+    for sgn in (1.0, -1.0):
+        P[S] = P0 + sgn * h * Dp
+        Q[S] = Q0 + sgn * h * Dq
+        plans.append(isdf.Plan(P, Q, idx, mode="fp64", max_rows=B))   # gathers the perturbed points
+    torch.cuda.synchronize()
+    # the rows at S themselves, with their own perturbed values
+    rows_s = []
+    for pl, sgn in zip(plans, (1.0, -1.0)):
+        P[S] = P0 + sgn * h * Dp
+        Q[S] = Q0 + sgn * h * Dq
+        rows_s.append(torch.stack([pl.fit_theta(int(r), 1)[0] for r in S.tolist()]))
+        torch.cuda.synchronize()
+    P[S], Q[S] = P0, Q0
+    tot = q_diff(rows_s[0], rows_s[1])
+    tp = torch.empty((B, w.n_mu), dtype=torch.complex128, device=DEV)
+    tm = torch.empty_like(tp)
+    s_h = S.cpu().numpy()
+    for r0 in range(0, w.n_r, B):
+        n = min(B, w.n_r - r0)
+        plans[0].fit_theta(r0, n, out=tp[:n])
+        plans[1].fit_theta(r0, n, out=tm[:n])
+        # every row of the block but those at S (fitted above from their perturbed values)
+        loc = torch.from_numpy(s_h[(s_h >= r0) & (s_h < r0 + n)] - r0).to(DEV)
+        tot += q_diff(tp[:n], tm[:n]) - (q_diff(tp[loc], tm[loc]) if len(loc) else 0.0)
+    for pl in plans:
+        pl.check()
+        pl.close()
+    fd = w.dV * tot / (2 * h)
+    assert abs(fd - an) <= 1e-6 * abs(an), (fd, an)
