@@ -60,6 +60,8 @@ struct MixedBuffers {
     __half *yh, *yl;                 // max_rows x 2 N_mu split Y block
     MixScales *sc;
     CUtensorMap m_a1h, m_a1l, m_a2h, m_a2l, m_b1h, m_b1l, m_b2h, m_b2l, m_bwh, m_bwl, m_yh, m_yl;
+    // the Gram operands B in 64-row boxes: each CTA of a pair loads half of a 128-column tile
+    CUtensorMap m_b1h_half, m_b1l_half, m_b2h_half, m_b2l_half;
     // adjoint (allocated on the first backward call)
     float2 *ac, *bc, *tc, *gc, *ybc;      // max_rows x N_mu complex64: P^phi, P^psi, Theta, G, Ybar
     __half *oah, *oal;                    // split A operand scratch (max(R 2N_mu, N_mu 2R) halves)
@@ -550,6 +552,278 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     if (warp == 0) tc::tmem_dealloc(tmem, NCOLS);
 }
 
+// ---------------------------------------------------------------- CTA-pair GEMM
+// The same products on CTA pairs (clusters of two, cta_group::2): one MMA of M = 256 rows covers the
+// pair's two 128-row halves, each CTA holding its 128 rows of A, half of the BN rows of B and its
+// 128 rows of the accumulator in its own TMEM. Per SM and per FLOP this halves the B bytes loaded
+// from L2 and the operand bytes the tensor core reads from shared memory (the single-CTA kernel is
+// bound by that operand feed). Roles:
+//  * rank 0 (leader): warp 0 lane 0 loads the leader's stages and, for every stage, arms it for the
+//    peer (a remote arrive on the peer's `armed` barrier) after adding both CTAs' bytes to the
+//    leader's full barrier; warp 1 lane 0 issues the pair's MMAs and commits them to both CTAs'
+//    empty and tfull barriers; warps 2-9 run the epilogue of the leader's rows;
+//  * rank 1 (peer): warp 0 lane 0 loads the peer's stages into its own shared memory, each only
+//    after the leader armed it (so every peer copy is counted by a leader barrier the leader drains
+//    before the pair exits), completing on the leader's full barrier; warps 2-9 run the epilogue of
+//    the peer's rows and release the accumulator with a remote arrive on the leader's tempty.
+// Every wait is bounded as in tc_gemm_persist; the pair decides to run or to skip (an earlier
+// failure) once, from the leader's reading, so both CTAs always meet at the cluster barriers.
+template <bool DUAL, int BN>
+struct PairCfg {
+    static constexpr int BH = BN / 2;                       // B rows per CTA
+    static constexpr int TILE_BH = BH * TK * 2;
+    static constexpr int STAGE = 2 * TILE_A + 2 * TILE_BH;  // per CTA
+    static constexpr int NSTAGE = (192 * 1024) / STAGE;     // 4 (BN = 128) or 3 (BN = 256)
+    static constexpr int SMEM = NSTAGE * STAGE + 1024;
+    static constexpr int PARTS = DUAL ? 2 : 1;
+    static constexpr uint32_t ACC = PARTS * BN;             // TMEM columns of one accumulator buffer
+    static constexpr uint32_t NCOLS = 2 * ACC;
+    static constexpr int HC = BN / 2;                       // columns per epilogue thread
+    static_assert(NCOLS <= 512, "TMEM");
+};
+
+template <bool DUAL, int BN>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(GEMM_THREADS, 1)
+    tc_gemm_pair(const __grid_constant__ CUtensorMap a1h, const __grid_constant__ CUtensorMap a1l,
+                 const __grid_constant__ CUtensorMap b1h, const __grid_constant__ CUtensorMap b1l,
+                 const __grid_constant__ CUtensorMap a2h, const __grid_constant__ CUtensorMap a2l,
+                 const __grid_constant__ CUtensorMap b2h, const __grid_constant__ CUtensorMap b2l, int kchunks,
+                 int a_row0, int rows, int n_tiles_n, int n_tiles, int seg, EpiParams ep)
+{
+    using C = PairCfg<DUAL, BN>;
+    constexpr int S = C::NSTAGE;
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full_bar[S];
+    __shared__ __align__(8) uint64_t empty_bar[S];
+    __shared__ __align__(8) uint64_t armed_bar[S];
+    __shared__ __align__(8) uint64_t tfull[2];
+    __shared__ __align__(8) uint64_t tempty[2];
+    __shared__ __align__(8) uint64_t drain_bar;
+    __shared__ __align__(8) uint64_t never_bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int failed;
+    __shared__ uint32_t skip;
+
+    const uint32_t rank = tc::cluster_rank();
+    const bool leader = rank == 0;
+    const long long budget = ep.budget > 0 ? ep.budget : WAIT_BUDGET;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t raw = tc::smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t *sbase = smem_raw + (base - raw);
+    const int n_pairs = gridDim.x >> 1, pair = blockIdx.x >> 1;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            tc::mbar_init(&full_bar[s], 1);
+            tc::mbar_init(&empty_bar[s], 1);
+            tc::mbar_init(&armed_bar[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            tc::mbar_init(&tfull[a], 1);
+            tc::mbar_init(&tempty[a], 2 * EPI_WARPS);
+        }
+        tc::mbar_init(&drain_bar, 1);
+        tc::mbar_init(&never_bar, 1);
+        failed = 0;
+        skip = *(volatile int *)ep.err ? 1u : 0u;   // only the leader's reading is used
+        tc::fence_barrier_init();
+    }
+    __syncthreads();
+    tc::cluster_sync();   // both CTAs' barriers initialised before any remote arrive
+    const bool run = tc::ld_shared_cluster(tc::map_shared(&skip, 0)) == 0u;
+    if (warp == 0) tc::tmem_alloc_pair(&tmem_slot, C::NCOLS);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = tmem_slot;
+    const int m_ptiles = n_tiles / n_tiles_n;
+    const int n_work = run ? n_tiles : 0;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            const CUtensorMap *maps[8] = {&a1h, &a1l, &b1h, &b1l, &a2h, &a2l, &b2h, &b2l};
+            for (int i = 0; i < 4 * C::PARTS; ++i) tc::prefetch_map(maps[i]);
+            const uint32_t full0 = tc::map_shared(&full_bar[0], 0);   // the leader's full barriers
+            int c = 0, issued = 0;
+            for (int t = pair; t < n_work && !failed; t += n_pairs) {
+                int m0, n0;
+                tile_coords(t, n_tiles_n, m_ptiles, m0, n0);          // m0 in pair tiles of TM, n0 in TN units
+                m0 = (m0 / TM) * (2 * TM) + (int)rank * TM;           // this CTA's 128 rows of the pair's 256
+                n0 = (n0 / TN) * BN + (int)rank * C::BH;              // this CTA's half of the pair's BN columns
+                for (int s0 = 0; s0 < kchunks && !failed; s0 += seg)
+                    for (int part = 0; part < C::PARTS && !failed; ++part)
+                        for (int kc = s0; kc < min(kchunks, s0 + seg); ++kc, ++c) {
+                            const int s = c % S, it = c / S;
+                            if (!tc::mbar_wait(&empty_bar[s], (it & 1) ^ 1, budget) ||
+                                (!leader && !tc::mbar_wait(&armed_bar[s], it & 1, budget))) {
+                                atomicExch(ep.err, 1);
+                                failed = 1;
+                                break;
+                            }
+                            if (leader) {
+                                tc::mbar_expect_tx(&full_bar[s], 2 * C::STAGE);   // both CTAs' bytes
+                                tc::mbar_arrive_cluster(tc::map_shared(&armed_bar[s], 1));
+                            }
+                            const CUtensorMap *const *mp = maps + 4 * part;
+                            uint8_t *st = sbase + s * C::STAGE;
+                            const uint32_t fb = full0 + (uint32_t)(s * sizeof(uint64_t));
+                            tc::tma_load_2d_pair(st, mp[0], fb, kc * TK, a_row0 + m0);
+                            tc::tma_load_2d_pair(st + TILE_A, mp[1], fb, kc * TK, a_row0 + m0);
+                            tc::tma_load_2d_pair(st + 2 * TILE_A, mp[2], fb, kc * TK, n0);
+                            tc::tma_load_2d_pair(st + 2 * TILE_A + C::TILE_BH, mp[3], fb, kc * TK, n0);
+                            issued = c + 1;
+                        }
+            }
+            // the leader waits for every stage it armed (its full barrier counts the peer's copies too)
+            if (leader)
+                for (int c2 = issued - S > 0 ? issued - S : 0; c2 < issued; ++c2)
+                    tc::mbar_wait(&full_bar[c2 % S], (c2 / S) & 1, WAIT_BUDGET);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0 && leader) {
+            constexpr uint32_t idesc = tc::idesc_f16(2 * TM, BN);
+            int c = 0, tl = 0;
+            bool ok = true;
+            if (ep.budget < 0 && !tc::mbar_wait(&never_bar, 0, -ep.budget)) {
+                atomicExch(ep.err, 1);
+                failed = 1;
+                ok = false;
+            }
+            for (int t = pair; t < n_work && !failed && ok; t += n_pairs) {
+                for (int s0 = 0; s0 < kchunks && ok; s0 += seg, ++tl) {
+                    const int acc = tl & 1, use = tl >> 1;
+                    if (!tc::mbar_wait(&tempty[acc], (use & 1) ^ 1, budget)) {
+                        atomicExch(ep.err, 1);
+                        failed = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after();
+                    const int s1 = min(kchunks, s0 + seg);
+                    for (int part = 0; part < C::PARTS && ok; ++part) {
+                        const uint32_t d = tmem + (uint32_t)acc * C::ACC + (uint32_t)part * BN;
+                        for (int kc = s0; kc < s1; ++kc, ++c) {
+                            const int s = c % S, it = c / S;
+                            if (!tc::mbar_wait(&full_bar[s], it & 1, budget)) {
+                                atomicExch(ep.err, 1);
+                                failed = 1;
+                                ok = false;
+                                break;
+                            }
+                            tc::fence_after();
+                            const uint32_t sa = base + s * C::STAGE;
+                            const uint64_t dah = tc::desc_sw128(sa), dal = tc::desc_sw128(sa + TILE_A);
+                            const uint64_t dbh = tc::desc_sw128(sa + 2 * TILE_A),
+                                           dbl = tc::desc_sw128(sa + 2 * TILE_A + C::TILE_BH);
+#pragma unroll
+                            for (int kk = 0; kk < TK / 16; ++kk) {
+                                const uint64_t o = (uint64_t)(2 * kk);
+                                tc::mma_f16_pair(d, dah + o, dbh + o, idesc, (kc > s0 || kk > 0) ? 1u : 0u);
+                                tc::mma_f16_pair(d, dah + o, dbl + o, idesc, 1u);
+                                tc::mma_f16_pair(d, dal + o, dbh + o, idesc, 1u);
+                            }
+                            tc::mma_commit_pair(&empty_bar[s], 0x3);
+                        }
+                    }
+                    if (!ok) break;
+                    tc::mma_commit_pair(&tfull[acc], 0x3);
+                }
+            }
+            // no MMA of the pair may still be running when either CTA releases its TMEM
+            tc::mma_commit_pair(&drain_bar, 0x1);
+            tc::mbar_wait(&drain_bar, 0, WAIT_BUDGET);
+        }
+        __syncwarp();
+    } else {
+        const int quarter = warp & 3;
+        const int half = (warp - 2) >> 2;
+        constexpr int HC = C::HC;
+        const uint32_t tempty0 = tc::map_shared(&tempty[0], 0);
+        int tl = 0;
+        for (int t = pair; t < n_work && !failed; t += n_pairs) {
+            int m0, n0;
+            tile_coords(t, n_tiles_n, m_ptiles, m0, n0);
+            m0 = (m0 / TM) * (2 * TM) + (int)rank * TM;
+            n0 = (n0 / TN) * BN;
+            const int row = m0 + quarter * 32 + lane;
+            float sa[HC], sb[DUAL ? HC : 1];
+#pragma unroll
+            for (int i = 0; i < HC; ++i) sa[i] = 0.f;
+#pragma unroll
+            for (int i = 0; i < (DUAL ? HC : 1); ++i) sb[i] = 0.f;
+            bool ok = true;
+            for (int s0 = 0; s0 < kchunks; s0 += seg, ++tl) {
+                const int acc = tl & 1, use = tl >> 1;
+                if (!tc::mbar_wait(&tfull[acc], use & 1, budget)) {
+                    atomicExch(ep.err, 1);
+                    failed = 1;
+                    ok = false;
+                    break;
+                }
+                tc::fence_after();
+                const uint32_t ta = tmem + (uint32_t)acc * C::ACC + ((uint32_t)(quarter * 32) << 16) + half * HC;
+#pragma unroll
+                for (int j = 0; j < HC / 16; ++j) {
+                    uint32_t r[16];
+                    tc::tmem_ld16(ta + 16 * j, r);
+                    if (DUAL) {
+                        uint32_t r2[16];
+                        tc::tmem_ld16(ta + BN + 16 * j, r2);
+                        tc::tmem_wait_ld();
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) sb[(16 * j + q) % (DUAL ? HC : 1)] += __uint_as_float(r2[q]);
+                    } else {
+                        tc::tmem_wait_ld();
+                    }
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) sa[16 * j + q] += __uint_as_float(r[q]);
+                }
+                tc::fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive_cluster(tempty0 + (uint32_t)(acc * sizeof(uint64_t)));
+            }
+            if (!ok) break;
+            if (row >= rows || n0 + half * HC >= ep.ncols) continue;
+            if (DUAL) {
+                const float fy = ep.sc->fy;
+#pragma unroll
+                for (int j = 0; j < HC / 32; ++j) {
+                    __half2 hv[16], lv[16];
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const float ar = sa[32 * j + 2 * q], ai = sa[32 * j + 2 * q + 1];
+                        const float br = sb[(32 * j + 2 * q) % (DUAL ? HC : 1)],
+                                    bi = sb[(32 * j + 2 * q + 1) % (DUAL ? HC : 1)];
+                        const float yr = (ar * br + ai * bi) * fy, yi = (ai * br - ar * bi) * fy;
+                        const __half2 h = __floats2half2_rn(yr, yi);
+                        const float2 hf = __half22float2(h);
+                        hv[q] = h;
+                        lv[q] = __floats2half2_rn(yr - hf.x, yi - hf.y);
+                    }
+                    uint4 *dh = reinterpret_cast<uint4 *>(ep.yh + row * ep.ldy + n0 + half * HC + 32 * j);
+                    uint4 *dl = reinterpret_cast<uint4 *>(ep.yl + row * ep.ldy + n0 + half * HC + 32 * j);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        dh[q] = reinterpret_cast<const uint4 *>(hv)[q];
+                        dl[q] = reinterpret_cast<const uint4 *>(lv)[q];
+                    }
+                }
+            } else {
+                const float f = ep.alpha / ((*ep.sa) * (*ep.sb));
+                float2 *dst = static_cast<float2 *>(ep.out) + row * ep.ldo + ((n0 + half * HC) >> 1);
+#pragma unroll
+                for (int q = 0; q < HC / 2; ++q) dst[q] = make_float2(sa[2 * q] * f, sa[2 * q + 1] * f);
+            }
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::cluster_sync();   // both CTAs done with TMEM, shared memory and the remote barriers
+    if (warp == 0) tc::tmem_dealloc_pair(tmem, C::NCOLS);
+}
+
 // ---------------------------------------------------------------- adjoint helpers
 // s = 2^(14 - e) from a max |.| held as float bits (a power of two, so scaling is exact)
 __global__ void scale_from_max(const unsigned int *maxbits, float *scale, int n)
@@ -670,14 +944,15 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 }
 
 // 2-D FP16 map: `inner` halves per row (row pitch `pitch` halves, default inner), `rows`
-// rows, box TK x 128 (128 bytes x 128 rows), 128-byte swizzle
-bool make_map(CUtensorMap *m, const void *base, uint64_t inner, uint64_t rows, uint64_t pitch = 0)
+// rows, box TK x box_rows (128 bytes x 128 rows by default), 128-byte swizzle
+bool make_map(CUtensorMap *m, const void *base, uint64_t inner, uint64_t rows, uint64_t pitch = 0,
+              uint32_t box_rows = TM)
 {
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
     if (!enc) return false;
     cuuint64_t dims[2] = {inner, rows};
     cuuint64_t strides[1] = {(pitch ? pitch : inner) * 2};
-    cuuint32_t box[2] = {TK, TM};
+    cuuint32_t box[2] = {TK, box_rows};
     cuuint32_t es[2] = {1, 1};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void *>(base), dims, strides, box, es,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -737,11 +1012,19 @@ static isdf_status mixed_alloc(isdf_plan *p)
     ok &= make_map(&b->m_bwl, b->bwl, 2 * nm, 2 * nm);
     ok &= make_map(&b->m_yh, b->yh, 2 * nm, p->max_rows);
     ok &= make_map(&b->m_yl, b->yl, 2 * nm, p->max_rows);
+    ok &= make_map(&b->m_b1h_half, b->b1h, 2 * n, 2 * nm, 0, TM / 2);
+    ok &= make_map(&b->m_b1l_half, b->b1l, 2 * n, 2 * nm, 0, TM / 2);
+    ok &= make_map(&b->m_b2h_half, b->b2h, 2 * n, 2 * nm, 0, TM / 2);
+    ok &= make_map(&b->m_b2l_half, b->b2l, 2 * n, 2 * nm, 0, TM / 2);
     if (!ok) return ISDF_ERR_CUDA;
     ISDF_CUDA_TRY(
         cudaFuncSetAttribute(tc_gemm_persist<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     ISDF_CUDA_TRY(
         cudaFuncSetAttribute(tc_gemm_persist<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    ISDF_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_pair<true, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       PairCfg<true, 128>::SMEM));
+    ISDF_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_pair<false, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       PairCfg<false, 256>::SMEM));
     return ISDF_OK;
 }
 
@@ -821,11 +1104,28 @@ isdf_status mixed_fit(isdf_plan *p, int64_t row_begin, int64_t row_count, void *
         const int n_tiles = n_tiles_n * m_tiles;
         const unsigned grid = (unsigned)(n_tiles < num_sms() ? n_tiles : num_sms());
         const unsigned threads = GEMM_THREADS;
+        // CTA pairs for the M^-1 application: 256 x 256 tiles (each CTA 128 rows and 128 B rows). The Gram
+        // product stays on single CTAs: as 256 x 128 pair tiles (two accumulators per tile leave no room for
+        // 256 columns) it ran 1.5x slower than the single-CTA kernel at N = 1024, N_mu = 4096.
+        const int m_ptiles = (rows + 2 * TM - 1) / (2 * TM);
+        const int pn_gram = (2 * nm) / TN, pn_apply = (2 * nm) / 256;
+        const int pairs = num_sms() / 2;
+        const bool use_pairs = (2 * nm) % 256 == 0;
+        constexpr bool kGramPairs = false;
         // a10: Y_b = (Phi_b Phi_mu^H) o conj(Psi_b Psi_mu^H), written split for the next GEMM
         timer_start(p, 0, st);
-        tc_gemm_persist<true><<<grid, threads, SMEM_BYTES, st>>>(b->m_a1h, b->m_a1l, b->m_b1h, b->m_b1l, b->m_a2h,
-                                                                 b->m_a2l, b->m_b2h, b->m_b2l, (2 * n) / TK, (int)r0,
-                                                                 rows, n_tiles_n, n_tiles, kGramSegment, ep); isdf_note_launch();
+        if (use_pairs && kGramPairs) {
+            const int pt = pn_gram * m_ptiles;
+            tc_gemm_pair<true, 128><<<2 * (pt < pairs ? pt : pairs), threads, PairCfg<true, 128>::SMEM, st>>>(
+                b->m_a1h, b->m_a1l, b->m_b1h_half, b->m_b1l_half, b->m_a2h, b->m_a2l, b->m_b2h_half, b->m_b2l_half,
+                (2 * n) / TK, (int)r0, rows, pn_gram, pt, kGramSegment, ep);
+        } else {
+            tc_gemm_persist<true><<<grid, threads, SMEM_BYTES, st>>>(b->m_a1h, b->m_a1l, b->m_b1h, b->m_b1l, b->m_a2h,
+                                                                     b->m_a2l, b->m_b2h, b->m_b2l, (2 * n) / TK,
+                                                                     (int)r0, rows, n_tiles_n, n_tiles, kGramSegment,
+                                                                     ep);
+        }
+        isdf_note_launch();
         timer_stop(p, 0, st, rows);
         ISDF_LAUNCH_CHECK();
         // a11: Theta_b = Y_b M^-1
@@ -836,9 +1136,17 @@ isdf_status mixed_fit(isdf_plan *p, int64_t row_begin, int64_t row_count, void *
         ep.sb = &b->sc->s_w;
         ep.alpha = 1.f;
         timer_start(p, 1, st);
-        tc_gemm_persist<false><<<grid, threads, SMEM_BYTES, st>>>(b->m_yh, b->m_yl, b->m_bwh, b->m_bwl, b->m_yh,
-                                                                  b->m_yl, b->m_bwh, b->m_bwl, (2 * nm) / TK, 0, rows,
-                                                                  n_tiles_n, n_tiles, kApplySegment, ep); isdf_note_launch();
+        if (use_pairs) {
+            const int pt = pn_apply * m_ptiles;
+            tc_gemm_pair<false, 256><<<2 * (pt < pairs ? pt : pairs), threads, PairCfg<false, 256>::SMEM, st>>>(
+                b->m_yh, b->m_yl, b->m_bwh, b->m_bwl, b->m_yh, b->m_yl, b->m_bwh, b->m_bwl, (2 * nm) / TK, 0, rows,
+                pn_apply, pt, kApplySegment, ep);
+        } else {
+            tc_gemm_persist<false><<<grid, threads, SMEM_BYTES, st>>>(b->m_yh, b->m_yl, b->m_bwh, b->m_bwl, b->m_yh,
+                                                                      b->m_yl, b->m_bwh, b->m_bwl, (2 * nm) / TK, 0,
+                                                                      rows, n_tiles_n, n_tiles, kApplySegment, ep);
+        }
+        isdf_note_launch();
         timer_stop(p, 1, st, rows);
         ISDF_LAUNCH_CHECK();
     }
