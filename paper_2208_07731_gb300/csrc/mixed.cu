@@ -255,13 +255,14 @@ constexpr int GEMM_THREADS = 64 + 32 * EPI_WARPS;
 // plain row-major order they span ~2 row tiles x every column tile, and a B operand larger than L2
 // (e.g. the 268 MB split M^-1 at N_mu = 4096) is re-read from HBM every ~2 row tiles.
 constexpr int kGroupM = 16;
+constexpr int kGroupPairM = 8;   // pair tiles are 256 rows: 8 of them hold the same 2,048 rows of A as 16 single tiles
 
-__device__ __forceinline__ void tile_coords(int mn, int n_tiles_n, int m_tiles, int &m0, int &n0)
+__device__ __forceinline__ void tile_coords(int mn, int n_tiles_n, int m_tiles, int &m0, int &n0, int group = kGroupM)
 {
-    const int per_group = kGroupM * n_tiles_n;
+    const int per_group = group * n_tiles_n;
     const int g = mn / per_group, r = mn - g * per_group;
-    const int gm0 = g * kGroupM;
-    const int gm = min(kGroupM, m_tiles - gm0);
+    const int gm0 = g * group;
+    const int gm = min(group, m_tiles - gm0);
     m0 = (gm0 + r % gm) * TM;
     n0 = (r / gm) * TN;
 }
@@ -648,7 +649,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(GEMM_THREADS, 1)
             int c = 0, issued = 0;
             for (int t = pair; t < n_work && !failed; t += n_pairs) {
                 int m0, n0;
-                tile_coords(t, n_tiles_n, m_ptiles, m0, n0);          // m0 in pair tiles of TM, n0 in TN units
+                tile_coords(t, n_tiles_n, m_ptiles, m0, n0, kGroupPairM);          // m0 in pair tiles of TM, n0 in TN units
                 m0 = (m0 / TM) * (2 * TM) + (int)rank * TM;           // this CTA's 128 rows of the pair's 256
                 n0 = (n0 / TN) * BN + (int)rank * C::BH;              // this CTA's half of the pair's BN columns
                 for (int s0 = 0; s0 < kchunks && !failed; s0 += seg)
@@ -744,7 +745,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(GEMM_THREADS, 1)
         int tl = 0;
         for (int t = pair; t < n_work && !failed; t += n_pairs) {
             int m0, n0;
-            tile_coords(t, n_tiles_n, m_ptiles, m0, n0);
+            tile_coords(t, n_tiles_n, m_ptiles, m0, n0, kGroupPairM);
             m0 = (m0 / TM) * (2 * TM) + (int)rank * TM;
             n0 = (n0 / TN) * BN;
             const int row = m0 + quarter * 32 + lane;
