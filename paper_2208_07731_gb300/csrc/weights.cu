@@ -17,6 +17,23 @@
 // accumulates; the 128-bit lane sums are added across the warp with carries.
 // GB300 issues FP64 at about 2 operations per clock per SM, so the integer
 // formulation keeps the kernel on the memory system instead of the FP64 pipe.
+//
+// Complex64 rows take a shorter integer path. A float component x = m 2^p
+// (p = max(b, 1) - 150 for the biased exponent b) has the term
+// floor((m 2^k)^2) with k = p + 55 - E. Whenever k >= 0 (every normal
+// component within 2^32 of the row maximum) y = m 2^k is an integer below
+// 2^56, and with y = yh 2^28 + yl,
+//     y^2 = yh^2 2^56 + yh yl 2^29 + yl^2,
+// three products below 2^56 that each lane sums in plain 64-bit registers
+// (128 of them stay below 2^63) and folds into its 128-bit sum every 128
+// terms. Pass 1 finds the smallest magnitude of the row as well as the
+// largest; a row whose components are all normal with k >= 0 runs a loop
+// without branches (k <= 32 there, so yh and yl are two clamped funnel
+// shifts of m 2^4), any other row checks each component and gives zeros,
+// subnormals and components with k < 0 (whose term is floored) the general
+// formula. The integer sum, hence the weight, is the same either way. Pass 1
+// marks the row's L2 lines evict-last and pass 2 evict-first, so that the
+// second read finds them in L2.
 #include <type_traits>
 
 #include "common.cuh"
@@ -29,6 +46,29 @@ constexpr int kNoExp = -0x40000000;   // no non-zero component seen
 struct U128 {
     unsigned long long lo, hi;
 };
+
+// L2 eviction priorities for the two reads of a row: the first read marks its lines evict-last so
+// that they are still in L2 for the second, which marks them evict-first
+__device__ __forceinline__ unsigned long long l2_evict_last()
+{
+    unsigned long long pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ unsigned long long l2_evict_first()
+{
+    unsigned long long pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ uint4 ld_policy(const uint4 *p, unsigned long long pol)
+{
+    uint4 r;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                 : "l"(p), "l"(pol));
+    return r;
+}
 
 __device__ __forceinline__ void add_u128(U128 &a, unsigned long long lo, unsigned long long hi)
 {
@@ -180,37 +220,195 @@ __device__ __forceinline__ int row_exp(const T *row, int n, int lane)
     return __reduce_max_sync(0xffffffffu, exp_of_max(m));
 }
 
-template <typename T>
-__device__ __forceinline__ void row_squares(const T *row, int n, int lane, int E, U128 &a)
+// The complex64 terms of one lane between two folds: sums of yh^2, yh yl, yl^2 and of the floored
+// terms (each below 2^46)
+struct Sq64 {
+    unsigned long long a2, a1, a0, as;
+};
+
+__device__ __forceinline__ void add_y(Sq64 &q, uint32_t m, int k)   // y = m 2^k < 2^56
 {
-    for_components(row, n, lane, [&](auto u) { add_square(a, u, E); });
+    const unsigned long long y = (unsigned long long)m << k;
+    const uint32_t yh = (uint32_t)(y >> 28), yl = (uint32_t)y & 0xFFFFFFFu;
+    q.a2 += (unsigned long long)yh * yh;
+    q.a1 += (unsigned long long)yh * yl;
+    q.a0 += (unsigned long long)yl * yl;
 }
 
-// alpha = 2: SSM (one window over both sets) or PSM (one per set, multiplied)
-template <typename T>
-__global__ void __launch_bounds__(kThreads) weights_squares(const T *__restrict__ phi, int64_t ld_phi, int n_phi,
-                                                            const T *__restrict__ psi, int64_t ld_psi, int n_psi,
-                                                            int64_t n_r, int psm, double *__restrict__ w, int acc)
+// one component: k = max(b, 1) - 95 - E; zeros, subnormals and components far below the row maximum
+// (k < 0: the term is floor(m^2 2^(2k)), m^2 < 2^48) leave the common branch
+__device__ __forceinline__ void add_square_c64(Sq64 &q, uint32_t u, int kbase)
+{
+    const int b = (int)((u >> 23) & 0xFFu);
+    uint32_t m = (u | 0x800000u) & 0xFFFFFFu;
+    int k = b + kbase;
+    if (b == 0 || k < 0) {
+        if (b == 0) {
+            m = u & 0x7FFFFFu;
+            k = 1 + kbase;
+        }
+        if (k < 0) {
+            if (k > -24) q.as += ((unsigned long long)m * m) >> (-2 * k);
+            return;
+        }
+    }
+    add_y(q, m, k);
+}
+
+__device__ __forceinline__ void fold(U128 &a, Sq64 &q)
+{
+    add_u128(a, q.a2 << 56, q.a2 >> 8);
+    add_u128(a, q.a1 << 29, q.a1 >> 35);
+    add_u128(a, q.a0, 0ull);
+    add_u128(a, q.as, 0ull);
+    q = Sq64{0ull, 0ull, 0ull, 0ull};
+}
+
+// A normal component with k = b - 95 - E >= 0 (then k <= 32, since y = m 2^k < 2^56 and m >= 2^23):
+// yh and yl come from m 2^4 < 2^28 by two clamped funnel shifts, without a branch.
+__device__ __forceinline__ void add_normal_c64(Sq64 &q, uint32_t u, int kbase)
+{
+    const uint32_t m4 = ((u << 4) & 0x7FFFFF0u) | 0x8000000u;
+    const unsigned k = (unsigned)((int)((u >> 23) & 0xFFu) + kbase);
+    const uint32_t yh = __funnelshift_lc(m4, 0u, k);        // floor(m 2^(k - 28))
+    const uint32_t yl = __funnelshift_lc(0u, m4, k) >> 4;   // (m 2^k) mod 2^28
+    q.a2 += (unsigned long long)yh * yh;
+    q.a1 += (unsigned long long)yh * yl;
+    q.a0 += (unsigned long long)yl * yl;
+}
+
+// The terms of one complex64 row in the window E, added to a; every lane folds after at most 128 terms.
+// NORMAL: every component of the row is normal and within 2^32 of the maximum (checked by the caller).
+template <bool NORMAL>
+__device__ __forceinline__ void row_squares_c64(const float2 *row, int n, int lane, int E, U128 &a,
+                                                unsigned long long pol)
+{
+    const int kbase = -95 - E;
+    Sq64 q{0ull, 0ull, 0ull, 0ull};
+    auto add = [&](uint32_t u) {
+        if (NORMAL) add_normal_c64(q, u, kbase);
+        else add_square_c64(q, u, kbase);
+    };
+    if ((reinterpret_cast<uintptr_t>(row) & 15) == 0) {
+        const uint4 *v = reinterpret_cast<const uint4 *>(row);
+        const int n2 = n >> 1;
+        for (int c0 = 0; c0 < n2; c0 += 32 * 32) {
+            const int c1 = min(n2, c0 + 32 * 32);
+#pragma unroll 4
+            for (int i = c0 + lane; i < c1; i += 32) {
+                const uint4 t = ld_policy(v + i, pol);
+                add(t.x);
+                add(t.y);
+                add(t.z);
+                add(t.w);
+            }
+            fold(a, q);
+        }
+        if ((n & 1) && lane == 0) {
+            const uint2 t = __ldg(reinterpret_cast<const uint2 *>(row) + (n - 1));
+            add(t.x);
+            add(t.y);
+            fold(a, q);
+        }
+    } else {
+        for (int c0 = 0; c0 < n; c0 += 64 * 32) {
+            const int c1 = min(n, c0 + 64 * 32);
+            for (int i = c0 + lane; i < c1; i += 32) {
+                const uint2 t = __ldg(reinterpret_cast<const uint2 *>(row) + i);
+                add(t.x);
+                add(t.y);
+            }
+            fold(a, q);
+        }
+    }
+}
+
+// The largest and smallest component magnitudes of a complex64 row as bit patterns (lane-local; the
+// caller reduces them over the warp)
+__device__ __forceinline__ void row_range_c64(const float2 *row, int n, int lane, unsigned long long pol,
+                                              uint32_t &mx, uint32_t &mn)
+{
+    auto see = [&](uint32_t u) {
+        const uint32_t v = u & 0x7FFFFFFFu;
+        mx = max(mx, v);
+        mn = min(mn, v);
+    };
+    if ((reinterpret_cast<uintptr_t>(row) & 15) == 0) {
+        const uint4 *v = reinterpret_cast<const uint4 *>(row);
+        const int n2 = n >> 1;
+#pragma unroll 4
+        for (int i = lane; i < n2; i += 32) {
+            const uint4 q = ld_policy(v + i, pol);
+            see(q.x);
+            see(q.y);
+            see(q.z);
+            see(q.w);
+        }
+        if ((n & 1) && lane == 0) {
+            const uint2 q = __ldg(reinterpret_cast<const uint2 *>(row) + (n - 1));
+            see(q.x);
+            see(q.y);
+        }
+    } else {
+        for (int i = lane; i < n; i += 32) {
+            const uint2 q = __ldg(reinterpret_cast<const uint2 *>(row) + i);
+            see(q.x);
+            see(q.y);
+        }
+    }
+}
+
+// row window E and whether the row takes the branch-free path: the smallest magnitude is a normal
+// number with k = b_min - 95 - E >= 0
+__device__ __forceinline__ bool all_normal(uint32_t mn, int E) { return (int)(mn >> 23) >= max(1, 95 + E); }
+
+template <bool NORMAL>
+__device__ __forceinline__ void row_pair_c64(const float2 *a, int na, const float2 *b, int nb, int lane, int E,
+                                             bool both, U128 &s, unsigned long long pol)
+{
+    row_squares_c64<NORMAL>(a, na, lane, E, s, pol);
+    if (both) row_squares_c64<NORMAL>(b, nb, lane, E, s, pol);
+}
+
+// alpha = 2 on complex64 rows: SSM (one window over both sets) or PSM (one per set, multiplied)
+__global__ void __launch_bounds__(kThreads, 4) weights_squares_c64(const float2 *__restrict__ phi, int64_t ld_phi,
+                                                                int n_phi, const float2 *__restrict__ psi,
+                                                                int64_t ld_psi, int n_psi, int64_t n_r, int psm,
+                                                                double *__restrict__ w, int acc)
 {
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const unsigned long long keep = l2_evict_last(), drop = l2_evict_first();
     for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n_r; r += nw) {
-        const T *a = phi + r * ld_phi, *b = psi + r * ld_psi;
-        const int ea = row_exp(a, n_phi, lane), eb = row_exp(b, n_psi, lane);
+        const float2 *a = phi + r * ld_phi, *b = psi + r * ld_psi;
+        uint32_t mxa = 0u, mna = 0xFFFFFFFFu, mxb = 0u, mnb = 0xFFFFFFFFu;
+        row_range_c64(a, n_phi, lane, keep, mxa, mna);
+        row_range_c64(b, n_psi, lane, keep, mxb, mnb);
+        mxa = __reduce_max_sync(0xffffffffu, mxa);
+        mna = __reduce_min_sync(0xffffffffu, mna);
+        mxb = __reduce_max_sync(0xffffffffu, mxb);
+        mnb = __reduce_min_sync(0xffffffffu, mnb);
+        const int ea = exp_of_max(mxa), eb = exp_of_max(mxb);
         double v;
         if (!psm) {
             const int E = max(ea, eb);
             U128 s{0ull, 0ull};
             if (E != kNoExp) {
-                row_squares(a, n_phi, lane, E, s);
-                row_squares(b, n_psi, lane, E, s);
+                if (all_normal(min(mna, mnb), E)) row_pair_c64<true>(a, n_phi, b, n_psi, lane, E, true, s, drop);
+                else row_pair_c64<false>(a, n_phi, b, n_psi, lane, E, true, s, drop);
             }
             s = warp_sum(s);
             v = E == kNoExp ? 0.0 : u128_scaled(s, 2 * E - 110);
         } else {
             U128 sa{0ull, 0ull}, sb{0ull, 0ull};
-            if (ea != kNoExp) row_squares(a, n_phi, lane, ea, sa);
-            if (eb != kNoExp) row_squares(b, n_psi, lane, eb, sb);
+            if (ea != kNoExp) {
+                if (all_normal(mna, ea)) row_pair_c64<true>(a, n_phi, b, n_psi, lane, ea, false, sa, drop);
+                else row_pair_c64<false>(a, n_phi, b, n_psi, lane, ea, false, sa, drop);
+            }
+            if (eb != kNoExp) {
+                if (all_normal(mnb, eb)) row_pair_c64<true>(b, n_psi, a, n_phi, lane, eb, false, sb, drop);
+                else row_pair_c64<false>(b, n_psi, a, n_phi, lane, eb, false, sb, drop);
+            }
             sa = warp_sum(sa);
             sb = warp_sum(sb);
             const double xa = ea == kNoExp ? 0.0 : u128_scaled(sa, 2 * ea - 110);
@@ -218,6 +416,44 @@ __global__ void __launch_bounds__(kThreads) weights_squares(const T *__restrict_
             v = __dmul_rn(xa, xb);
         }
         if (lane == 0) w[r] = acc ? __dadd_rn(w[r], v) : v;   // shared weight of several pairs: one rounding per pair
+    }
+}
+
+// alpha = 2 on complex128 rows: SSM (one window over both sets) or PSM (one per set, multiplied)
+__global__ void __launch_bounds__(kThreads) weights_squares_c128(const double2 *__restrict__ phi, int64_t ld_phi,
+                                                                 int n_phi, const double2 *__restrict__ psi,
+                                                                 int64_t ld_psi, int n_psi, int64_t n_r, int psm,
+                                                                 double *__restrict__ w, int acc)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    auto squares = [&](const double2 *row, int n, int E, U128 &s) {
+        for_components(row, n, lane, [&](unsigned long long u) { add_square(s, u, E); });
+    };
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n_r; r += nw) {
+        const double2 *a = phi + r * ld_phi, *b = psi + r * ld_psi;
+        const int ea = row_exp(a, n_phi, lane), eb = row_exp(b, n_psi, lane);
+        double v;
+        if (!psm) {
+            const int E = max(ea, eb);
+            U128 s{0ull, 0ull};
+            if (E != kNoExp) {
+                squares(a, n_phi, E, s);
+                squares(b, n_psi, E, s);
+            }
+            s = warp_sum(s);
+            v = E == kNoExp ? 0.0 : u128_scaled(s, 2 * E - 110);
+        } else {
+            U128 sa{0ull, 0ull}, sb{0ull, 0ull};
+            if (ea != kNoExp) squares(a, n_phi, ea, sa);
+            if (eb != kNoExp) squares(b, n_psi, eb, sb);
+            sa = warp_sum(sa);
+            sb = warp_sum(sb);
+            const double xa = ea == kNoExp ? 0.0 : u128_scaled(sa, 2 * ea - 110);
+            const double xb = eb == kNoExp ? 0.0 : u128_scaled(sb, 2 * eb - 110);
+            v = __dmul_rn(xa, xb);
+        }
+        if (lane == 0) w[r] = acc ? __dadd_rn(w[r], v) : v;
     }
 }
 
@@ -301,8 +537,12 @@ isdf_status launch_weights(const void *phi, int64_t ld_phi, int n_phi, const voi
     const T *a = static_cast<const T *>(phi);
     const T *b = static_cast<const T *>(psi);
     const double ha = 0.5 * alpha;
-    if (psm || alpha == 2.0)
-        weights_squares<T><<<grid, kThreads, 0, st>>>(a, ld_phi, n_phi, b, ld_psi, n_psi, n_r, psm, w, acc);
+    if (psm || alpha == 2.0) {
+        if constexpr (sizeof(T) == 8)
+            weights_squares_c64<<<grid, kThreads, 0, st>>>(a, ld_phi, n_phi, b, ld_psi, n_psi, n_r, psm, w, acc);
+        else
+            weights_squares_c128<<<grid, kThreads, 0, st>>>(a, ld_phi, n_phi, b, ld_psi, n_psi, n_r, psm, w, acc);
+    }
     else if (alpha == 1.0)
         weights_terms<T, 1><<<grid, kThreads, 0, st>>>(a, ld_phi, n_phi, b, ld_psi, n_psi, n_r, ha, w, acc);
     else if (alpha == 3.0)

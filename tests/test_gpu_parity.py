@@ -69,6 +69,48 @@ def test_weights_complex64_ragged_strided(isdf):
     assert np.array_equal(isdf.weights(A, B, "psm").cpu().numpy(), O.weights(a[:, :n], b, "psm"))
 
 
+def _dynamic_range_rows(rng, n_r, n, scale_exp):
+    """complex64 rows that reach every branch of the integer sum: components up to 2^-60 below the
+    row maximum, exact zeros, subnormals, rows whose maximum is tiny or subnormal, all-zero rows"""
+    x = (rng.standard_normal((n_r, n)) + 1j * rng.standard_normal((n_r, n))).astype(np.complex64)
+    for r in range(n_r):
+        k = r % 7
+        if k == 1:
+            x[r] *= (2.0 ** rng.integers(-60, 1, n)).astype(np.float32)
+        elif k == 2:
+            x[r, rng.random(n) < 0.3] = 0
+        elif k == 3:
+            x[r] = (x[r] * np.float32(1e-40)).astype(np.complex64)          # subnormal components
+        elif k == 4:
+            x[r] = (x[r] * np.float32(1e-30)).astype(np.complex64)
+            x[r, 0] = np.complex64(1e-38 + 2e-39j)
+        elif k == 5:
+            x[r] = 0
+        elif k == 6:
+            x[r] = 0
+            x[r, rng.integers(n)] = np.complex64(3e-45)
+    return (x * np.float32(2.0 ** scale_exp)).astype(np.complex64)
+
+
+def test_weights_complex64_dynamic_range(isdf):
+    # widths above 2048 (a lane folds its 64-bit sums more than once per row), an odd width (the tail
+    # element) and an odd leading dimension (rows alternately 16-byte aligned or not); Psi sits 2^-40
+    # below Phi in half of the rows, so under SSM its whole set lies below the shared window's 2^32 range
+    rng = np.random.default_rng(11)
+    n_r, n_a, n_b = 70, 2101, 40
+    a = _dynamic_range_rows(rng, n_r, n_a, 0)
+    b = _dynamic_range_rows(rng, n_r, n_b, 0)
+    b[::2] = (b[::2] * np.float32(2.0 ** -40)).astype(np.complex64)
+    A, B = torch.from_numpy(a).to(DEV), torch.from_numpy(b).to(DEV)
+    for kind in ("ssm", "psm"):
+        assert np.array_equal(isdf.weights(A, B, kind).cpu().numpy(), O.weights(a, b, kind)), kind
+    # the same rows with the two sets swapped and an even leading dimension of 2102 (all rows aligned)
+    pad = np.zeros((n_r, n_a + 1), np.complex64)
+    pad[:, :n_a] = a
+    P = torch.from_numpy(pad).to(DEV)[:, :n_a]
+    assert np.array_equal(isdf.weights(B, P).cpu().numpy(), O.weights(b, a))
+
+
 def test_weights_medium_bit_exact(isdf, medium):
     w, phi, psi = medium
     ref = O.weights(phi.numpy(), psi.numpy())
