@@ -206,7 +206,12 @@ ISDF_API isdf_status isdf_kmeans_noalloc(const double *w, int32_t nx, int32_t ny
  * forms M = (Phi_mu Phi_mu^H) o conj(Psi_mu Psi_mu^H) in FP64, factors
  * M = L L^H (blocked Cholesky, FP64) and forms M^-1 = L^-H L^-1 in FP64.
  * The plan keeps phi/psi pointers: the orbitals must stay alive and unchanged
- * while the plan is used. idx must hold n_mu distinct indices in [0, n_r)
+ * while the plan is used, with one exception: in ISDF_MIXED mode
+ * isdf_fit_theta and isdf_fit_theta_host read only the FP16 operand copies
+ * that isdf_plan_create / isdf_plan_update made, so once the create or update
+ * has completed on its stream the orbitals may be overwritten (for instance
+ * with the next decomposition's orbitals) until the next isdf_plan_update or
+ * adjoint call, which read them again. idx must hold n_mu distinct indices in [0, n_r)
  * (duplicates make M singular: ISDF_ERR_NOT_HPD). max_rows bounds the rows
  * of one internal block (the plan holds two blocks of max_rows x n_mu
  * complex128 scratch); larger requests are processed in several blocks.
@@ -228,6 +233,22 @@ ISDF_API isdf_status isdf_plan_create(isdf_plan **plan, const void *phi, int64_t
  * complex128 in ISDF_FP64 mode and complex64 in ISDF_MIXED mode. */
 ISDF_API isdf_status isdf_fit_theta(isdf_plan *plan, int64_t row_begin, int64_t row_count,
                            void *theta, int64_t ld_theta, void *stream);
+
+/* The same Theta rows written to host memory. The rows are fitted block by
+ * block (max_rows rows each) into one of three device staging blocks owned by
+ * the plan (allocated on the first call, freed by isdf_plan_destroy); each
+ * block is copied to theta_host on a copy stream of the plan while the next
+ * block is fitted. theta_host: row_count x n_mu, row-major with leading
+ * dimension ld_theta_host >= n_mu, complex128 (ISDF_FP64) / complex64
+ * (ISDF_MIXED), and the whole range must be page-locked host memory
+ * (cudaHostAlloc, cudaMallocHost or cudaHostRegister); pageable or device
+ * memory is refused with ISDF_ERR_INVALID_ARG before any work is enqueued.
+ * Ordered on stream: work enqueued on stream after the call runs after the
+ * last copy has landed (synchronise stream before reading theta_host), also
+ * when the call returns an error after enqueueing part of the work. The
+ * caller must not write theta_host until then. */
+ISDF_API isdf_status isdf_fit_theta_host(isdf_plan *plan, int64_t row_begin, int64_t row_count,
+                                         void *theta_host, int64_t ld_theta_host, void *stream);
 
 /* Adjoint of Theta(Phi, Psi) at fixed idx, for one block of rows.
  * Given dL/dTheta = G (convention G = dL/dRe Theta + i dL/dIm Theta) on the

@@ -57,6 +57,7 @@ def lib():
         L.isdf_kmeans.argtypes = [P, I32, I32, I32, P, I32, P, I32, I32, P, P, P, P, P, P, ctypes.c_size_t, P]
         L.isdf_plan_create.argtypes = [P, P, I64, P, I64, I64, I32, I32, I32, P, I32, I32, I64, P]
         L.isdf_fit_theta.argtypes = [P, I64, I64, P, I64, P]
+        L.isdf_fit_theta_host.argtypes = [P, I64, I64, P, I64, P]
         L.isdf_fit_theta_backward.argtypes = [P, I64, I64, P, I64, P, D, P, I64, P, I64, P, P]
         L.isdf_fit_theta_backward_finalize.argtypes = [P, P, I64, P, I64, P]
         L.isdf_plan_status.argtypes = [P, P]
@@ -92,7 +93,7 @@ def lib():
         L.isdf_status_string.argtypes = [I32]
         L.isdf_status_string.restype = ctypes.c_char_p
         for f in ("isdf_weights", "isdf_kmeans_workspace", "isdf_kmeans", "isdf_plan_create", "isdf_fit_theta",
-                  "isdf_fit_theta_backward", "isdf_fit_theta_backward_finalize", "isdf_plan_status",
+                  "isdf_fit_theta_host", "isdf_fit_theta_backward", "isdf_fit_theta_backward_finalize", "isdf_plan_status",
                   "isdf_plan_copy_matrix", "isdf_plan_update", "isdf_plan_enable_timing", "isdf_plan_kernel_time",
                   "isdf_fit_error", "isdf_cluster_residual", "isdf_exchange_create", "isdf_exchange_potential",
                   "isdf_exchange_apply", "isdf_exchange_status", "isdf_plan_set_wait_budget",
@@ -280,6 +281,21 @@ class Plan:
         _check(lib().isdf_fit_theta(self._h, int(row_begin), int(row_count), _ptr(th), th.stride(0),
                                     _stream(stream)), "isdf_fit_theta")
         return th
+
+    def fit_theta_host(self, out, row_begin: int = 0, row_count: int | None = None, stream=None):
+        """Theta rows into `out`, a pinned CPU tensor (row_count x n_mu, unit column stride): each row block is
+        fitted into a device staging block and copied to `out` while the next block is fitted. Ordered on
+        `stream`; synchronise it before reading `out`."""
+        if row_count is None:
+            row_count = self.n_r - row_begin
+        if out.device.type != "cpu" or not out.is_pinned():
+            raise ValueError("out must be a pinned (page-locked) CPU tensor")
+        if (out.dtype != self.theta_dtype or out.dim() != 2 or out.stride(1) != 1 or out.shape[0] < row_count
+                or out.shape[1] < self.n_mu):
+            raise ValueError("theta output has the wrong dtype, shape or layout")
+        _check(lib().isdf_fit_theta_host(self._h, int(row_begin), int(row_count), _ptr(out), out.stride(0),
+                                         _stream(stream)), "isdf_fit_theta_host")
+        return out
 
     def fit_error(self, row_begin: int = 0, row_count: int | None = None, stream=None) -> dict:
         """Least-squares residual of the fit (Appendix A): device scalars z2 = ||Z||_F^2,

@@ -13,7 +13,12 @@
 //    exceeds a rigorous bound E on |d_fp32 - d_exact| (+ FP64 rounding) the
 //    FP32 winner is the FP64 winner. Otherwise the point re-evaluates the close
 //    candidates with the FP64 formula ((dx*dx + dy*dy) + dz*dz) and takes the
-//    smallest (distance, mu) pair - exactly the brute-force FP64 decision;
+//    smallest (distance, mu) pair - exactly the brute-force FP64 decision. The
+//    bound and the gap test are evaluated in FP32 with upward margins (a test
+//    that errs sends a point to the FP64 path, never past it), and the grid
+//    coordinates RN(i h) of a tile come from a per-CTA table: GB300 issues
+//    FP64 at about 2 operations per clock per SM, so the pass keeps FP64 for
+//    the decisions and the products w*x of the exact sums;
 //  * exact update: each FP64 product w*x enters as the 128-bit integer
 //    floor(w*x*2^s); sums are integer (associative, so the result does not
 //    depend on thread or block order): per warp by shuffles for each distinct
@@ -74,8 +79,7 @@ struct U128 {
 __device__ __forceinline__ U128 fixed_of(double v, int s)
 {
     U128 r{0ull, 0ull};
-    if (v == 0.0) return r;
-    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);   // +-0 gives m = 0 below
     const int e = (int)((b >> 52) & 0x7ff);
     unsigned long long m = b & 0xFFFFFFFFFFFFFull;
     int sh;
@@ -280,18 +284,42 @@ __global__ void __launch_bounds__(32 * NW, 1) km_assign(KmArgs a, int t)
     __shared__ unsigned long long redu[NW];
     __shared__ unsigned long long redu2[NW];
 
+    // grid coordinates of the tile (xs[i] = RN((ix0 + i) hx), ...) and its FP32 extents, formed once per CTA:
+    // the FP64 pipe (about 2 operations per clock per SM) is the scarce unit of this kernel
+    __shared__ double xs[TXE], ys[TY], zs[TZ];
+    __shared__ float hdr32[11];  // hx, hy, hz, Px, Py, Pz (tile extents), ox, oy, oz (origin), L, hmin^2 in FP32
+    __shared__ int s_fix_sh;
+
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int b = blockIdx.x;
     const int tz = b % a.ntz, ty = (b / a.ntz) % a.nty, tx = b / (a.ntz * a.nty);
     const int ix0 = tx * TXE, iy0 = ty * TY, iz0 = tz * TZ;
     const int ex = min(TXE, a.nx - ix0), ey = min(TY, a.ny - iy0), ez = min(TZ, a.nz - iz0);
-    const double ox = __dmul_rn((double)ix0, a.hx), oy = __dmul_rn((double)iy0, a.hy), oz = __dmul_rn((double)iz0, a.hz);
-    const float hx = (float)a.hx, hy = (float)a.hy, hz = (float)a.hz;
-    const float Px = (float)((ex - 1) * a.hx), Py = (float)((ey - 1) * a.hy), Pz = (float)((ez - 1) * a.hz);
+    if (tid < TXE) xs[tid] = __dmul_rn((double)(ix0 + tid), a.hx);
+    else if (tid < TXE + TY) ys[tid - TXE] = __dmul_rn((double)(iy0 + tid - TXE), a.hy);
+    else if (tid < TXE + TY + TZ) zs[tid - TXE - TY] = __dmul_rn((double)(iz0 + tid - TXE - TY), a.hz);
+    else if (tid == 32) {
+        hdr32[0] = (float)a.hx;
+        hdr32[1] = (float)a.hy;
+        hdr32[2] = (float)a.hz;
+        hdr32[3] = (float)((ex - 1) * a.hx);
+        hdr32[4] = (float)((ey - 1) * a.hy);
+        hdr32[5] = (float)((ez - 1) * a.hz);
+        hdr32[6] = (float)__dmul_rn((double)ix0, a.hx);   // = (float)xs[0], ...
+        hdr32[7] = (float)__dmul_rn((double)iy0, a.hy);
+        hdr32[8] = (float)__dmul_rn((double)iz0, a.hz);
+        hdr32[9] = (float)a.lmax;
+        hdr32[10] = (float)a.tie_floor;
+        n_cand = 0u;
+        if (!FINAL) s_fix_sh = fixed_scale(a);
+    }
+    __syncthreads();
+    const double ox = xs[0], oy = ys[0], oz = zs[0];
+    const float hx = hdr32[0], hy = hdr32[1], hz = hdr32[2];
+    const float Px = hdr32[3], Py = hdr32[4], Pz = hdr32[5];
 
-    if (tid == 0) n_cand = 0u;
     // ---- tile scan (FP32, conservative): min over centroids of the largest squared distance to the tile
-    const float ox32 = (float)ox, oy32 = (float)oy, oz32 = (float)oz;
+    const float ox32 = hdr32[6], oy32 = hdr32[7], oz32 = hdr32[8];
     const float dq = a.scan_err;
     float mub = INFINITY;
     for (int m = tid; m < a.n_mu; m += NT) {
@@ -382,11 +410,15 @@ __global__ void __launch_bounds__(32 * NW, 1) km_assign(KmArgs a, int t)
     // rigorous bound on |d_fp32 - d_exact| (+ FP64 rounding) for this warp: the point coordinates
     // (integer offset x FP32 spacing) carry <= 2.01 u32 |p|, the candidates <= 1.0001 u32 |q|,
     // their difference one more rounding, then three FP32 products and two FP32 additions
-    const double u32 = 5.9604644775390625e-8;  // 2^-24
-    const double Pm = (double)Tmx, Qm = (double)wq;
-    const double Tm = (Pm + Qm) * (1.0 + 4.0 * u32);
-    const double del = 1.01 * u32 * (2.01 * Pm + 1.0001 * Qm + (Pm + Qm)) + 8e-16 * a.lmax;
-    const double E = 1.01 * (3.0 * del * (2.0 * Tm + del) + 9.001 * u32 * Tm * Tm + 1.6e-15 * 3.0 * Tm * Tm);
+    // It is evaluated in FP32: every quantity is positive, so each operation adds at most a relative
+    // 2^-24 (a fused multiply-add one rounding); the factor 1 + 2^-16 covers the dozen roundings, and the
+    // formula's 1 % slack the rounding of its decimal constants and of L.
+    constexpr float u32 = 5.9604644775390625e-8f;   // 2^-24
+    constexpr float up = 1.f + 1.52587890625e-5f;   // 1 + 2^-16
+    const float Pm = Tmx, Qm = wq;
+    const float Tm = (Pm + Qm) * (1.f + 4.f * u32);
+    const float del = 1.01f * u32 * (2.01f * Pm + 1.0001f * Qm + (Pm + Qm)) + 8e-16f * hdr32[9];
+    const float E = 1.01f * (3.f * del * (2.f * Tm + del) + 9.001f * u32 * Tm * Tm + 1.6e-15f * 3.f * Tm * Tm) * up;
 
     // ---- the two points of this lane
     const int lx2 = lane >> 4, ly = (lane >> 2) & 3, lz = lane & 3;
@@ -424,7 +456,7 @@ __global__ void __launch_bounds__(32 * NW, 1) km_assign(KmArgs a, int t)
 
     double jv = 0.0;
     unsigned long long my_ties = 0, my_ref = 0;
-    const int s_fix = FINAL ? 0 : fixed_scale(a);
+    const int s_fix = FINAL ? 0 : s_fix_sh;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         int key = -1;
@@ -432,13 +464,13 @@ __global__ void __launch_bounds__(32 * NW, 1) km_assign(KmArgs a, int t)
         if (valid[h]) {
             const int ix = ix0 + bx + lx2 + 2 * h, iy = iy0 + by + ly, iz = iz0 + bz + lz;
             const int64_t r = ((int64_t)ix * a.ny + iy) * a.nz + iz;
-            const double x = __dmul_rn((double)ix, a.hx), y = __dmul_rn((double)iy, a.hy),
-                         z = __dmul_rn((double)iz, a.hz);
-            const double dd1 = (double)d1[h];
-            const double gap = 2.0 * E + 2.0e-12 * fmax(dd1 + E, a.tie_floor) + 1.0e-14 * (dd1 + E);
+            const double x = xs[bx + lx2 + 2 * h], y = ys[by + ly], z = zs[bz + lz];   // RN(ix hx), ...
+            // the FP32 winner is the FP64 winner when the runner-up is further than the gap; the test is
+            // conservative in FP32 (gap rounded up by 1 + 2^-16, the difference scaled down by 1 - 2^-22)
+            const float gap = (2.f * E + 2.0e-12f * fmaxf(d1[h] + E, hdr32[10]) + 1.0e-14f * (d1[h] + E)) * up;
             int win_j = j1[h], win_mu = __float_as_int(cand[j1[h]].w);
             double win_d = 0.0;
-            if ((double)d2[h] - dd1 > gap) {
+            if ((d2[h] - d1[h]) * (1.f - 2.384185791015625e-7f) > gap) {
                 if (FINAL || a.want_obj)
                     win_d = dist2_fp64(x, y, z, a.cent[3 * win_mu], a.cent[3 * win_mu + 1], a.cent[3 * win_mu + 2]);
             } else {
@@ -446,7 +478,7 @@ __global__ void __launch_bounds__(32 * NW, 1) km_assign(KmArgs a, int t)
                 my_ref += 1;
                 double b1 = INFINITY, b2 = INFINITY;
                 int bm = 0x7fffffff, bj = 0;
-                const double lim = dd1 + gap;
+                const double lim = (double)d1[h] + (double)gap;
                 for (int i = 0; i < cnt; ++i) {
                     const int j = use_w ? (int)wlist[warp][i] : i;
                     const float4 q = cand[j];

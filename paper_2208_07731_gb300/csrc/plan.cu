@@ -518,6 +518,75 @@ extern "C" isdf_status isdf_fit_theta(isdf_plan *p, int64_t row_begin, int64_t r
     return ISDF_OK;
 }
 
+// Staging blocks, copy stream and events of isdf_fit_theta_host, made on its first call.
+static isdf_status host_stage_init(isdf_plan *p, size_t es)
+{
+    if (!p->hcopy) {
+        ISDF_CUDA_TRY(cudaStreamCreateWithFlags(&p->hcopy, cudaStreamNonBlocking));
+        ISDF_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_hjoin, cudaEventDisableTiming));
+        for (int s = 0; s < ISDF_HOST_STAGES; ++s) {
+            ISDF_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_hfit[s], cudaEventDisableTiming));
+            ISDF_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_hcopied[s], cudaEventDisableTiming));
+        }
+    }
+    for (int s = 0; s < ISDF_HOST_STAGES; ++s)
+        if (!p->hstage[s]) ISDF_CUDA_TRY(cudaMalloc(&p->hstage[s], (size_t)p->max_rows * p->n_mu * es));
+    return ISDF_OK;
+}
+
+// true when [q, q + bytes) starts and ends in page-locked host memory
+static bool page_locked(const void *q, size_t bytes)
+{
+    const char *ends[2] = {static_cast<const char *>(q), static_cast<const char *>(q) + bytes - 1};
+    for (const char *e : ends) {
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, e) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        if (a.type != cudaMemoryTypeHost) return false;
+    }
+    return true;
+}
+
+extern "C" isdf_status isdf_fit_theta_host(isdf_plan *p, int64_t row_begin, int64_t row_count, void *theta_host,
+                                           int64_t ld_theta_host, void *stream)
+{
+    if (!p || row_begin < 0 || row_count < 0 || row_begin + row_count > p->n_r || ld_theta_host < p->n_mu)
+        return ISDF_ERR_INVALID_ARG;
+    if (row_count == 0) return ISDF_OK;
+    const size_t es = p->mode == ISDF_FP64 ? 16 : 8;
+    const size_t row_bytes = (size_t)p->n_mu * es, pitch = (size_t)ld_theta_host * es;
+    if (!theta_host || !aligned(theta_host, es) ||
+        !page_locked(theta_host, (size_t)(row_count - 1) * pitch + row_bytes))
+        return ISDF_ERR_INVALID_ARG;
+    ISDF_TRY(host_stage_init(p, es));
+    cudaStream_t st = as_stream(stream);
+    p->last_stream = st;
+    // every return below leaves the caller's stream waiting for the copies issued so far
+    StreamJoin join;
+    join.arm(st, p->hcopy, p->ev_hjoin);
+    char *dst = static_cast<char *>(theta_host);
+    for (int64_t i = 0, r0 = row_begin; r0 < row_begin + row_count; ++i, r0 += p->max_rows) {
+        const int s = (int)(i % ISDF_HOST_STAGES);
+        const int64_t rows = (row_begin + row_count - r0) < p->max_rows ? (row_begin + row_count - r0) : p->max_rows;
+        // the copy out of this staging block (block i - ISDF_HOST_STAGES) has finished; earlier calls ended joined
+        if (i >= ISDF_HOST_STAGES) ISDF_CUDA_TRY(cudaStreamWaitEvent(st, p->ev_hcopied[s], 0));
+        ISDF_TRY(isdf_fit_theta(p, r0, rows, p->hstage[s], p->n_mu, stream));
+        ISDF_CUDA_TRY(cudaEventRecord(p->ev_hfit[s], st));
+        ISDF_CUDA_TRY(cudaStreamWaitEvent(p->hcopy, p->ev_hfit[s], 0));
+        char *d = dst + (size_t)(r0 - row_begin) * pitch;
+        if (pitch == row_bytes)
+            ISDF_CUDA_TRY(cudaMemcpyAsync(d, p->hstage[s], (size_t)rows * row_bytes, cudaMemcpyDeviceToHost, p->hcopy));
+        else
+            ISDF_CUDA_TRY(cudaMemcpy2DAsync(d, pitch, p->hstage[s], row_bytes, row_bytes, (size_t)rows,
+                                            cudaMemcpyDeviceToHost, p->hcopy));
+        ISDF_CUDA_TRY(cudaEventRecord(p->ev_hcopied[s], p->hcopy));
+    }
+    ISDF_CUDA_TRY(join.join());
+    return ISDF_OK;
+}
+
 extern "C" isdf_status isdf_fit_error(isdf_plan *p, int64_t row_begin, int64_t row_count, double *sums,
                                       void *stream)
 {
@@ -850,5 +919,15 @@ extern "C" void isdf_plan_destroy(isdf_plan *p)
     }
     if (p->ev_aux_fork) cudaEventDestroy(p->ev_aux_fork);
     if (p->ev_aux_join) cudaEventDestroy(p->ev_aux_join);
+    if (p->hcopy) {
+        cudaStreamSynchronize(p->hcopy);
+        cudaStreamDestroy(p->hcopy);
+    }
+    for (int s = 0; s < ISDF_HOST_STAGES; ++s) {
+        if (p->hstage[s]) cudaFree(p->hstage[s]);
+        if (p->ev_hfit[s]) cudaEventDestroy(p->ev_hfit[s]);
+        if (p->ev_hcopied[s]) cudaEventDestroy(p->ev_hcopied[s]);
+    }
+    if (p->ev_hjoin) cudaEventDestroy(p->ev_hjoin);
     free(p);
 }

@@ -8,6 +8,7 @@
 struct MixedBuffers;
 
 #define ISDF_TIMER_KINDS 7
+#define ISDF_HOST_STAGES 3   // device staging blocks of isdf_fit_theta_host
 
 struct isdf_plan {
     const void *phi, *psi;
@@ -33,6 +34,10 @@ struct isdf_plan {
     cudaEvent_t ev_fork, ev_join;             // its fork / join points
     cudaStream_t aux;                         // orbital operand preparation, concurrent with a8-a9
     cudaEvent_t ev_aux_fork, ev_aux_join;
+    // isdf_fit_theta_host: device staging blocks (max_rows x n_mu each), their copy stream and events
+    void *hstage[ISDF_HOST_STAGES];
+    cudaStream_t hcopy;
+    cudaEvent_t ev_hfit[ISDF_HOST_STAGES], ev_hcopied[ISDF_HOST_STAGES], ev_hjoin;
     // optional event timing: kinds 0 Gram kernel, 1 M^-1 application kernel,
     // 2 gather + M, 3 Cholesky factor, 4 triangular inverse, 5 M^-1 = L^-H L^-1,
     // 6 tensor-core operand preparation

@@ -74,6 +74,7 @@ def test_host_side_validation(lib):
     assert lib.isdf_plan_create(ctypes.byref(plan), dummy, 4, dummy, 4, 100, 4, 4, 0, dummy, 200, 0, 64, None) == 1
     assert lib.isdf_plan_create(ctypes.byref(plan), dummy, 4, dummy, 4, 100, 4, 4, 0, dummy, 8, 5, 64, None) == 1
     assert lib.isdf_fit_theta(None, 0, 1, dummy, 8, None) == 1
+    assert lib.isdf_fit_theta_host(None, 0, 1, dummy, 8, None) == 1
     assert lib.isdf_plan_status(None, None) == 1
     assert lib.isdf_fit_error(None, 0, 1, dummy, None) == 1
     lab, ix = P(512), P(1024)
