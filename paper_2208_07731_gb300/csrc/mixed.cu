@@ -559,14 +559,15 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
 // 128 rows of the accumulator in its own TMEM. Per SM and per FLOP this halves the B bytes loaded
 // from L2 and the operand bytes the tensor core reads from shared memory (the single-CTA kernel is
 // bound by that operand feed). Roles:
-//  * rank 0 (leader): warp 0 lane 0 loads the leader's stages and, for every stage, arms it for the
-//    peer (a remote arrive on the peer's `armed` barrier) after adding both CTAs' bytes to the
-//    leader's full barrier; warp 1 lane 0 issues the pair's MMAs and commits them to both CTAs'
-//    empty and tfull barriers; warps 2-9 run the epilogue of the leader's rows;
-//  * rank 1 (peer): warp 0 lane 0 loads the peer's stages into its own shared memory, each only
-//    after the leader armed it (so every peer copy is counted by a leader barrier the leader drains
-//    before the pair exits), completing on the leader's full barrier; warps 2-9 run the epilogue of
-//    the peer's rows and release the accumulator with a remote arrive on the leader's tempty.
+//  * rank 0 (leader): warp 0 lane 0 loads the leader's stages and adds both CTAs' bytes to the
+//    leader's full barrier of each stage; warp 1 lane 0 issues the pair's MMAs and commits them to
+//    both CTAs' empty and tfull barriers; warps 2-9 run the epilogue of the leader's rows;
+//  * rank 1 (peer): warp 0 lane 0 loads the peer's stages into its own shared memory, completing on
+//    the leader's full barrier, as soon as the slot is empty (the barrier's transaction count is
+//    signed, so the peer's bytes may land before the leader's expect: the phase still needs the
+//    leader's arrival and every byte); at the end it reports its stage count to the leader, which
+//    drains every copy of both CTAs before the pair exits; warps 2-9 run the epilogue of the peer's
+//    rows and release the accumulator with a remote arrive on the leader's tempty.
 // Every wait is bounded as in tc_gemm_persist; the pair decides to run or to skip (an earlier
 // failure) once, from the leader's reading, so both CTAs always meet at the cluster barriers.
 template <bool DUAL, int BN>
@@ -596,7 +597,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(GEMM_THREADS, 1)
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[S];
     __shared__ __align__(8) uint64_t empty_bar[S];
-    __shared__ __align__(8) uint64_t armed_bar[S];
+    __shared__ __align__(8) uint64_t peer_bar;   // leader: the peer's producer has finished (count below)
+    __shared__ volatile int peer_issued;          // leader: stages the peer's producer loaded
     __shared__ __align__(8) uint64_t tfull[2];
     __shared__ __align__(8) uint64_t tempty[2];
     __shared__ __align__(8) uint64_t drain_bar;
@@ -618,7 +620,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(GEMM_THREADS, 1)
         for (int s = 0; s < S; ++s) {
             tc::mbar_init(&full_bar[s], 1);
             tc::mbar_init(&empty_bar[s], 1);
-            tc::mbar_init(&armed_bar[s], 1);
         }
         for (int a = 0; a < 2; ++a) {
             tc::mbar_init(&tfull[a], 1);
@@ -626,6 +627,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(GEMM_THREADS, 1)
         }
         tc::mbar_init(&drain_bar, 1);
         tc::mbar_init(&never_bar, 1);
+        tc::mbar_init(&peer_bar, 1);
         failed = 0;
         skip = *(volatile int *)ep.err ? 1u : 0u;   // only the leader's reading is used
         tc::fence_barrier_init();
@@ -656,16 +658,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(GEMM_THREADS, 1)
                     for (int part = 0; part < C::PARTS && !failed; ++part)
                         for (int kc = s0; kc < min(kchunks, s0 + seg); ++kc, ++c) {
                             const int s = c % S, it = c / S;
-                            if (!tc::mbar_wait(&empty_bar[s], (it & 1) ^ 1, budget) ||
-                                (!leader && !tc::mbar_wait(&armed_bar[s], it & 1, budget))) {
+                            if (!tc::mbar_wait(&empty_bar[s], (it & 1) ^ 1, budget)) {
                                 atomicExch(ep.err, 1);
                                 failed = 1;
                                 break;
                             }
-                            if (leader) {
-                                tc::mbar_expect_tx(&full_bar[s], 2 * C::STAGE);   // both CTAs' bytes
-                                tc::mbar_arrive_cluster(tc::map_shared(&armed_bar[s], 1));
-                            }
+                            if (leader) tc::mbar_expect_tx(&full_bar[s], 2 * C::STAGE);   // both CTAs' bytes
                             const CUtensorMap *const *mp = maps + 4 * part;
                             uint8_t *st = sbase + s * C::STAGE;
                             const uint32_t fb = full0 + (uint32_t)(s * sizeof(uint64_t));
@@ -676,10 +674,22 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(GEMM_THREADS, 1)
                             issued = c + 1;
                         }
             }
-            // the leader waits for every stage it armed (its full barrier counts the peer's copies too)
-            if (leader)
-                for (int c2 = issued - S > 0 ? issued - S : 0; c2 < issued; ++c2)
+            // Every copy of either CTA completes on a leader barrier, so the leader drains them all before the
+            // pair exits: the peer reports how many stages it loaded, and the leader waits for the last S
+            // stages of either CTA, arming for the peer's bytes alone the stages only the peer loaded (after a
+            // failure the peer can run up to S stages ahead of the leader's producer, never more: it loads a
+            // stage only after the MMA released the slot's previous stage, which the leader loaded).
+            if (!leader) {
+                tc::st_shared_cluster(tc::map_shared((const void *)&peer_issued, 0), (uint32_t)issued);
+                tc::mbar_arrive_cluster(tc::map_shared(&peer_bar, 0));
+            } else {
+                int hi = issued;
+                if (tc::mbar_wait_cluster(&peer_bar, 0, WAIT_BUDGET)) hi = max(hi, (int)peer_issued);
+                for (int c2 = hi - S > 0 ? hi - S : 0; c2 < hi; ++c2) {
+                    if (c2 >= issued) tc::mbar_expect_tx(&full_bar[c2 % S], C::STAGE);
                     tc::mbar_wait(&full_bar[c2 % S], (c2 / S) & 1, WAIT_BUDGET);
+                }
+            }
         }
         __syncwarp();
     } else if (warp == 1) {

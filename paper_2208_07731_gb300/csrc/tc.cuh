@@ -184,6 +184,31 @@ __device__ __forceinline__ uint32_t ld_shared_cluster(uint32_t addr)
 }
 
 // arrive on an mbarrier of another CTA of the cluster (shared::cluster address)
+// a 32-bit store into the shared memory of a CTA of the cluster (addr from map_shared)
+__device__ __forceinline__ void st_shared_cluster(uint32_t addr, uint32_t v)
+{
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+
+// a bounded wait with cluster-scope acquire: afterwards this thread sees what another CTA of the cluster
+// wrote before its release arrive on the barrier
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t *bar, uint32_t parity, long long budget)
+{
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > budget) return false;
+    }
+}
+
 __device__ __forceinline__ void mbar_arrive_cluster(uint32_t addr)
 {
     asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(addr) : "memory");
