@@ -237,8 +237,8 @@ ISDF_API isdf_status isdf_fit_theta(isdf_plan *plan, int64_t row_begin, int64_t 
 /* The same Theta rows written to host memory. The rows are fitted block by
  * block (max_rows rows each) into one of three device staging blocks owned by
  * the plan (allocated on the first call, freed by isdf_plan_destroy); each
- * block is copied to theta_host on a copy stream of the plan while the next
- * block is fitted. theta_host: row_count x n_mu, row-major with leading
+ * block is copied to theta_host, in two halves on two copy streams of the
+ * plan, while the next block is fitted. theta_host: row_count x n_mu, row-major with leading
  * dimension ld_theta_host >= n_mu, complex128 (ISDF_FP64) / complex64
  * (ISDF_MIXED), and the whole range must be page-locked host memory
  * (cudaHostAlloc, cudaMallocHost or cudaHostRegister); pageable or device

@@ -521,13 +521,16 @@ extern "C" isdf_status isdf_fit_theta(isdf_plan *p, int64_t row_begin, int64_t r
 // Staging blocks, copy stream and events of isdf_fit_theta_host, made on its first call.
 static isdf_status host_stage_init(isdf_plan *p, size_t es)
 {
-    if (!p->hcopy) {
-        ISDF_CUDA_TRY(cudaStreamCreateWithFlags(&p->hcopy, cudaStreamNonBlocking));
-        ISDF_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_hjoin, cudaEventDisableTiming));
+    if (!p->ev_hjoin) {
+        if (!p->hcopy) ISDF_CUDA_TRY(cudaStreamCreateWithFlags(&p->hcopy, cudaStreamNonBlocking));
+        if (!p->hcopy2) ISDF_CUDA_TRY(cudaStreamCreateWithFlags(&p->hcopy2, cudaStreamNonBlocking));
         for (int s = 0; s < ISDF_HOST_STAGES; ++s) {
-            ISDF_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_hfit[s], cudaEventDisableTiming));
-            ISDF_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_hcopied[s], cudaEventDisableTiming));
+            if (!p->ev_hfit[s]) ISDF_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_hfit[s], cudaEventDisableTiming));
+            if (!p->ev_hcopied[s]) ISDF_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_hcopied[s], cudaEventDisableTiming));
+            if (!p->ev_hhalf[s]) ISDF_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_hhalf[s], cudaEventDisableTiming));
         }
+        if (!p->ev_hjoin2) ISDF_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_hjoin2, cudaEventDisableTiming));
+        ISDF_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_hjoin, cudaEventDisableTiming));   // last: marks all made
     }
     for (int s = 0; s < ISDF_HOST_STAGES; ++s)
         if (!p->hstage[s]) ISDF_CUDA_TRY(cudaMalloc(&p->hstage[s], (size_t)p->max_rows * p->n_mu * es));
@@ -564,8 +567,9 @@ extern "C" isdf_status isdf_fit_theta_host(isdf_plan *p, int64_t row_begin, int6
     cudaStream_t st = as_stream(stream);
     p->last_stream = st;
     // every return below leaves the caller's stream waiting for the copies issued so far
-    StreamJoin join;
+    StreamJoin join, join2;
     join.arm(st, p->hcopy, p->ev_hjoin);
+    join2.arm(st, p->hcopy2, p->ev_hjoin2);
     char *dst = static_cast<char *>(theta_host);
     for (int64_t i = 0, r0 = row_begin; r0 < row_begin + row_count; ++i, r0 += p->max_rows) {
         const int s = (int)(i % ISDF_HOST_STAGES);
@@ -574,15 +578,28 @@ extern "C" isdf_status isdf_fit_theta_host(isdf_plan *p, int64_t row_begin, int6
         if (i >= ISDF_HOST_STAGES) ISDF_CUDA_TRY(cudaStreamWaitEvent(st, p->ev_hcopied[s], 0));
         ISDF_TRY(isdf_fit_theta(p, r0, rows, p->hstage[s], p->n_mu, stream));
         ISDF_CUDA_TRY(cudaEventRecord(p->ev_hfit[s], st));
-        ISDF_CUDA_TRY(cudaStreamWaitEvent(p->hcopy, p->ev_hfit[s], 0));
+        // the block leaves in two halves on two copy streams (two copy engines when the device has them);
+        // the first stream records the block's event once both halves have landed
+        const int64_t h0 = (rows + 1) / 2;
+        const char *src = static_cast<const char *>(p->hstage[s]);
         char *d = dst + (size_t)(r0 - row_begin) * pitch;
-        if (pitch == row_bytes)
-            ISDF_CUDA_TRY(cudaMemcpyAsync(d, p->hstage[s], (size_t)rows * row_bytes, cudaMemcpyDeviceToHost, p->hcopy));
-        else
-            ISDF_CUDA_TRY(cudaMemcpy2DAsync(d, pitch, p->hstage[s], row_bytes, row_bytes, (size_t)rows,
-                                            cudaMemcpyDeviceToHost, p->hcopy));
+        cudaStream_t cs[2] = {p->hcopy, p->hcopy2};
+        for (int k = 0; k < 2; ++k) {
+            const int64_t a = k ? h0 : 0, n = k ? rows - h0 : h0;
+            ISDF_CUDA_TRY(cudaStreamWaitEvent(cs[k], p->ev_hfit[s], 0));
+            if (n == 0) continue;
+            if (pitch == row_bytes)
+                ISDF_CUDA_TRY(cudaMemcpyAsync(d + (size_t)a * pitch, src + (size_t)a * row_bytes, (size_t)n * row_bytes,
+                                              cudaMemcpyDeviceToHost, cs[k]));
+            else
+                ISDF_CUDA_TRY(cudaMemcpy2DAsync(d + (size_t)a * pitch, pitch, src + (size_t)a * row_bytes, row_bytes,
+                                                row_bytes, (size_t)n, cudaMemcpyDeviceToHost, cs[k]));
+        }
+        ISDF_CUDA_TRY(cudaEventRecord(p->ev_hhalf[s], p->hcopy2));
+        ISDF_CUDA_TRY(cudaStreamWaitEvent(p->hcopy, p->ev_hhalf[s], 0));
         ISDF_CUDA_TRY(cudaEventRecord(p->ev_hcopied[s], p->hcopy));
     }
+    ISDF_CUDA_TRY(join2.join());
     ISDF_CUDA_TRY(join.join());
     return ISDF_OK;
 }
@@ -919,15 +936,18 @@ extern "C" void isdf_plan_destroy(isdf_plan *p)
     }
     if (p->ev_aux_fork) cudaEventDestroy(p->ev_aux_fork);
     if (p->ev_aux_join) cudaEventDestroy(p->ev_aux_join);
-    if (p->hcopy) {
-        cudaStreamSynchronize(p->hcopy);
-        cudaStreamDestroy(p->hcopy);
-    }
+    for (cudaStream_t c : {p->hcopy, p->hcopy2})
+        if (c) {
+            cudaStreamSynchronize(c);
+            cudaStreamDestroy(c);
+        }
     for (int s = 0; s < ISDF_HOST_STAGES; ++s) {
         if (p->hstage[s]) cudaFree(p->hstage[s]);
         if (p->ev_hfit[s]) cudaEventDestroy(p->ev_hfit[s]);
         if (p->ev_hcopied[s]) cudaEventDestroy(p->ev_hcopied[s]);
+        if (p->ev_hhalf[s]) cudaEventDestroy(p->ev_hhalf[s]);
     }
     if (p->ev_hjoin) cudaEventDestroy(p->ev_hjoin);
+    if (p->ev_hjoin2) cudaEventDestroy(p->ev_hjoin2);
     free(p);
 }

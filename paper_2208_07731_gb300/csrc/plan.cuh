@@ -36,8 +36,8 @@ struct isdf_plan {
     cudaEvent_t ev_aux_fork, ev_aux_join;
     // isdf_fit_theta_host: device staging blocks (max_rows x n_mu each), their copy stream and events
     void *hstage[ISDF_HOST_STAGES];
-    cudaStream_t hcopy;
-    cudaEvent_t ev_hfit[ISDF_HOST_STAGES], ev_hcopied[ISDF_HOST_STAGES], ev_hjoin;
+    cudaStream_t hcopy, hcopy2;               // each block leaves in two halves, one per stream (copy engine)
+    cudaEvent_t ev_hfit[ISDF_HOST_STAGES], ev_hcopied[ISDF_HOST_STAGES], ev_hhalf[ISDF_HOST_STAGES], ev_hjoin, ev_hjoin2;
     // optional event timing: kinds 0 Gram kernel, 1 M^-1 application kernel,
     // 2 gather + M, 3 Cholesky factor, 4 triangular inverse, 5 M^-1 = L^-H L^-1,
     // 6 tensor-core operand preparation
