@@ -80,10 +80,10 @@ def algorithmic_flops(w):
 # DRAM bytes (read + write) per launch from one ncu capture of the same kernel version on GB300 (only valid for the
 # workload, launch size and kernel version profiled). Silica apply and Gram: the 32,768-row launches of `bench.py
 # --op gemm --workload silica --rows 65536` (the apply on CTA pairs, tiles in groups of 8 pair rows, the peer CTA
-# loading each stage as soon as its slot is empty), scaled by rows
+# loading each stage as soon as its slot is empty, K segments of 1,024), scaled by rows
 # to the 131,072-row launches of the step. Silica weights: the 262,144-row launch of `bench.py --op weights
 # --workload silica --rows 262144`, scaled by rows to the 128^3 grid.
-NCU_TRAFFIC = {("silica", "apply"): 4 * (18.344303e9 + 1.101701e9),
+NCU_TRAFFIC = {("silica", "apply"): 4 * (12.530186e9 + 1.116051e9),
                ("silica", "gram"): 4 * (4.062169e9 + 1.107082e9),
                ("silica", "weights"): 8 * (4.316357e9 + 5.800448e6),
                # the five passes of one exchange potential (ncu on the x, y and fused z passes: 2 x, 2 y, z)

@@ -39,9 +39,13 @@ constexpr int TILE_B = TN * TK * 2;
 constexpr int STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
 constexpr long long WAIT_BUDGET = 200000000LL;   // SM cycles (~0.1 s); normal waits take microseconds
-constexpr int kSegmentK = 512;                   // K per TMEM accumulation segment (summed in FP32 registers)
-constexpr int kApplySegment = kSegmentK / TK;    // K chunks per segment in the M^-1 GEMM
-constexpr int kGramSegment = kSegmentK / TK;     // the same for each of the two Gram products
+// K per TMEM accumulation segment (segments are summed in FP32 registers). Measured on silica-like orbitals
+// (80^3, N = 1024, N_mu = 4096; Theta against the FP64 mode on 16,384 rows): Gram segments of 512 give 5.4e-6, one
+// segment over the whole K 2.3e-5; M^-1 segments of 512 or 1024 give 5.4e-6 / 5.3e-6, one segment 1.2e-5. The
+// longer M^-1 segments drain TMEM half as often (7.45 -> 7.05 ms per 32,768 rows).
+constexpr int kGramSegmentK = 512, kApplySegmentK = 1024;
+constexpr int kApplySegment = kApplySegmentK / TK;   // K chunks per segment in the M^-1 GEMM
+constexpr int kGramSegment = kGramSegmentK / TK;     // the same for each of the two Gram products
 
 struct MixScales {
     unsigned int maxabs_phi, maxrho_phi, maxabs_psi, maxrho_psi, maxabs_w;  // float bits
