@@ -56,23 +56,13 @@ __device__ __forceinline__ double recip_pos(double d)
 // columns) D^-1/2. The inverse of L_kk is not on this critical path: the
 // panel is a forward substitution with L_kk (panel_solve) and the inverses of
 // all diagonal blocks are formed together after the factorisation (inv_diag).
-__global__ void __launch_bounds__(DT) potrf_diag(double2 *A, int64_t lda, const double2 *M0, int k, int nb,
-                                                DeviceStatus *st)
+// The elimination of an nb x nb block held in shared memory (lower triangle of T; d0s its original diagonal
+// entries of M), by every thread of a DT-thread CTA. Afterwards T's columns hold the eliminated values with
+// d_j on the diagonal. Returns false (status set) at a pivot not above 1e-13 of d0 or not finite.
+__device__ bool factor_block(double2 (*T)[NB + 1], const double *d0s, double *rpiv, int *bad, int k, int nb,
+                             DeviceStatus *st)
 {
-    __shared__ double2 T[NB][NB + 1];
-    __shared__ double d0s[NB];     // original diagonal entries of M
-    __shared__ double rpiv[NB];    // 1 / d_j
-    __shared__ double rs[NB];      // 1 / sqrt(d_j)
-    __shared__ int bad[2];         // failing pivot + 1, or 0: written in step j - 1 into slot j & 1,
-                                   // read at the top of step j (two slots keep the read race-free)
-    if (st->code != 0) return;
     const int tid = threadIdx.x;
-    for (int e = tid; e < NB * NB; e += DT) {
-        const int i = e / NB, j = e % NB;
-        T[i][j] = (i < nb && j <= i) ? A[(int64_t)(k + i) * lda + (k + j)] : make_double2(0.0, 0.0);
-    }
-    if (tid < nb) d0s[tid] = M0[(int64_t)(k + tid) * lda + (k + tid)].x;
-    __syncthreads();
     if (tid == 0) {
         const double d = T[0][0].x;
         bad[0] = (!(d > 1e-13 * d0s[0]) || isinf(d)) ? 1 : 0;
@@ -83,7 +73,7 @@ __global__ void __launch_bounds__(DT) potrf_diag(double2 *A, int64_t lda, const 
         const int b = bad[j & 1];   // uniform: written before the last barrier, not rewritten until the next
         if (b) {
             if (tid == 0) set_status(st, isnan(T[b - 1][b - 1].x) ? ISDF_ERR_NONFINITE : ISDF_ERR_NOT_HPD, k + b - 1);
-            return;
+            return false;
         }
         const double r = rpiv[j];
         const int rows = nb - 1 - j;               // i = j+1 .. nb-1
@@ -133,6 +123,27 @@ __global__ void __launch_bounds__(DT) potrf_diag(double2 *A, int64_t lda, const 
         }
         __syncthreads();
     }
+    return true;
+}
+
+__global__ void __launch_bounds__(DT) potrf_diag(double2 *A, int64_t lda, const double2 *M0, int k, int nb,
+                                                DeviceStatus *st)
+{
+    __shared__ double2 T[NB][NB + 1];
+    __shared__ double d0s[NB];     // original diagonal entries of M
+    __shared__ double rpiv[NB];    // 1 / d_j
+    __shared__ double rs[NB];      // 1 / sqrt(d_j)
+    __shared__ int bad[2];         // failing pivot + 1, or 0: written in step j - 1 into slot j & 1,
+                                   // read at the top of step j (two slots keep the read race-free)
+    if (st->code != 0) return;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < NB * NB; e += DT) {
+        const int i = e / NB, j = e % NB;
+        T[i][j] = (i < nb && j <= i) ? A[(int64_t)(k + i) * lda + (k + j)] : make_double2(0.0, 0.0);
+    }
+    if (tid < nb) d0s[tid] = M0[(int64_t)(k + tid) * lda + (k + tid)].x;
+    __syncthreads();
+    if (!factor_block(T, d0s, rpiv, bad, k, nb, st)) return;
     if (tid < nb) rs[tid] = 1.0 / sqrt(T[tid][tid].x);
     __syncthreads();
     for (int e = tid; e < nb * nb; e += DT) {
@@ -176,6 +187,100 @@ __global__ void __launch_bounds__(32 * PW) panel_solve(double2 *L, int64_t ld, i
             }
         }
         if (lane < nb) row[lane] = x;
+    }
+}
+
+// One look-ahead step in a single launch. With block column k final and the next block column at
+// k1 = k + NB (nb1 wide, `rows` rows below its diagonal block):
+//   D   = A[k1:k1+nb1, k1:k1+nb1] - P P^H,  P = L[k1:k1+nb1, k:k+NB]   every CTA, in shared memory
+//   L11 = chol(D)                                                      every CTA, the same elimination
+//   x_r L11^H = A[r, k1:k1+nb1] - L[r, k:k+NB] P^H                      this CTA's rows r, one warp each
+// Every CTA reads the old diagonal block before anyone may overwrite it: the CTA that arrives last on the
+// status word's counter (after its reads) writes L11 back and resets the counter; no CTA waits for another.
+// This replaces the column update, its split-K reduction, potrf_diag and panel_solve on the critical path.
+constexpr int kStepCtas = 152;   // at most one CTA per SM: each repeats the diagonal block's FP64 work
+__global__ void __launch_bounds__(DT) chol_step(double2 *A, int64_t lda, const double2 *M0, int k, int k1, int nb1,
+                                               int rows, DeviceStatus *st)
+{
+    __shared__ double2 T[NB][NB + 1];
+    __shared__ double2 P[NB][NB + 1];
+    __shared__ double d0s[NB], rpiv[NB], rs[NB], rd[NB];
+    __shared__ int bad[2];
+    __shared__ int last;
+    if (st->code != 0) return;
+    const int tid = threadIdx.x;
+    const double2 zero = make_double2(0.0, 0.0);
+    for (int e = tid; e < NB * NB; e += DT) {
+        const int i = e / NB, l = e % NB;
+        P[i][l] = i < nb1 ? A[(int64_t)(k1 + i) * lda + (k + l)] : zero;
+    }
+    if (tid < nb1) d0s[tid] = M0[(int64_t)(k1 + tid) * lda + (k1 + tid)].x;
+    __syncthreads();
+    for (int e = tid; e < NB * NB; e += DT) {   // D = A - P P^H, lower triangle
+        const int i = e / NB, j = e % NB;
+        double2 t = zero;
+        if (i < nb1 && j <= i) {
+            t = A[(int64_t)(k1 + i) * lda + (k1 + j)];
+#pragma unroll 4
+            for (int l = 0; l < NB; ++l) {   // t -= P_il conj(P_jl)
+                const double2 a = P[i][l], b = P[j][l];
+                t.x = fma(-a.x, b.x, fma(-a.y, b.y, t.x));
+                t.y = fma(-a.y, b.x, fma(a.x, b.y, t.y));
+            }
+        }
+        T[i][j] = t;
+    }
+    __syncthreads();   // this CTA's reads of the old diagonal block are done
+    if (tid == 0) {
+        __threadfence();
+        last = atomicAdd(&st->ticket, 1) == (int)gridDim.x - 1;
+    }
+    if (!factor_block(T, d0s, rpiv, bad, k1, nb1, st)) return;
+    if (tid < nb1) rs[tid] = 1.0 / sqrt(T[tid][tid].x);
+    __syncthreads();
+    for (int e = tid; e < NB * NB; e += DT) {   // L11 in place: columns scaled by d^-1/2, diagonal sqrt(d)
+        const int i = e / NB, j = e % NB;
+        if (i < nb1 && j < i) T[i][j] = make_double2(T[i][j].x * rs[j], T[i][j].y * rs[j]);
+        else if (i < nb1 && j == i) T[i][i] = make_double2(T[i][i].x * rs[i], 0.0);
+        else T[i][j] = zero;
+    }
+    __syncthreads();
+    if (tid < nb1) rd[tid] = 1.0 / T[tid][tid].x;
+    if (last) {
+        for (int e = tid; e < nb1 * nb1; e += DT) {
+            const int i = e / nb1, j = e % nb1;
+            A[(int64_t)(k1 + i) * lda + (k1 + j)] = T[i][j];
+        }
+        if (tid == 0) st->ticket = 0;
+    }
+    __syncthreads();
+    const int warp = tid >> 5, lane = tid & 31;
+    if (warp >= PW) return;
+    for (int r = blockIdx.x * PW + warp; r < rows; r += gridDim.x * PW) {
+        double2 *row = A + (int64_t)(k1 + nb1 + r) * lda;
+        const double2 lr = lane < NB ? row[k + lane] : zero;
+        double2 acc = lane < nb1 ? row[k1 + lane] : zero;
+        for (int l = 0; l < NB; ++l) {   // acc -= L[r, k + l] conj(P_cl)
+            const double ax = __shfl_sync(0xffffffffu, lr.x, l), ay = __shfl_sync(0xffffffffu, lr.y, l);
+            if (lane < nb1) {
+                const double2 b = P[lane][l];
+                acc.x = fma(-ax, b.x, fma(-ay, b.y, acc.x));
+                acc.y = fma(-ay, b.x, fma(ax, b.y, acc.y));
+            }
+        }
+        double2 x = zero;
+        for (int c = 0; c < nb1; ++c) {   // forward substitution x L11^H = acc, as panel_solve
+            double2 xs = make_double2(acc.x * rd[c], acc.y * rd[c]);
+            xs.x = __shfl_sync(0xffffffffu, xs.x, c);
+            xs.y = __shfl_sync(0xffffffffu, xs.y, c);
+            if (lane == c) x = xs;
+            if (lane > c && lane < nb1) {   // acc -= x_c conj(L_lc)
+                const double2 b = T[lane][c];
+                acc.x = fma(-xs.x, b.x, fma(-xs.y, b.y, acc.x));
+                acc.y = fma(-xs.y, b.x, fma(xs.x, b.y, acc.y));
+            }
+        }
+        if (lane < nb1) row[k1 + lane] = x;
     }
 }
 
@@ -314,33 +419,22 @@ isdf_status tri_inv(const double2 *L, double2 *Linv, double2 *tmp, int64_t ld, i
 // Right-looking blocked factorisation of the diagonal block L[o:o+m, o:o+m] in place (its lower
 // triangle holds the matrix; earlier columns are already final). Look-ahead: after the panel of
 // block k, a side stream updates block column k+1, factors its diagonal block and forms its panel
-// while this stream updates the rest of the block's trailing matrix (disjoint columns). Each
-// stream has its own split-K scratch.
+// (one chol_step launch) while this stream updates the rest of the block's trailing matrix
+// (disjoint columns).
 isdf_status chol_blocked(const double2 *M0, double2 *L, int64_t ld, int o, int m, double2 *part, size_t part_n,
                          DeviceStatus *st, cudaStream_t stream, isdf_plan *tp)
 {
     const int end = o + m;
     cudaStream_t side = (tp && tp->side) ? tp->side : nullptr;
-    const size_t side_need = (size_t)4 * m * NB;
-    double2 *pside = nullptr, *pmain = part;
-    size_t nmain = part_n;
-    if (part && part_n >= 2 * side_need) {
-        pside = part + (part_n - side_need);
-        nmain = part_n - side_need;
-    } else {
-        side = nullptr;
-    }
-    auto panel = [&](int k, int nb, int rest, cudaStream_t s) -> isdf_status {
-        const int g = (rest + PW - 1) / PW;
-        panel_solve<<<g < 4096 ? g : 4096, 32 * PW, 0, s>>>(L, ld, k, nb, rest, st); isdf_note_launch();
-        ISDF_LAUNCH_CHECK();
-        return ISDF_OK;
-    };
     {
         const int nb = m < NB ? m : NB;
         potrf_diag<<<1, DT, 0, stream>>>(L, ld, M0, o, nb, st); isdf_note_launch();
         ISDF_LAUNCH_CHECK();
-        if (m - nb > 0) ISDF_TRY(panel(o, nb, m - nb, stream));
+        if (m - nb > 0) {
+            const int g = (m - nb + PW - 1) / PW;
+            panel_solve<<<g < 4096 ? g : 4096, 32 * PW, 0, stream>>>(L, ld, o, nb, m - nb, st); isdf_note_launch();
+            ISDF_LAUNCH_CHECK();
+        }
     }
     for (int k = o; k + NB < end; k += NB) {
         const int k1 = k + NB, rest = end - k1;            // next block at k1, rows below block k
@@ -352,25 +446,17 @@ isdf_status chol_blocked(const double2 *M0, double2 *L, int64_t ld, int o, int m
             ISDF_CUDA_TRY(cudaStreamWaitEvent(side, tp->ev_fork, 0));
             fork.arm(stream, side, tp->ev_join);
         }
-        // side: A[k1:, k1:k1+nb1] -= L21 L21[0:nb1]^H, then factor block k1 and its panel
-        ZGemm a = single(rest, nb1, NB, op(L + (int64_t)k1 * ld + k, ld, 1, 0), op(L + (int64_t)k1 * ld + k, 1, ld, 1),
-                         L + (int64_t)k1 * ld + k1, ld, -1.0, 1);
-        a.tile = 32;
-        if (pside) {
-            a.splits = NB >= 32 ? 4 : 2;   // K = NB in chunks of 8
-            a.partial = pside;
-        }
-        ISDF_TRY(zgemm(a, s2));
-        potrf_diag<<<1, DT, 0, s2>>>(L, ld, M0, k1, nb1, st); isdf_note_launch();
+        // side: block column k1 updated by block column k, its diagonal block factored, its panel formed
+        const int g = rest1 > 0 ? ((rest1 + PW - 1) / PW < kStepCtas ? (rest1 + PW - 1) / PW : kStepCtas) : 1;
+        chol_step<<<g, DT, 0, s2>>>(L, ld, M0, k, k1, nb1, rest1, st); isdf_note_launch();
         ISDF_LAUNCH_CHECK();
-        if (rest1 > 0) ISDF_TRY(panel(k1, nb1, rest1, s2));
         // this stream: A[k1+nb1:, k1+nb1:] -= L21[nb1:] L21[nb1:]^H (lower tiles)
         if (rest1 > 0) {
             const double2 *l21 = L + (int64_t)(k1 + nb1) * ld + k;
             ZGemm u = single(rest1, rest1, NB, op(l21, ld, 1, 0), op(l21, 1, ld, 1),
                              L + (int64_t)(k1 + nb1) * ld + (k1 + nb1), ld, -1.0, 1);
             u.lower_only = 1;
-            ISDF_TRY(zgemm_auto(u, pmain, nmain, stream));
+            ISDF_TRY(zgemm_auto(u, part, part_n, stream));
         }
         ISDF_CUDA_TRY(fork.join());
     }

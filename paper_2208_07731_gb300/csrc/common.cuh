@@ -65,6 +65,8 @@ static inline bool aligned(const void *p, size_t a) { return (reinterpret_cast<u
 struct DeviceStatus {
     int32_t code;    // isdf_status
     int32_t detail;  // e.g. the failing pivot
+    int32_t ticket;  // arrival counter of the fused Cholesky step: its last CTA writes back and resets it
+    int32_t pad;
 };
 
 __device__ __forceinline__ void set_status(DeviceStatus *st, int32_t code, int32_t detail)
