@@ -78,3 +78,22 @@ def test_surrogate_gradient_closed_form():
     D = rng.standard_normal(T.shape) + 1j * rng.standard_normal(T.shape)
     fd = (O.surrogate_loss(T + h * D, K, 0.5) - O.surrogate_loss(T - h * D, K, 0.5)) / (2 * h)
     assert abs(fd - np.real(np.vdot(g, D))) < 1e-6 * abs(fd)
+
+
+def test_finite_differences_on_the_nearly_singular_small_case():
+    # the 8^3 case of the GPU adjoint test (48 points for 64 orbital products, a nearly singular M): with
+    # the oracle's own fits, the non-cancelling central difference at h = 1e-5 is within 1e-6 of the
+    # oracle's adjoint on the same 32 directions (at h = 1e-6 FP64 rounding of the fits reaches ~1e-6)
+    w = W.small_workload(n=8, L=6.0, n_orb=8, n_mu=48, iters=10, ecut=6.0, seed=5)
+    phi, psi = (x.numpy() for x in W.make_pair(w))
+    wt = O.weights(phi, psi)
+    idx = O.kmeans(wt, (w.n,) * 3, (w.L,) * 3, w.n_mu, W.init_indices(wt, w.n_mu, 17), w.iters)["idx"]
+    K = W.loss_matrix(w.n_mu, 23)
+    g = O.theta_backward(phi, psi, idx, lambda rows, T: O.surrogate_grad_theta(T, K, w.dV))
+    h = 1e-5
+    for D in W.directions((2,) + phi.shape, 32, 99):
+        tp = O.fit_theta(phi + h * D[0], psi + h * D[1], idx)["theta"]
+        tm = O.fit_theta(phi - h * D[0], psi - h * D[1], idx)["theta"]
+        fd = w.dV * np.real(np.sum(np.conj(tp - tm) * ((tp + tm) @ K.T))) / (2 * h)
+        an = np.real(np.vdot(g["grad_phi"], D[0]) + np.vdot(g["grad_psi"], D[1]))
+        assert abs(fd - an) <= 1e-6 * abs(an), (fd, an)
